@@ -1,0 +1,128 @@
+"""Planted mistakes: each test copies the oracle's C source, plants one
+plausible mistake (a dropped term, a wrong comparison, an off-by-one, a wrong
+neighbourhood), builds it on the CPU and checks that the pins reject it.  The
+oracle itself is never modified."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import brute
+import golden_io
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "oracle", "vl_oracle.c")
+
+MUTANTS = {
+    "reach_drops_l0": ("out[i] = phi1[i] ? 1 : 0;", "out[i] = 0;"),
+    "reach_ignores_phi2": ("if (phi2[u] && !pushed[u])", "if (!pushed[u])"),
+    "reach_needs_phi2_at_x": ("out[u] = 1;                       /* u = pi_0, v = pi_1 */",
+                              "if (phi2[u]) out[u] = 1;"),
+    "near_not_reflexive": ("if (!is_offset(dy, dx, conn)) continue;\n          int yy = y + dy, xx = x + dx;\n          if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;\n          if (a[",
+                           "if (!is_offset(dy, dx, conn) || (dy == 0 && dx == 0)) continue;\n          int yy = y + dy, xx = x + dx;\n          if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;\n          if (a["),
+    "cross_is_square": ("if (conn == 4) return (dy == 0) || (dx == 0);", "(void)conn;"),
+    "threshold_not_strict": ("out[i] = gt ? (v > t) : (v < t);", "out[i] = gt ? (v >= t) : (v <= t);"),
+    "percentile_off_by_one": ("int64_t k = (int64_t)(q * (double)(n - 1));",
+                              "int64_t k = (int64_t)(q * (double)(n - 1) + 0.5);"),
+    "ccl_labels_by_last_pixel": ("labels[u] = (int32_t)s;", "labels[u] = (int32_t)u;"),
+}
+
+
+def _build(tmp, name, old, new):
+    src = open(SRC).read()
+    assert old in src, f"mutation {name} no longer applies"
+    path = os.path.join(tmp, f"{name}.c")
+    with open(path, "w") as fh:
+        fh.write(src.replace(old, new, 1))
+    so = os.path.join(tmp, f"{name}.so")
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-o", so, path])
+    lib = C.CDLL(so)
+    P = C.c_void_p
+    lib.vlo_threshold.argtypes = [P, C.c_int64, C.c_float, C.c_int, P]
+    lib.vlo_near.argtypes = [P, C.c_int, C.c_int, C.c_int, P]
+    lib.vlo_reach.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P]
+    lib.vlo_ccl.argtypes = [P, C.c_int, C.c_int, C.c_int, P]
+    lib.vlo_ccl.restype = C.c_int64
+    lib.vlo_percentile.argtypes = [P, C.c_int64, C.c_double]
+    lib.vlo_percentile.restype = C.c_float
+    return lib
+
+
+def _pins_pass(lib) -> bool:
+    """A compact copy of the pins: hand-worked fixtures, brute-force reach,
+    scipy-free dilation by definition, strict thresholds, percentile ranks,
+    canonical labels."""
+    def near(m, conn):
+        m = np.ascontiguousarray(m, np.uint8)
+        o = np.empty_like(m)
+        lib.vlo_near(m.ctypes.data, m.shape[0], m.shape[1], conn, o.ctypes.data)
+        return o
+
+    def reach(a, b, conn):
+        a = np.ascontiguousarray(a, np.uint8)
+        b = np.ascontiguousarray(b, np.uint8)
+        o = np.empty_like(a)
+        lib.vlo_reach(a.ctypes.data, b.ctypes.data, a.shape[0], a.shape[1], conn, o.ctypes.data)
+        return o
+
+    def ccl(m, conn):
+        m = np.ascontiguousarray(m, np.uint8)
+        o = np.empty(m.shape, np.int32)
+        lib.vlo_ccl(m.ctypes.data, m.shape[0], m.shape[1], conn, o.ctypes.data)
+        return o
+
+    for fx in golden_io.all_fixtures():
+        for conn, exp in fx["expect"].items():
+            if fx["op"] == "near" and not np.array_equal(near(fx["phi"], conn), exp):
+                return False
+            if fx["op"] == "reach" and not np.array_equal(reach(fx["phi1"], fx["phi2"], conn), exp):
+                return False
+            if fx["op"] == "ccl" and not np.array_equal(ccl(fx["phi"], conn), exp):
+                return False
+        if fx["op"] == "percentile":
+            v = np.array([float(x) for x in fx["kv"][0][1:]], np.float32)
+            for _, q, want in fx["kv"][1:]:
+                if lib.vlo_percentile(v.ctypes.data, v.size, float(q)) != float(want):
+                    return False
+    rng = np.random.default_rng(5)
+    for conn in (4, 8):
+        for _ in range(20):
+            a = (rng.random((4, 4)) < 0.2).astype(np.uint8)
+            b = (rng.random((4, 4)) < 0.5).astype(np.uint8)
+            if not np.array_equal(reach(a, b, conn), brute.reach_by_paths(a, b, conn)):
+                return False
+            # dilation by its definition: OR over the neighbourhood, pixel included
+            nb = brute.neighbours(4, 4, conn)
+            exp = np.array([a.ravel()[v] or any(a.ravel()[u] for u in nb[v]) for v in range(16)],
+                           np.uint8).reshape(4, 4)
+            if not np.array_equal(near(a, conn), exp):
+                return False
+    ch = np.array([0.25, 0.5, 0.75], np.float32)
+    o = np.empty(3, np.uint8)
+    lib.vlo_threshold(ch.ctypes.data, 3, C.c_float(0.5), 1, o.ctypes.data)
+    if list(o) != [0, 0, 1]:
+        return False
+    return True
+
+
+@pytest.fixture(scope="module")
+def tmpdir_mod():
+    d = tempfile.mkdtemp(prefix="vlo_mut_")
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+def test_unmutated_source_passes(tmpdir_mod):
+    assert _pins_pass(_build(tmpdir_mod, "clean", "", ""))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_rejected(tmpdir_mod, name):
+    old, new = MUTANTS[name]
+    assert not _pins_pass(_build(tmpdir_mod, name, old, new)), f"pins missed mutant {name}"
