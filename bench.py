@@ -1,0 +1,357 @@
+"""Benchmark: SLCS formula evaluation on GB300.
+
+Workload (one step): the large random formula -- a 2000-node DAG (35 %
+thresholds, 35 % not/and, 20 % N, 10 % rho, depth <= 500, seed 0) over one
+2048 x 2048 float32 U[0,1) image, 8-adjacency, every root mask produced.
+Inputs are resident in HBM; L2 (129 MB) is flushed between timed steps by
+writing a 512 MiB buffer.  `value` is Gpixel-ops/s: primitive nodes after
+expansion and sharing x pixels / step time, summed over ranks.
+
+Also reported: the plain per-operator form on the same workload, full
+connected-component labelling of an 8192 x 8192 Bernoulli(0.5) mask (CCL
+Gpix/s), end-to-end throughput through the public API with host buffers,
+per-step p50/p99, the roofline of the persistent executor, SM clocks during
+the timed region, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 2048
+N_NODES = 2000
+DAG_SEED = 0
+CONN = 8
+METRIC = "Gpixel-ops/s and CCL Gpix/s, batched vs plain on 1 GB300, bit-exact; p99 ms"
+UNIT = "Gpixel-ops/s"
+FLUSH_BYTES = 512 << 20
+CPU_ROWS_REF = 64     # rows of the image per reference-arm step
+CPU_ROWS_BASE = 512   # rows for the cpu_baseline sample
+
+
+def workload_config(n_gpus: int) -> dict:
+    return {"workload": "random-formula-2048x2048",
+            "image": [H, W], "formula_nodes": N_NODES, "dag_seed": DAG_SEED,
+            "connectivity": CONN, "l2": "flushed between steps (512 MiB write)",
+            "parallelism": f"replicas{n_gpus}"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0]:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(rows: int):
+    """CPU oracle on the same formula over the top `rows` rows of the image."""
+    import oracle
+    import workloads as wl
+    f = wl.random_dag(N_NODES, seed=DAG_SEED)
+    img = wl.uniform_image(H, W, seed=0)[:, :rows, :].copy()
+    rec = wl.formula_to_records(f)
+    t0 = time.perf_counter()
+    r = oracle.evaluate(rec, f.roots, [img], conn=CONN)
+    dt = time.perf_counter() - t0
+    return r.n_primitive * rows * W / dt / 1e9, dt, r.n_primitive
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample(CPU_ROWS_REF)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt, _ = oracle_sample(CPU_ROWS_REF)
+        vals.append(v)
+        times.append(dt)
+    total = sum(times)
+    n_prim = oracle_sample(1)[2]
+    value = n_prim * CPU_ROWS_REF * W * args.steps / total / 1e9
+    sample = f"full {N_NODES}-node formula on the top {CPU_ROWS_REF} rows of the 2048x2048 image per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/ccl/e2e/cpu legs")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2010_07284_gb300 as vg
+    import workloads as wl
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ctx = vg.Context(device=local)
+    f = wl.random_dag(N_NODES, seed=DAG_SEED)
+    rec = wl.formula_to_records(f)
+    F = ctx.compile(rec, f.roots, CONN)
+    info = F.info()
+    n_prim = info["n_primitive"]
+    P = H * W
+    stream = torch.cuda.Stream()
+    host_img = wl.uniform_image(H, W, seed=rank)
+    dev_img = torch.from_numpy(host_img).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        image = ctx.image(dev_img, stream)
+        batch = ctx.batch([(F, [image])], stream)
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            flush.zero_()
+            batch.run(stream)
+        stream.synchronize()
+        st = batch.result(0).sync()
+        if st != 0:
+            raise SystemExit(f"device status {st}: {ctx.last_error()}")
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            pass
+        clocks = ClockSampler(uuid)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks.start()
+        time.sleep(0.25)
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            batch.run(stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+        st = batch.result(0).sync()
+        if st != 0:
+            raise SystemExit(f"device status {st}: {ctx.last_error()}")
+    total_ms = float(step_ms.sum())
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = world * args.steps * n_prim * P / (total_max / 1e3) / 1e9
+    ms_per_step = total_max / args.steps
+
+    # roofline of the persistent executor (the only kernel of a step):
+    # algorithmic bytes of the whole DAG per launch, per the accounting of
+    # each channel read once, each materialised mask written and
+    # read back once per consumer, and 8.375 B/px per rho
+    alg_bytes = (4.0 * P * info["n_channels_read"]
+                 + P / 8.0 * (info["mask_writes"] + info["mask_reads"])
+                 + P * (8.0 + 2.0 / 8.0) * info["n_selects"])
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (float(np.mean(step_ms)) / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            from paper_2010_07284_gb300 import buildlib
+            if tj.get("source_hash") == buildlib.source_hash():
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": workload_config(world),
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_src} hbm_gbs", "kernel": "k_exec",
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "clocks": clk,
+            "formula": {"n_primitive": n_prim, "n_reach": info["n_reach"],
+                        "n_steps": info["n_steps"], "n_groups": info["n_groups"],
+                        "n_roots": info["n_roots"]}}
+
+    if not args.no_extras:
+        # ---- plain per-operator form, same workload and image
+        with torch.cuda.stream(stream):
+            pe = []
+            for k in range(4):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r = ctx.eval(F, [image], stream=stream, mode="plain")
+                b.record(stream)
+                stream.synchronize()
+                if r.sync() != 0:
+                    raise SystemExit("plain form failed")
+                if k:
+                    pe.append(a.elapsed_time(b))
+                r.close()
+        line["plain"] = {"value": n_prim * P / (np.mean(pe) / 1e3) / 1e9, "unit": UNIT,
+                         "ms_per_step": float(np.mean(pe)), "steps": len(pe),
+                         "launches_per_step": "one per primitive (4 per rho select + 2)"}
+        line["batched_over_plain"] = line["value"] / world / line["plain"]["value"]
+        # ---- full CCL on an 8192 x 8192 Bernoulli(0.5) mask
+        S = 8192
+        m = torch.rand((S, S), device="cuda", generator=torch.Generator("cuda").manual_seed(3)) < 0.5
+        with torch.cuda.stream(stream):
+            mimg = ctx.mask(m.to(torch.uint8), stream)
+            labels = torch.empty(S * S, dtype=torch.int32, device="cuda")
+            ce = []
+            for k in range(6):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.ccl(mimg, labels, 8, stream)
+                b.record(stream)
+                if k >= 2:
+                    ce.append((a, b))
+            stream.synchronize()
+            if ctx.ccl_status(stream) != 0:
+                raise SystemExit("ccl failed: " + ctx.last_error())
+        cms = float(np.mean([a.elapsed_time(b) for a, b in ce]))
+        line["ccl"] = {"value": S * S / (cms / 1e3) / 1e9, "unit": "Gpix/s", "ms": cms,
+                       "mask": "8192x8192 Bernoulli(0.5), 8-adjacency",
+                       "achieved_GBps": 4.125 * S * S / (cms / 1e3) / 1e9,
+                       "frac": 4.125 * S * S / (cms / 1e3) / 1e9 / peak}
+        del labels, m, mimg
+        # ---- end to end through the public API with host buffers
+        import torch as _t
+        pin_in = _t.from_numpy(host_img).pin_memory()
+        res_words = info["n_roots"] * H * (((W + 127) // 128) * 4)
+        pin_out = _t.empty(res_words, dtype=_t.int32).pin_memory()
+        e2e = []
+        with torch.cuda.stream(stream):
+            for k in range(4):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                im = ctx.image(pin_in.numpy(), stream)
+                r = ctx.eval(F, [im], stream=stream)
+                r.masks_into(pin_out.numpy(), on_device=False, stream=stream)
+                t1 = time.perf_counter()
+                if r.sync() != 0:
+                    raise SystemExit("e2e failed")
+                if k:
+                    e2e.append(t1 - t0)
+                r.close()
+                im.close()
+        line["e2e"] = {"value": world * n_prim * P / float(np.mean(e2e)) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": int(host_img.nbytes),
+                       "d2h_bytes_per_step": int(res_words * 4),
+                       "ms_per_step": 1e3 * float(np.mean(e2e))}
+        # ---- CPU oracle on a bounded sample (rank 0 only)
+        if rank == 0:
+            v, dt, _ = oracle_sample(CPU_ROWS_BASE)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"full formula on the top {CPU_ROWS_BASE} rows "
+                                              f"(of 2048) of the image, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,402 @@
+/*
+ * vl.h -- C ABI of a GB300-native (sm_103a) spatial model checker for the
+ * logic SLCS on 2D images.
+ *
+ * What it computes (paper "A spatial model checker in GPU", Sec. 2): a
+ * formula phi ::= p | not phi | phi1 and phi2 | N phi | rho phi1[phi2]
+ * (Eq. def:syntax) is interpreted on the pixels of an image of fixed size,
+ * and its value is the binary image of the pixels satisfying it.  Atomic
+ * propositions are thresholds on an image feature; not / and are pixel-wise;
+ * N phi is the dilation of phi by the Moore neighbourhood (8-adjacency) or by
+ * the cross (4-adjacency); rho phi1[phi2] holds at x when some path from x
+ * reaches a phi1 pixel with every intermediate pixel in phi2.  As in the
+ * paper's tool (Sec. 3.2), a formula is a DAG of operator tasks whose
+ * sub-expressions are shared, evaluated on data that stays on the device
+ * (Sec. 3.2) and read back only on request; rho reduces to connected
+ * component labelling (Sec. 3.2-3.3).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a vl_status.  Nothing aborts or throws across the ABI.
+ *    After an error, vl_last_error(ctx) gives a one-line message.
+ *  - Handles (vl_context, vl_image, vl_formula, vl_result, vl_server) are
+ *    owned by the library; release each with vl_free().  vl_free(NULL) is a
+ *    no-op.  A handle must not be freed while work that uses it is still
+ *    queued on a stream (call vl_result_sync first).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Work is enqueued asynchronously and ordered on that
+ *    stream like any CUDA call; the host does not wait unless an entry point
+ *    says so.
+ *  - Pointers: "host" pointers are ordinary CPU memory (pinned or not);
+ *    "device" pointers are CUDA global memory on the context's device.
+ *  - Masks are bit-packed, LSB first: pixel (y, x) of an H x W mask is bit
+ *    (x mod 32) of word y*Wp + x/32, with Wp = 4 * ceil(W / 128) words per
+ *    row (rows padded to 16 bytes).  Padding bits are always 0.
+ *  - Labels are int32, row-major H x W; a component is labelled by its
+ *    minimum linear index y*W + x; background pixels are -1.
+ */
+#ifndef VL_H_
+#define VL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(_WIN32)
+#define VL_API __declspec(dllexport)
+#else
+#define VL_API __attribute__((visibility("default")))
+#endif
+
+/* ------------------------------------------------------------------ status */
+
+typedef enum {
+  VL_OK = 0,
+  VL_ERR_ARG = 1,       /* bad argument (null pointer, bad size, bad handle) */
+  VL_ERR_FORMULA = 2,   /* malformed formula: operand order, arity, op code */
+  VL_ERR_SHAPE = 3,     /* images of a call do not share H x W, bad channel */
+  VL_ERR_OOM = 4,       /* device memory could not be obtained */
+  VL_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+  VL_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out (status word) */
+  VL_ERR_BUSY = 7,      /* not finished yet / queue full */
+  VL_ERR_INTERNAL = 8,  /* a device-side consistency check failed */
+  VL_ERR_CANCELLED = 9  /* a served query was cancelled */
+} vl_status;
+
+/* ----------------------------------------------------------------- handles */
+
+typedef struct vl_context vl_context;
+typedef struct vl_image vl_image;
+typedef struct vl_formula vl_formula;
+typedef struct vl_result vl_result;
+typedef struct vl_server vl_server;
+
+/* Execution forms. */
+typedef enum {
+  VL_EXEC_FUSED = 0,  /* persistent executor: fused tile groups, one launch */
+  VL_EXEC_PLAIN = 1   /* one kernel launch per primitive operator */
+} vl_exec_mode;
+
+typedef struct {
+  int32_t device;         /* CUDA device ordinal (default 0) */
+  int32_t exec_mode;      /* vl_exec_mode for vl_eval (default FUSED) */
+  int32_t use_graphs;     /* capture batched launches in CUDA graphs (1) */
+  int32_t reserved0;
+  int64_t spin_limit;     /* cap on polls of every device-side wait; 0 =
+                             default (~2^22 polls with back-off, about a
+                             second); a wait that runs out sets
+                             VL_ERR_TIMEOUT in the result's status word;
+                             negative = every wait expires at once (to
+                             exercise the timeout path) */
+  int64_t memory_budget;  /* bytes the server may hold; 0 = free HBM minus
+                             a reserve */
+  int32_t tile_rows;      /* 0 = autotune; else rows per fused tile */
+  int32_t tile_words;     /* 0 = autotune; else 32-px words per fused tile */
+  int32_t reserved[6];
+} vl_config;
+
+/* Fill *cfg with defaults. */
+VL_API void vl_config_default(vl_config* cfg);
+
+/* Create a context on cfg->device (cfg may be NULL for defaults).  The
+ * context owns a device-memory pool and the formula/plan caches.  Not
+ * thread-safe: one host thread per context, except for vl_server_* which
+ * run their own thread. */
+VL_API vl_status vl_context_create(const vl_config* cfg, vl_context** out);
+
+/* Message of the last error on this context (never NULL; "" if none). */
+VL_API const char* vl_last_error(vl_context* ctx);
+
+/* Release any handle returned by this library (context last).  NULL ok. */
+VL_API void vl_free(void* handle);
+
+/* ------------------------------------------------------------------ images */
+
+/* A float32 image of `channels` planar channels, H x W each: the model of
+ * Sec. 2 with its features (intensity, colour components).  `data` holds
+ * channels*h*w floats, channel-major then row-major, on the host
+ * (data_on_device = 0) or the device (1).  The library copies it into its
+ * own padded device layout on `stream` (the copy is ordered on the stream;
+ * the caller may reuse host memory once the stream reaches it).
+ * Errors: VL_ERR_ARG for h, w, channels < 1 or > 65535, NULL data. */
+VL_API vl_status vl_image_create(vl_context* ctx, int32_t h, int32_t w,
+                                 int32_t channels, const float* data,
+                                 int32_t data_on_device, void* stream,
+                                 vl_image** out);
+
+/* A binary image used directly as an atomic proposition (the paper's atoms
+ * "correspond to binary images", Sec. 2).  `data` is h*w bytes (nonzero =
+ * true), host or device. */
+VL_API vl_status vl_mask_create(vl_context* ctx, int32_t h, int32_t w,
+                                const uint8_t* data, int32_t data_on_device,
+                                void* stream, vl_image** out);
+
+/* Same, from an already bit-packed mask (h * Wp uint32 words, layout as at
+ * the top of this file; padding bits are cleared by the library). */
+VL_API vl_status vl_mask_create_packed(vl_context* ctx, int32_t h, int32_t w,
+                                       const uint32_t* words,
+                                       int32_t data_on_device, void* stream,
+                                       vl_image** out);
+
+/* Shape of an image: any output pointer may be NULL.  is_mask = 1 for
+ * images made by vl_mask_create*. */
+VL_API vl_status vl_image_info(const vl_image* img, int32_t* h, int32_t* w,
+                               int32_t* channels, int32_t* is_mask);
+
+/* ---------------------------------------------------------------- formulas */
+
+/* Operators of a formula node.  The primitive ones follow Eq. (def:syntax);
+ * the derived ones are expanded by the compiler into primitives:
+ *   OR(a,b)         = not(not a and not b)
+ *   INTERIOR(a)     = not N not a                    (erosion, Sec. 2)
+ *   SURROUNDED(a,b) = a and not rho(not(a or b))[not b]
+ *   GROW(a,b)       = a or (b and rho a[b])           (Sec. 4.2)
+ *   TOUCH(a,b)      = a and rho b[a]
+ * Atoms: THR_GT / THR_LT compare channel `channel` of image `image` with the
+ * float32 constant `t`, strictly; PCT_GT / PCT_LT compare it with that
+ * channel's percentile: the value of rank floor(q*(n-1)) in ascending order
+ * of its n = H*W values (the "percentiles" normalisation of Sec. 4.2); MASK
+ * reads the binary image `image`; TRUE / FALSE are constants. */
+typedef enum {
+  VL_OP_TRUE = 0, VL_OP_FALSE = 1, VL_OP_THR_GT = 2, VL_OP_THR_LT = 3,
+  VL_OP_PCT_GT = 4, VL_OP_PCT_LT = 5, VL_OP_MASK = 6, VL_OP_NOT = 7,
+  VL_OP_AND = 8, VL_OP_NEAR = 9, VL_OP_REACH = 10, VL_OP_OR = 11,
+  VL_OP_INTERIOR = 12, VL_OP_SURROUNDED = 13, VL_OP_GROW = 14,
+  VL_OP_TOUCH = 15
+} vl_op;
+
+/* One node (32 bytes).  Operands a, b index earlier nodes of the same array
+ * (a, b < own index; -1 when unused).  For REACH, a = phi1 (the target) and
+ * b = phi2 (the intermediate pixels). */
+typedef struct {
+  int32_t op;
+  int32_t a;
+  int32_t b;
+  int32_t image;    /* index into the image list given at evaluation */
+  int32_t channel;  /* channel of that image (threshold atoms) */
+  float t;          /* threshold constant (THR_*) */
+  double q;         /* percentile level in [0, 1] (PCT_*) */
+} vl_node;
+
+/* Compile a formula DAG given as `n_nodes` nodes in topological order and
+ * `n_roots` output node indices (a root may be any node; Sec. 3.2 "output
+ * instructions").  connectivity is 4 or 8 and governs both N and the paths
+ * of rho.  The compiler expands derived operators, shares identical
+ * sub-expressions, and plans fused execution.  Host-only; no device work.
+ * Errors: VL_ERR_FORMULA (operand out of order, unknown op, bad arity,
+ * percentile level outside [0,1]), VL_ERR_ARG.  ctx may be NULL: the plan is
+ * then made for the default tile configuration (a formula is only
+ * evaluated by contexts with the tile configuration it was planned for). */
+VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes,
+                                    int32_t n_nodes, const int32_t* roots,
+                                    int32_t n_roots, int32_t connectivity,
+                                    vl_formula** out);
+
+/* Introspection of a compiled plan (debugging and host-side tests).  Call
+ * with NULL arrays to get the sizes, then again with arrays of at least
+ * those lengths.  Steps run in order; a step of kind 1 (fused group) runs
+ * its instructions on every tile; kinds 2-5 are the four passes of a batch
+ * of component selects (tile labelling, border merge, flag propagation,
+ * final select); kind 0 computes percentiles.  Instruction opcodes: 1
+ * threshold, 2 load slot, 3 not, 4 and, 5 or, 6 N, 7 constant, 8 store
+ * slot, 9 and-not.  Slots: [0, n_inter) intermediates, then one per
+ * distinct root, then one per mask image. */
+typedef struct {
+  int32_t n_steps, n_insns, n_selects, n_pct;
+  int32_t n_inter_slots, n_root_slots, n_mask_slots, n_roots;
+} vl_plan_sizes;
+typedef struct {
+  int32_t kind, insn_off, insn_cnt, halo, sel_off, sel_cnt, pct_off, pct_cnt;
+} vl_plan_step;
+typedef struct {
+  uint8_t op, dst, a, b;   /* b: direction (1 = less-than) for thresholds, value for constants */
+  int16_t halo, slot, image, channel;
+  float t;
+} vl_plan_insn;
+typedef struct {
+  int16_t phi1_slot, phi2_slot, z_slot, scratch;
+} vl_plan_select;
+typedef struct {
+  int16_t image, channel, slot, pad;
+  double q;
+} vl_plan_pct;
+
+VL_API vl_status vl_formula_plan(const vl_formula* f, vl_plan_sizes* sizes,
+                                 vl_plan_step* steps, vl_plan_insn* insns,
+                                 vl_plan_select* selects, vl_plan_pct* pct,
+                                 int32_t* root_slots, int32_t* mask_slot_images);
+
+/* Counts of a compiled formula (any pointer may be NULL):
+ *   n_primitive -- primitive nodes (threshold, not, and, N, rho, constants,
+ *                  masks) after derived-operator expansion and sharing,
+ *                  before any algebraic simplification: the unit of the
+ *                  pixel-operation throughput metric;
+ *   n_reach     -- rho nodes among them;
+ *   n_roots     -- outputs;
+ *   n_images    -- 1 + the largest image index the formula reads. */
+VL_API vl_status vl_formula_info(const vl_formula* f, int64_t* n_primitive,
+                                 int64_t* n_reach, int32_t* n_roots,
+                                 int32_t* n_images);
+
+/* Plan statistics (for accounting and benchmarks). */
+typedef struct {
+  int64_t n_primitive;      /* as vl_formula_info */
+  int64_t n_reach;
+  int64_t n_threshold;      /* threshold / percentile atoms */
+  int64_t n_not, n_and, n_near;
+  int32_t n_roots;
+  int32_t n_images;
+  int32_t n_steps;          /* executor steps (groups + 4 per select batch + percentiles) */
+  int32_t n_groups;         /* fused tile groups */
+  int32_t n_selects;        /* component selects (one per rho after sharing) */
+  int32_t n_channels_read;  /* distinct (image, channel) pairs read by thresholds */
+  int64_t mask_writes;      /* masks written to global memory per evaluation */
+  int64_t mask_reads;       /* masks read back from global memory per evaluation */
+  int32_t max_halo;         /* largest halo of a fused group */
+  int32_t reserved;
+} vl_formula_stats;
+
+VL_API vl_status vl_formula_stats_get(const vl_formula* f, vl_formula_stats* st);
+
+/* -------------------------------------------------------------- evaluation */
+
+/* Evaluate `f` on the images imgs[0..n_imgs) (all H x W; node.image indexes
+ * this list; threshold atoms need float images, MASK atoms mask images).
+ * Enqueues all work on `stream` and returns without waiting; *out receives
+ * a result handle that owns one device mask per root.  The execution form is
+ * the context's exec_mode.  Errors: VL_ERR_SHAPE, VL_ERR_ARG, VL_ERR_OOM,
+ * VL_ERR_CUDA; device-side errors surface at vl_result_sync. */
+VL_API vl_status vl_eval(vl_context* ctx, const vl_formula* f,
+                         vl_image* const* imgs, int32_t n_imgs, void* stream,
+                         vl_result** out);
+
+/* Same with an explicit execution form (vl_exec_mode). */
+VL_API vl_status vl_eval_mode(vl_context* ctx, const vl_formula* f,
+                              vl_image* const* imgs, int32_t n_imgs,
+                              int32_t exec_mode, void* stream,
+                              vl_result** out);
+
+/* One (formula, images) pair of a batch. */
+typedef struct {
+  const vl_formula* formula;
+  vl_image* const* images;
+  int32_t n_images;
+  int32_t reserved;
+} vl_job;
+
+/* Evaluate many jobs (images of different sizes allowed between jobs) in
+ * one persistent launch; outs[i] receives job i's result.  When the
+ * context's use_graphs is set, the launch sequence is captured into a CUDA
+ * graph cached by the batch's structure and replayed.  Enqueue only. */
+VL_API vl_status vl_eval_batch(vl_context* ctx, const vl_job* jobs,
+                               int32_t n_jobs, void* stream, vl_result** outs);
+
+/* Prepared batches: the jobs' plans, device tables, scratch and result
+ * buffers are set up once; vl_batch_run replays the whole batch (one
+ * persistent launch, through a cached CUDA graph when the context's
+ * use_graphs is set) on the same images and into the same result buffers.
+ * The images must stay alive as long as the batch.  Results are borrowed:
+ * valid until vl_free(batch), never freed by the caller. */
+typedef struct vl_batch vl_batch;
+VL_API vl_status vl_batch_prepare(vl_context* ctx, const vl_job* jobs, int32_t n_jobs,
+                                  void* stream, vl_batch** out);
+VL_API vl_status vl_batch_run(vl_batch* b, void* stream);
+VL_API vl_status vl_batch_result(vl_batch* b, int32_t job, vl_result** out);
+
+/* Shape of a batch launch: work items, CTAs, dynamic shared memory. */
+VL_API vl_status vl_batch_info(const vl_batch* b, int64_t* n_items, int32_t* grid,
+                               int64_t* smem_bytes);
+
+/* Wait for the result's work and return its device status word: VL_OK,
+ * VL_ERR_TIMEOUT (a bounded device wait ran out) or VL_ERR_INTERNAL. */
+VL_API vl_status vl_result_sync(vl_result* res);
+
+/* Shape of a result (any pointer may be NULL); words_per_row = Wp. */
+VL_API vl_status vl_result_info(const vl_result* res, int32_t* h, int32_t* w,
+                                int32_t* words_per_row, int32_t* n_roots);
+
+/* Copy root `root`'s mask (h * Wp uint32 words) to dst, host or device,
+ * ordered on `stream` (host copies complete before returning). */
+VL_API vl_status vl_result_mask(const vl_result* res, int32_t root,
+                                uint32_t* dst, int32_t dst_on_device,
+                                void* stream);
+
+/* All roots at once: root r goes to dst + r * h * Wp words (host or
+ * device); one host wait at the end for host destinations. */
+VL_API vl_status vl_result_masks(const vl_result* res, uint32_t* dst,
+                                 int32_t dst_on_device, void* stream);
+
+/* Same, unpacked to h * w bytes of 0/1 by a device kernel. */
+VL_API vl_status vl_result_mask_u8(const vl_result* res, int32_t root,
+                                   uint8_t* dst, int32_t dst_on_device,
+                                   void* stream);
+
+/* Device pointer of root `root`'s packed mask (valid until the result is
+ * freed). */
+VL_API vl_status vl_result_device_ptr(const vl_result* res, int32_t root,
+                                      const uint32_t** ptr);
+
+/* ------------------------------------------------- connected components */
+
+/* Full connected component labelling of a mask image (the operation rho
+ * reduces to, Sec. 3.2-3.3): labels_dev receives H*W int32 labels (minimum
+ * linear index per component, -1 background).  labels_dev is a caller-owned
+ * device buffer of at least H*W int32.  Union-find: tile-local labelling in
+ * shared memory, then a global merge with atomics.  Enqueue only; device
+ * errors are reported by vl_ccl_status. */
+VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask,
+                        int32_t connectivity, int32_t* labels_dev,
+                        void* stream);
+
+/* Synchronise `stream` and return the status word of the last vl_ccl call
+ * on this context (VL_OK, VL_ERR_TIMEOUT, VL_ERR_INTERNAL). */
+VL_API vl_status vl_ccl_status(vl_context* ctx, void* stream);
+
+/* ----------------------------------------------------------------- serving */
+
+typedef struct {
+  int32_t max_inflight_batches;  /* launches in flight at once (default 2) */
+  int32_t max_batch_jobs;        /* jobs per launch (default 256) */
+  int64_t memory_budget;         /* bytes; 0 = free HBM minus reserve */
+  int64_t batch_window_us;       /* how long to gather arrivals (default 200) */
+  int32_t reserved[8];
+} vl_server_config;
+
+typedef struct {
+  int64_t submitted, completed, cancelled, failed;
+  int64_t batches;               /* launches issued */
+  int64_t bytes_in_use;          /* device bytes held by admitted queries */
+  int64_t peak_bytes;
+  double p50_ms, p99_ms;         /* submit -> done latency of completed */
+} vl_server_stats;
+
+/* Start a serving loop on its own host thread.  Queries are admitted while
+ * their device memory fits the budget and a batch slot is free; admitted
+ * queries are packed into persistent launches on rotating streams, so new
+ * arrivals run while earlier batches are still on the GPU. */
+VL_API vl_status vl_server_create(vl_context* ctx, const vl_server_config* cfg,
+                                  vl_server** out);
+
+/* Queue a query; returns at once with a ticket.  The images must stay alive
+ * until the query completes. */
+VL_API vl_status vl_server_submit(vl_server* srv, const vl_formula* f,
+                                  vl_image* const* imgs, int32_t n_imgs,
+                                  int64_t* ticket);
+
+/* Wait up to timeout_us (-1 = forever) for a ticket.  On VL_OK *out gets
+ * the query's result (caller frees it); VL_ERR_BUSY if still running;
+ * VL_ERR_CANCELLED if cancelled; other codes for failed queries. */
+VL_API vl_status vl_server_wait(vl_server* srv, int64_t ticket,
+                                int64_t timeout_us, vl_result** out);
+
+/* Cancel a queued query (no effect once it has been launched). */
+VL_API vl_status vl_server_cancel(vl_server* srv, int64_t ticket);
+
+VL_API vl_status vl_server_stats_get(vl_server* srv, vl_server_stats* st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VL_H_ */

@@ -1,0 +1,327 @@
+"""Python front-end of the C ABI (include/vl.h): thin handle classes that
+marshal arguments to the CUDA library.  Host arrays are numpy; device arrays
+are torch CUDA tensors (PyTorch supplies device memory and streams only)."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _native as N
+
+NodeRec = Tuple[str, int, int, int, int, float, float]
+
+
+def _stream_handle(stream) -> int:
+    """cudaStream_t of a torch stream / int / None (= torch's current stream)."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+class _Handle:
+    _ptr: Optional[int] = None
+
+    def _check(self, rc: int, ctx=None):
+        if rc != N.OK:
+            c = ctx if ctx is not None else getattr(self, "ctx", None)
+            msg = N.load().vl_last_error(c._ptr).decode() if c is not None and c._ptr else ""
+            raise N.VlError(rc, msg)
+
+    def close(self):
+        if self._ptr:
+            N.load().vl_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context(_Handle):
+    def __init__(self, device: int = 0, exec_mode: str = "fused", use_graphs: bool = True,
+                 spin_limit: int = 0, tile_rows: int = 0, tile_words: int = 0):
+        lib = N.load()
+        cfg = N.VlConfig()
+        lib.vl_config_default(C.byref(cfg))
+        cfg.device = device
+        cfg.exec_mode = N.EXEC_PLAIN if exec_mode == "plain" else N.EXEC_FUSED
+        cfg.use_graphs = 1 if use_graphs else 0
+        cfg.spin_limit = spin_limit
+        cfg.tile_rows = tile_rows
+        cfg.tile_words = tile_words
+        out = C.c_void_p()
+        rc = lib.vl_context_create(C.byref(cfg), C.byref(out))
+        if rc != N.OK:
+            raise N.VlError(rc, "context creation failed")
+        self._ptr = out.value
+        self.ctx = self
+
+    # ------------------------------------------------------------ images
+    def image(self, data, stream=None) -> "Image":
+        """Float image (C, H, W) from a numpy array (host) or a CUDA tensor."""
+        lib = N.load()
+        out = C.c_void_p()
+        if _is_torch_cuda(data):
+            t = data.contiguous().float()
+            if t.dim() == 2:
+                t = t[None]
+            c, h, w = t.shape
+            rc = lib.vl_image_create(self._ptr, h, w, c, t.data_ptr(), 1, _stream_handle(stream), C.byref(out))
+            keep = t
+        else:
+            a = np.ascontiguousarray(data, dtype=np.float32)
+            if a.ndim == 2:
+                a = a[None]
+            c, h, w = a.shape
+            rc = lib.vl_image_create(self._ptr, h, w, c, a.ctypes.data, 0, _stream_handle(stream), C.byref(out))
+            keep = a
+        self._check(rc)
+        return Image(self, out.value, keep)
+
+    def mask(self, data, stream=None) -> "Image":
+        """Binary image (H, W) from bytes/bools (numpy host or CUDA uint8 tensor)."""
+        lib = N.load()
+        out = C.c_void_p()
+        if _is_torch_cuda(data):
+            import torch
+            t = data.contiguous().to(torch.uint8)
+            h, w = t.shape
+            rc = lib.vl_mask_create(self._ptr, h, w, t.data_ptr(), 1, _stream_handle(stream), C.byref(out))
+            keep = t
+        else:
+            a = np.ascontiguousarray(np.asarray(data) != 0, dtype=np.uint8)
+            h, w = a.shape
+            rc = lib.vl_mask_create(self._ptr, h, w, a.ctypes.data, 0, _stream_handle(stream), C.byref(out))
+            keep = a
+        self._check(rc)
+        return Image(self, out.value, keep)
+
+    def mask_packed(self, words, h: int, w: int, stream=None) -> "Image":
+        lib = N.load()
+        out = C.c_void_p()
+        if _is_torch_cuda(words):
+            t = words.contiguous()
+            rc = lib.vl_mask_create_packed(self._ptr, h, w, t.data_ptr(), 1, _stream_handle(stream), C.byref(out))
+            keep = t
+        else:
+            a = np.ascontiguousarray(words, dtype=np.uint32)
+            rc = lib.vl_mask_create_packed(self._ptr, h, w, a.ctypes.data, 0, _stream_handle(stream), C.byref(out))
+            keep = a
+        self._check(rc)
+        return Image(self, out.value, keep)
+
+    # ---------------------------------------------------------- formulas
+    def compile(self, nodes: Sequence, roots: Sequence[int], conn: int = 8) -> "Formula":
+        lib = N.load()
+        arr = (N.VlNode * max(1, len(nodes)))()
+        for i, nd in enumerate(nodes):
+            op, a, b, img, ch, t, q = tuple(nd)
+            arr[i] = N.VlNode(N.OPCODES[op] if isinstance(op, str) else int(op), int(a), int(b),
+                              int(img), int(ch), float(np.float32(t)), float(q))
+        rts = (C.c_int32 * max(1, len(roots)))(*[int(r) for r in roots])
+        out = C.c_void_p()
+        rc = lib.vl_formula_compile(self._ptr, arr, len(nodes), rts, len(roots), conn, C.byref(out))
+        self._check(rc)
+        return Formula(self, out.value)
+
+    # -------------------------------------------------------- evaluation
+    def eval(self, formula: "Formula", images: Sequence["Image"], stream=None,
+             mode: Optional[str] = None) -> "Result":
+        lib = N.load()
+        arr = (C.c_void_p * len(images))(*[im._ptr for im in images])
+        out = C.c_void_p()
+        if mode is None:
+            rc = lib.vl_eval(self._ptr, formula._ptr, arr, len(images), _stream_handle(stream), C.byref(out))
+        else:
+            m = N.EXEC_PLAIN if mode == "plain" else N.EXEC_FUSED
+            rc = lib.vl_eval_mode(self._ptr, formula._ptr, arr, len(images), m,
+                                  _stream_handle(stream), C.byref(out))
+        self._check(rc)
+        return Result(self, out.value, keep=(formula, list(images)))
+
+    def _jobs(self, jobs):
+        arrs = []
+        cj = (N.VlJob * len(jobs))()
+        for k, (f, ims) in enumerate(jobs):
+            a = (C.c_void_p * len(ims))(*[im._ptr for im in ims])
+            arrs.append(a)
+            cj[k] = N.VlJob(f._ptr, C.cast(a, C.POINTER(C.c_void_p)), len(ims), 0)
+        return cj, arrs
+
+    def eval_batch(self, jobs: Sequence[Tuple["Formula", Sequence["Image"]]], stream=None) -> List["Result"]:
+        lib = N.load()
+        cj, arrs = self._jobs(jobs)
+        outs = (C.c_void_p * len(jobs))()
+        rc = lib.vl_eval_batch(self._ptr, cj, len(jobs), _stream_handle(stream), outs)
+        self._check(rc)
+        return [Result(self, outs[k], keep=jobs[k]) for k in range(len(jobs))]
+
+    def batch(self, jobs: Sequence[Tuple["Formula", Sequence["Image"]]], stream=None) -> "Batch":
+        lib = N.load()
+        cj, arrs = self._jobs(jobs)
+        out = C.c_void_p()
+        rc = lib.vl_batch_prepare(self._ptr, cj, len(jobs), _stream_handle(stream), C.byref(out))
+        self._check(rc)
+        return Batch(self, out.value, len(jobs), keep=list(jobs))
+
+    # --------------------------------------------------------------- ccl
+    def ccl(self, mask: "Image", labels, conn: int = 8, stream=None) -> None:
+        """Labels into a caller-owned int32 CUDA tensor of H*W elements."""
+        rc = N.load().vl_ccl(self._ptr, mask._ptr, conn, labels.data_ptr(), _stream_handle(stream))
+        self._check(rc)
+
+    def ccl_status(self, stream=None) -> int:
+        return N.load().vl_ccl_status(self._ptr, _stream_handle(stream))
+
+    def last_error(self) -> str:
+        return N.load().vl_last_error(self._ptr).decode()
+
+    def close(self):
+        super().close()
+
+
+class Image(_Handle):
+    def __init__(self, ctx: Context, ptr: int, keep=None):
+        self.ctx, self._ptr, self._keep = ctx, ptr, keep
+        h, w, c, m = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        N.load().vl_image_info(ptr, C.byref(h), C.byref(w), C.byref(c), C.byref(m))
+        self.h, self.w, self.channels, self.is_mask = h.value, w.value, c.value, bool(m.value)
+
+    def release_source(self):
+        """Drop the reference to the source array once the stream has copied it."""
+        self._keep = None
+
+
+def compile_formula(nodes: Sequence, roots: Sequence[int], conn: int = 8) -> "Formula":
+    """Compile without a context (host only): the plan targets the default
+    tile configuration."""
+    lib = N.load()
+    arr = (N.VlNode * max(1, len(nodes)))()
+    for i, nd in enumerate(nodes):
+        op, a, b, img, ch, t, q = tuple(nd)
+        arr[i] = N.VlNode(N.OPCODES[op] if isinstance(op, str) else int(op), int(a), int(b),
+                          int(img), int(ch), float(np.float32(t)), float(q))
+    rts = (C.c_int32 * max(1, len(roots)))(*[int(r) for r in roots])
+    out = C.c_void_p()
+    rc = lib.vl_formula_compile(None, arr, len(nodes), rts, len(roots), conn, C.byref(out))
+    if rc != N.OK:
+        raise N.VlError(rc, "formula compilation failed")
+    return Formula(None, out.value)
+
+
+class Formula(_Handle):
+    def __init__(self, ctx: Optional[Context], ptr: int):
+        self.ctx, self._ptr = ctx, ptr
+
+    def plan(self) -> dict:
+        """The compiled execution plan (steps, instructions, selects, slots)."""
+        lib = N.load()
+        sz = N.VlPlanSizes()
+        self._check(lib.vl_formula_plan(self._ptr, C.byref(sz), None, None, None, None, None, None))
+        steps = (N.VlPlanStep * max(1, sz.n_steps))()
+        insns = (N.VlPlanInsn * max(1, sz.n_insns))()
+        sels = (N.VlPlanSelect * max(1, sz.n_selects))()
+        pct = (N.VlPlanPct * max(1, sz.n_pct))()
+        roots = (C.c_int32 * max(1, sz.n_roots))()
+        masks = (C.c_int32 * max(1, sz.n_mask_slots))()
+        self._check(lib.vl_formula_plan(self._ptr, C.byref(sz), steps, insns, sels, pct, roots, masks))
+        rec = lambda x: {f: getattr(x, f) for f, _ in x._fields_}
+        return {
+            "sizes": rec(sz),
+            "steps": [rec(steps[i]) for i in range(sz.n_steps)],
+            "insns": [rec(insns[i]) for i in range(sz.n_insns)],
+            "selects": [rec(sels[i]) for i in range(sz.n_selects)],
+            "pct": [rec(pct[i]) for i in range(sz.n_pct)],
+            "root_slots": [roots[i] for i in range(sz.n_roots)],
+            "mask_slot_images": [masks[i] for i in range(sz.n_mask_slots)],
+        }
+
+    def info(self) -> dict:
+        s = N.VlFormulaStats()
+        self._check(N.load().vl_formula_stats_get(self._ptr, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in N.VlFormulaStats._fields_ if f != "reserved"}
+
+    @property
+    def n_primitive(self) -> int:
+        return self.info()["n_primitive"]
+
+
+class Result(_Handle):
+    def __init__(self, ctx: Context, ptr: int, keep=None, borrowed: bool = False):
+        self.ctx, self._ptr, self._keep, self._borrowed = ctx, ptr, keep, borrowed
+        h, w, wp, nr = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        N.load().vl_result_info(ptr, C.byref(h), C.byref(w), C.byref(wp), C.byref(nr))
+        self.h, self.w, self.wp, self.n_roots = h.value, w.value, wp.value, nr.value
+
+    def sync(self) -> int:
+        """Wait; returns the device status (0 ok) without raising."""
+        return N.load().vl_result_sync(self._ptr)
+
+    def check(self) -> None:
+        self._check(self.sync())
+
+    def mask(self, root: int = 0, stream=None) -> np.ndarray:
+        """Root mask as (H, W) uint8 on the host (unpacked by a device kernel)."""
+        out = np.empty((self.h, self.w), dtype=np.uint8)
+        self._check(N.load().vl_result_mask_u8(self._ptr, root, out.ctypes.data, 0, _stream_handle(stream)))
+        return out
+
+    def mask_packed(self, root: int = 0, stream=None) -> np.ndarray:
+        out = np.empty((self.h, self.wp), dtype=np.uint32)
+        self._check(N.load().vl_result_mask(self._ptr, root, out.ctypes.data, 0, _stream_handle(stream)))
+        return out
+
+    def mask_into(self, root: int, dst, on_device: bool, stream=None) -> None:
+        ptr = dst.data_ptr() if on_device else dst.ctypes.data
+        self._check(N.load().vl_result_mask(self._ptr, root, ptr, 1 if on_device else 0,
+                                            _stream_handle(stream)))
+
+    def masks_into(self, dst, on_device: bool, stream=None) -> None:
+        """All roots, packed, back to back (n_roots x H x Wp uint32)."""
+        ptr = dst.data_ptr() if on_device else dst.ctypes.data
+        self._check(N.load().vl_result_masks(self._ptr, ptr, 1 if on_device else 0,
+                                             _stream_handle(stream)))
+
+    def device_ptr(self, root: int = 0) -> int:
+        p = C.c_void_p()
+        self._check(N.load().vl_result_device_ptr(self._ptr, root, C.byref(p)))
+        return p.value
+
+    def close(self):
+        if not self._borrowed:
+            super().close()
+        self._ptr = None
+
+
+class Batch(_Handle):
+    def __init__(self, ctx: Context, ptr: int, n_jobs: int, keep=None):
+        self.ctx, self._ptr, self.n_jobs, self._keep = ctx, ptr, n_jobs, keep
+
+    def run(self, stream=None) -> None:
+        self._check(N.load().vl_batch_run(self._ptr, _stream_handle(stream)))
+
+    def result(self, job: int) -> Result:
+        p = C.c_void_p()
+        self._check(N.load().vl_batch_result(self._ptr, job, C.byref(p)))
+        return Result(self.ctx, p.value, borrowed=True)
+
+    def info(self) -> dict:
+        n, g, s = C.c_int64(), C.c_int32(), C.c_int64()
+        self._check(N.load().vl_batch_info(self._ptr, C.byref(n), C.byref(g), C.byref(s)))
+        return {"n_items": n.value, "grid": g.value, "smem_bytes": s.value}

@@ -1,0 +1,1019 @@
+// C ABI of the library: contexts, images, formulas, evaluation, results,
+// connected components.  See include/vl.h for the contract of each call.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "runtime.h"
+
+using namespace vl;
+
+namespace vl {
+
+DevBlock::~DevBlock() {
+  if (!ptr) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != device) cudaSetDevice(device);
+  cudaFreeAsync(ptr, stream);
+  if (cur != device && cur >= 0) cudaSetDevice(cur);
+}
+
+vl_status set_err(vl_context* ctx, vl_status code, const std::string& msg) {
+  if (ctx) {
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    ctx->err = msg;
+  }
+  return code;
+}
+
+vl_status cuda_err(vl_context* ctx, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear the sticky-free error state of the runtime
+  return set_err(ctx, e == cudaErrorMemoryAllocation ? VL_ERR_OOM : VL_ERR_CUDA, m);
+}
+
+cudaError_t dev_alloc(vl_context* ctx, size_t bytes, cudaStream_t st, DevBlockPtr* out) {
+  auto b = std::make_shared<DevBlock>();
+  b->bytes = bytes;
+  b->stream = st;
+  b->device = ctx->device;
+  if (bytes) {
+    cudaError_t e = cudaMallocAsync(&b->ptr, bytes, st);
+    if (e != cudaSuccess) {
+      b->ptr = nullptr;
+      return e;
+    }
+  }
+  *out = std::move(b);
+  return cudaSuccess;
+}
+
+}  // namespace vl
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool valid(const void* h, uint32_t tag) {
+  return h && *reinterpret_cast<const uint32_t*>(h) == tag;
+}
+
+// Check the images of a job against a plan; returns shape in H, W.
+vl_status check_job_images(vl_context* ctx, const Plan& P, vl_image* const* imgs, int n_imgs,
+                           int* H, int* W) {
+  if (n_imgs < (int)P.img_kind.size())
+    return set_err(ctx, VL_ERR_ARG, "formula reads image " + std::to_string(P.img_kind.size() - 1) +
+                                        " but only " + std::to_string(n_imgs) + " were given");
+  if (n_imgs < 1 || !imgs) return set_err(ctx, VL_ERR_ARG, "at least one image is needed");
+  int h = -1, w = -1;
+  for (int i = 0; i < n_imgs; ++i) {
+    const vl_image* im = imgs[i];
+    if (!valid(im, TAG_IMG)) return set_err(ctx, VL_ERR_ARG, "bad image handle " + std::to_string(i));
+    if (h < 0) { h = im->H; w = im->W; }
+    if (im->H != h || im->W != w)
+      return set_err(ctx, VL_ERR_SHAPE, "images of one evaluation must share H x W");
+    if (i < (int)P.img_kind.size()) {
+      if (P.img_kind[i] == 1 && (im->is_mask || im->C < P.img_channels[i]))
+        return set_err(ctx, VL_ERR_SHAPE, "image " + std::to_string(i) +
+                                              " must be a float image with enough channels");
+      if (P.img_kind[i] == 2 && !im->is_mask)
+        return set_err(ctx, VL_ERR_SHAPE, "image " + std::to_string(i) + " must be a mask");
+    }
+  }
+  *H = h;
+  *W = w;
+  return VL_OK;
+}
+
+int ccl_merge_chunks(int H, int Wp) {
+  const long long n = (long long)(ccl_tiles_y(H) - 1) * Wp + (long long)(ccl_tiles_x(Wp) - 1) * H;
+  return (int)std::max<long long>(1, (n + EXEC_THREADS - 1) / EXEC_THREADS);
+}
+int ccl_flag_chunks(int H, int Wp) {
+  return std::max(1, std::min(64, ccl_tiles_y(H) * ccl_tiles_x(Wp) / 4));
+}
+
+}  // namespace
+
+// ================================================================ batch ==
+
+struct vl_batch {
+  uint32_t tag = TAG_BAT;
+  vl_context* ctx = nullptr;
+  int n_jobs = 0;
+  DevBlockPtr persist;  // root buffers + status words (kept by results)
+  DevBlockPtr trans;    // tables, counters, slots, scratch
+  size_t counters_off = 0, counters_bytes = 0;
+  int32_t* status_base = nullptr;
+  int n_status = 0;
+  ExecLaunch L{};
+  std::vector<vl_result*> results;
+  bool released = false;
+  std::shared_ptr<EventHolder> done;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int64_t bytes = 0;
+};
+
+namespace vl {
+
+int64_t batch_bytes(const vl_batch* b) { return b ? b->bytes : 0; }
+
+vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStream_t st,
+                      vl_batch** out) {
+  if (n_jobs < 1 || !jobs) return set_err(ctx, VL_ERR_ARG, "empty batch");
+  struct JobInfo {
+    const Plan* P;
+    int H, W, Wp, pitch;
+    int gty, gtx, cty, ctx_, ctiles;
+    std::vector<int> need;
+    size_t off_images, off_slotptrs, off_pct, off_slots, off_scratch[MAX_RZ_BATCH * 3];
+    size_t off_roots, off_status, off_fcount;
+    int step_base, fcount_base;
+    int flist_cap;
+    int formula_idx;
+  };
+  std::vector<JobInfo> J(n_jobs);
+  std::map<const Plan*, int> formula_index;
+  std::vector<const Plan*> formulas;
+  for (int j = 0; j < n_jobs; ++j) {
+    const vl_formula* f = jobs[j].formula;
+    if (!valid(f, TAG_FML)) return set_err(ctx, VL_ERR_ARG, "bad formula handle in job " + std::to_string(j));
+    if (f->pp.group_buffers != ctx->pp.group_buffers || f->pp.hmax != ctx->pp.hmax)
+      return set_err(ctx, VL_ERR_ARG, "formula was planned for another tile configuration");
+    vl_status s = check_job_images(ctx, f->plan, jobs[j].images, jobs[j].n_images, &J[j].H, &J[j].W);
+    if (s != VL_OK) return s;
+    J[j].P = &f->plan;
+    if (!formula_index.count(&f->plan)) {
+      formula_index[&f->plan] = (int)formulas.size();
+      formulas.push_back(&f->plan);
+    }
+    J[j].formula_idx = formula_index[&f->plan];
+  }
+  // ---- layout of the transient block
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t a = 256) { off = align_up(off, a); size_t o = off; off += bytes; return o; };
+  const size_t off_jobs = take(sizeof(DevJob) * n_jobs);
+  std::vector<size_t> f_steps(formulas.size()), f_insns(formulas.size()), f_rz(formulas.size()),
+      f_pct(formulas.size());
+  for (size_t k = 0; k < formulas.size(); ++k) {
+    const Plan* P = formulas[k];
+    f_steps[k] = take(sizeof(StepDesc) * std::max<size_t>(1, P->steps.size()));
+    f_insns[k] = take(sizeof(Insn) * std::max<size_t>(1, P->insns.size()));
+    f_rz[k] = take(sizeof(RzDesc) * std::max<size_t>(1, P->rz.size()));
+    f_pct[k] = take(sizeof(PctDesc) * std::max<size_t>(1, P->pct.size()));
+  }
+  int total_steps = 0, total_rz = 0;
+  std::vector<WorkItem> items;
+  const int grid = std::max(1, ctx->sm_count * ctx->ctas_per_sm);
+  for (int j = 0; j < n_jobs; ++j) {
+    JobInfo& I = J[j];
+    const Plan& P = *I.P;
+    I.Wp = words_per_row(I.W);
+    I.pitch = 32 * I.Wp;
+    I.gty = (I.H + ctx->gth - 1) / ctx->gth;
+    I.gtx = (I.Wp + ctx->gtww - 1) / ctx->gtww;
+    I.cty = ccl_tiles_y(I.H);
+    I.ctx_ = ccl_tiles_x(I.Wp);
+    I.ctiles = I.cty * I.ctx_;
+    I.flist_cap = ccl_flist_cap(I.H, I.Wp);
+    I.step_base = total_steps;
+    I.fcount_base = total_rz;
+    total_steps += (int)P.steps.size();
+    total_rz += (int)P.rz.size();
+    for (const StepDesc& s : P.steps) {
+      int n = 1;
+      switch (s.kind) {
+        case SK_PCT: n = s.pct_cnt; break;
+        case SK_GROUP: n = I.gty * I.gtx; break;
+        case SK_RZ_LOCAL: case SK_RZ_FINAL: n = s.rz_cnt * I.ctiles; break;
+        case SK_RZ_MERGE: n = s.rz_cnt * ccl_merge_chunks(I.H, I.Wp); break;
+        case SK_RZ_FLAGS: n = s.rz_cnt * ccl_flag_chunks(I.H, I.Wp); break;
+      }
+      I.need.push_back(std::max(1, n));
+    }
+    I.off_images = take(sizeof(DevImage) * jobs[j].n_images);
+    I.off_slotptrs = take(sizeof(uint32_t*) * std::max(1, P.n_inter_slots + P.n_root_slots + P.n_mask_slots));
+  }
+  // work items: step-major across jobs so that dependencies come first
+  int max_steps = 0;
+  for (auto& I : J) max_steps = std::max(max_steps, (int)I.need.size());
+  for (int s = 0; s < max_steps; ++s)
+    for (int j = 0; j < n_jobs; ++j) {
+      if (s >= (int)J[j].need.size()) continue;
+      const int n = J[j].need[s];
+      int chunk = 1;
+      if ((long long)n_jobs * 2 >= grid) chunk = n;
+      else chunk = std::max(1, (int)((long long)n * n_jobs / (2LL * grid)));
+      for (int first = 0; first < n; first += chunk)
+        items.push_back(WorkItem{j, s, first, std::min(chunk, n - first)});
+    }
+  const size_t off_items = take(sizeof(WorkItem) * std::max<size_t>(1, items.size()));
+  const size_t off_need = take(sizeof(int32_t) * std::max(1, total_steps));
+  // counters: head, done[steps], fcount[rz] -- zeroed before every run
+  const size_t off_counters = take(sizeof(int32_t) * (1 + total_steps + std::max(1, total_rz)));
+  const size_t counters_bytes = sizeof(int32_t) * (1 + total_steps + std::max(1, total_rz));
+  const size_t tables_end = off;
+  // buffers
+  for (int j = 0; j < n_jobs; ++j) {
+    JobInfo& I = J[j];
+    const Plan& P = *I.P;
+    const size_t mask_bytes = (size_t)I.H * I.Wp * 4;
+    const size_t P_px = (size_t)I.H * I.W;
+    I.off_pct = take(sizeof(float) * std::max(1, P.n_pct_slots));
+    I.off_slots = take(mask_bytes * P.n_inter_slots);
+    for (int k = 0; k < P.max_rz_batch; ++k) {
+      I.off_scratch[3 * k + 0] = take(P_px * 4);
+      I.off_scratch[3 * k + 1] = take(P_px);
+      I.off_scratch[3 * k + 2] = take((size_t)I.flist_cap * 4);
+    }
+  }
+  const size_t trans_bytes = align_up(off, 256);
+  // persistent block: root buffers and status words
+  size_t poff = 0;
+  auto ptake = [&](size_t bytes) { poff = align_up(poff, 256); size_t o = poff; poff += bytes; return o; };
+  const size_t off_status = ptake(sizeof(int32_t) * n_jobs);
+  for (int j = 0; j < n_jobs; ++j) {
+    JobInfo& I = J[j];
+    I.off_roots = ptake((size_t)I.H * I.Wp * 4 * I.P->n_root_slots);
+  }
+  auto b = std::make_unique<vl_batch>();
+  b->ctx = ctx;
+  b->n_jobs = n_jobs;
+  cudaError_t e = dev_alloc(ctx, trans_bytes, st, &b->trans);
+  if (e) return cuda_err(ctx, e, "allocating batch tables and scratch");
+  e = dev_alloc(ctx, align_up(poff, 256), st, &b->persist);
+  if (e) return cuda_err(ctx, e, "allocating result buffers");
+  b->bytes = (int64_t)(trans_bytes + poff);
+  char* tb = static_cast<char*>(b->trans->ptr);
+  char* pb = static_cast<char*>(b->persist->ptr);
+  // ---- host copy of the tables
+  std::vector<char> host(tables_end, 0);
+  for (size_t k = 0; k < formulas.size(); ++k) {
+    const Plan* P = formulas[k];
+    if (!P->steps.empty()) std::memcpy(&host[f_steps[k]], P->steps.data(), sizeof(StepDesc) * P->steps.size());
+    if (!P->insns.empty()) std::memcpy(&host[f_insns[k]], P->insns.data(), sizeof(Insn) * P->insns.size());
+    if (!P->rz.empty()) std::memcpy(&host[f_rz[k]], P->rz.data(), sizeof(RzDesc) * P->rz.size());
+    if (!P->pct.empty()) std::memcpy(&host[f_pct[k]], P->pct.data(), sizeof(PctDesc) * P->pct.size());
+  }
+  DevJob* hj = reinterpret_cast<DevJob*>(&host[off_jobs]);
+  int32_t* hneed = reinterpret_cast<int32_t*>(&host[off_need]);
+  int32_t* counters_dev = reinterpret_cast<int32_t*>(tb + off_counters);
+  int32_t* status_dev = reinterpret_cast<int32_t*>(pb + off_status);
+  for (int j = 0; j < n_jobs; ++j) {
+    JobInfo& I = J[j];
+    const Plan& P = *I.P;
+    DevJob d{};
+    d.H = I.H; d.W = I.W; d.Wp = I.Wp; d.pitch = I.pitch;
+    d.n_steps = (int)P.steps.size();
+    d.step_base = I.step_base;
+    d.gth = ctx->gth; d.gtww = ctx->gtww;
+    d.g_tiles_y = I.gty; d.g_tiles_x = I.gtx;
+    d.c_tiles_y = I.cty; d.c_tiles_x = I.ctx_;
+    d.conn = P.conn;
+    d.n_images = jobs[j].n_images;
+    DevImage* him = reinterpret_cast<DevImage*>(&host[I.off_images]);
+    for (int i = 0; i < jobs[j].n_images; ++i) {
+      const vl_image* im = jobs[j].images[i];
+      him[i] = DevImage{im->data, im->mask, im->C, im->is_mask};
+    }
+    d.images = reinterpret_cast<const DevImage*>(tb + I.off_images);
+    uint32_t** hs = reinterpret_cast<uint32_t**>(&host[I.off_slotptrs]);
+    const size_t mask_bytes = (size_t)I.H * I.Wp * 4;
+    for (int s = 0; s < P.n_inter_slots; ++s)
+      hs[s] = reinterpret_cast<uint32_t*>(tb + I.off_slots + mask_bytes * s);
+    for (int s = 0; s < P.n_root_slots; ++s)
+      hs[P.n_inter_slots + s] = reinterpret_cast<uint32_t*>(pb + I.off_roots + mask_bytes * s);
+    for (int s = 0; s < P.n_mask_slots; ++s)
+      hs[P.n_inter_slots + P.n_root_slots + s] = jobs[j].images[P.mask_slot_image[s]]->mask;
+    d.slots = reinterpret_cast<uint32_t* const*>(tb + I.off_slotptrs);
+    const int k = I.formula_idx;
+    d.insns = reinterpret_cast<const Insn*>(tb + f_insns[k]);
+    d.steps = reinterpret_cast<const StepDesc*>(tb + f_steps[k]);
+    d.rz = reinterpret_cast<const RzDesc*>(tb + f_rz[k]);
+    d.pct = reinterpret_cast<const PctDesc*>(tb + f_pct[k]);
+    d.pct_val = reinterpret_cast<float*>(tb + I.off_pct);
+    for (int s = 0; s < P.max_rz_batch; ++s) {
+      d.G[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[3 * s + 0]);
+      d.F[s] = reinterpret_cast<uint8_t*>(tb + I.off_scratch[3 * s + 1]);
+      d.flist[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[3 * s + 2]);
+    }
+    d.fcount = counters_dev + 1 + total_steps + I.fcount_base;
+    d.flist_cap = I.flist_cap;
+    d.status = status_dev + j;
+    hj[j] = d;
+    for (size_t s = 0; s < I.need.size(); ++s) hneed[I.step_base + s] = I.need[s];
+  }
+  // items with job-relative steps
+  if (!items.empty()) std::memcpy(&host[off_items], items.data(), sizeof(WorkItem) * items.size());
+  e = cudaMemcpyAsync(tb, host.data(), tables_end, cudaMemcpyHostToDevice, st);
+  if (e) return cuda_err(ctx, e, "uploading batch tables");
+  // ---- launch description
+  b->counters_off = off_counters;
+  b->counters_bytes = counters_bytes;
+  b->status_base = status_dev;
+  b->n_status = n_jobs;
+  ExecLaunch& L = b->L;
+  L.jobs = reinterpret_cast<const DevJob*>(tb + off_jobs);
+  L.items = reinterpret_cast<const WorkItem*>(tb + off_items);
+  L.n_items = (int32_t)items.size();
+  L.head = counters_dev;
+  L.done = counters_dev + 1;
+  L.need = reinterpret_cast<const int32_t*>(tb + off_need);
+  L.spin_limit = ctx->cfg.spin_limit != 0 ? ctx->cfg.spin_limit : (1LL << 22);
+  L.group_buffers = ctx->nb;
+  L.group_bh = ctx->gth + 2 * ctx->hmax;
+  L.group_bw = ctx->gtww + 2;
+  L.grid = std::max(1, std::min<int>(grid, (int)items.size()));
+  // ---- results
+  b->done = std::make_shared<EventHolder>();
+  e = cudaEventCreateWithFlags(&b->done->ev, cudaEventDisableTiming);
+  if (e) return cuda_err(ctx, e, "creating an event");
+  for (int j = 0; j < n_jobs; ++j) {
+    JobInfo& I = J[j];
+    const Plan& P = *I.P;
+    auto* r = new vl_result();
+    r->ctx = ctx;
+    r->H = I.H; r->W = I.W; r->Wp = I.Wp;
+    r->n_roots = P.n_roots;
+    const size_t mask_bytes = (size_t)I.H * I.Wp * 4;
+    for (int q = 0; q < P.n_roots; ++q)
+      r->roots.push_back(reinterpret_cast<uint32_t*>(pb + I.off_roots +
+                                                     mask_bytes * (P.root_slot[q] - P.n_inter_slots)));
+    r->status = status_dev + j;
+    r->stream = st;
+    r->done = b->done;
+    r->borrowed = true;
+    r->keep.push_back(b->persist);
+    b->results.push_back(r);
+  }
+  *out = b.release();
+  return VL_OK;
+}
+
+vl_status batch_run(vl_batch* b, cudaStream_t st) {
+  vl_context* ctx = b->ctx;
+  cudaError_t e;
+  char* tb = static_cast<char*>(b->trans->ptr);
+  const bool graphs = ctx->cfg.use_graphs && st != nullptr && st != cudaStreamLegacy &&
+                      st != cudaStreamPerThread;
+  if (graphs && !b->gexec) {
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e) return cuda_err(ctx, e, "beginning graph capture");
+    cudaError_t e1 = cudaMemsetAsync(tb + b->counters_off, 0, b->counters_bytes, st);
+    cudaError_t e2 = cudaMemsetAsync(b->status_base, 0, sizeof(int32_t) * b->n_status, st);
+    cudaError_t e3 = launch_exec(b->L, st);
+    e = cudaStreamEndCapture(st, &b->graph);
+    if (e1 || e2 || e3 || e) {
+      if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+      return cuda_err(ctx, e1 ? e1 : e2 ? e2 : e3 ? e3 : e, "capturing the executor graph");
+    }
+    e = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+    if (e) return cuda_err(ctx, e, "instantiating the executor graph");
+  }
+  if (b->gexec) {
+    e = cudaGraphLaunch(b->gexec, st);
+    if (e) return cuda_err(ctx, e, "launching the executor graph");
+  } else {
+    if ((e = cudaMemsetAsync(tb + b->counters_off, 0, b->counters_bytes, st)))
+      return cuda_err(ctx, e, "zeroing counters");
+    if ((e = cudaMemsetAsync(b->status_base, 0, sizeof(int32_t) * b->n_status, st)))
+      return cuda_err(ctx, e, "zeroing status words");
+    if ((e = launch_exec(b->L, st))) return cuda_err(ctx, e, "launching the executor");
+  }
+  if ((e = cudaEventRecord(b->done->ev, st))) return cuda_err(ctx, e, "recording an event");
+  for (vl_result* r : b->results) r->stream = st;
+  return VL_OK;
+}
+
+vl_status batch_release_results(vl_batch* b, vl_result** outs) {
+  for (size_t j = 0; j < b->results.size(); ++j) {
+    vl_result* r = b->results[j];
+    r->borrowed = false;
+    outs[j] = r;
+  }
+  b->results.clear();
+  b->released = true;
+  return VL_OK;
+}
+
+void batch_destroy(vl_batch* b) {
+  if (!b) return;
+  for (vl_result* r : b->results) {
+    r->tag = TAG_DEAD;
+    delete r;
+  }
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->tag = TAG_DEAD;
+  delete b;
+}
+
+}  // namespace vl
+
+// ========================================================== plain form ==
+
+namespace {
+
+vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs, int n_imgs,
+                     cudaStream_t st, vl_result** out) {
+  const Plan& P = f->plan;
+  int H, W;
+  vl_status s = check_job_images(ctx, P, imgs, n_imgs, &H, &W);
+  if (s != VL_OK) return s;
+  const int Wp = words_per_row(W), pitch = 32 * Wp;
+  const MaskGeom g{H, W, Wp};
+  const size_t mask_bytes = (size_t)H * Wp * 4;
+  cudaError_t e;
+  DevBlockPtr persist;
+  if ((e = dev_alloc(ctx, align_up(sizeof(int32_t), 256) + mask_bytes * P.n_root_slots, st, &persist)))
+    return cuda_err(ctx, e, "allocating results");
+  char* pb = static_cast<char*>(persist->ptr);
+  int32_t* status = reinterpret_cast<int32_t*>(pb);
+  auto root_buf = [&](int slot) {
+    return reinterpret_cast<uint32_t*>(pb + 256 + mask_bytes * (slot - P.n_inter_slots));
+  };
+  if ((e = cudaMemsetAsync(status, 0, sizeof(int32_t), st))) return cuda_err(ctx, e, "zeroing status");
+  // percentiles
+  DevBlockPtr pct;
+  if (P.n_pct_slots) {
+    if ((e = dev_alloc(ctx, sizeof(float) * P.n_pct_slots, st, &pct))) return cuda_err(ctx, e, "allocating percentiles");
+    for (const PctDesc& d : P.pct) {
+      const long long n = (long long)H * W;
+      const long long rank = (long long)(d.q * (double)(n - 1));
+      const float* plane = imgs[d.img]->data + (size_t)d.ch * H * pitch;
+      if ((e = launch_select(plane, pitch, H, W, rank, static_cast<float*>(pct->ptr) + d.slot, st)))
+        return cuda_err(ctx, e, "launching a percentile select");
+    }
+  }
+  // rho scratch
+  DevBlockPtr scratch;
+  CclScratch sc{};
+  if (!P.rz.empty()) {
+    const size_t px = (size_t)H * W;
+    const int cap = ccl_flist_cap(H, Wp);
+    const size_t bytes = align_up(px * 4, 256) + align_up(px, 256) + align_up((size_t)cap * 4, 256) + 256;
+    if ((e = dev_alloc(ctx, bytes, st, &scratch))) return cuda_err(ctx, e, "allocating select scratch");
+    char* p = static_cast<char*>(scratch->ptr);
+    sc.G = reinterpret_cast<int32_t*>(p);
+    sc.F = reinterpret_cast<uint8_t*>(p + align_up(px * 4, 256));
+    sc.flist = reinterpret_cast<int32_t*>(p + align_up(px * 4, 256) + align_up(px, 256));
+    sc.fcount = reinterpret_cast<int32_t*>(p + align_up(px * 4, 256) + align_up(px, 256) +
+                                           align_up((size_t)cap * 4, 256));
+    sc.flist_cap = cap;
+  }
+  const int N = (int)P.exec.size();
+  std::vector<int> uses(N, 0), root_slot(N, -1);
+  for (int i = 0; i < N; ++i) {
+    const ENode& x = P.exec[i];
+    if (x.a >= 0 && (x.op == E_NOT || x.op == E_NEAR || x.op == E_COPY || x.op == E_AND ||
+                     x.op == E_OR || x.op == E_ANDNOT || x.op == E_RZ)) uses[x.a]++;
+    if (x.b >= 0 && (x.op == E_AND || x.op == E_OR || x.op == E_ANDNOT || x.op == E_RZ)) uses[x.b]++;
+  }
+  for (int q = 0; q < P.n_roots; ++q) root_slot[P.exec_roots[q]] = P.root_slot[q];
+  std::vector<uint32_t*> val(N, nullptr);
+  std::vector<DevBlockPtr> own(N);
+  for (int i = 0; i < N; ++i) {
+    const ENode& x = P.exec[i];
+    if (x.op == E_MASK) { val[i] = imgs[x.img]->mask; continue; }
+    if (root_slot[i] >= 0) {
+      val[i] = root_buf(root_slot[i]);
+    } else {
+      if ((e = dev_alloc(ctx, mask_bytes, st, &own[i]))) return cuda_err(ctx, e, "allocating a mask");
+      val[i] = static_cast<uint32_t*>(own[i]->ptr);
+    }
+    uint32_t* o = val[i];
+    switch (x.op) {
+      case E_TRUE: e = launch_const(g, true, o, st); break;
+      case E_FALSE: e = launch_const(g, false, o, st); break;
+      case E_THR: e = launch_threshold(imgs[x.img]->data + (size_t)x.ch * H * pitch, pitch, g, x.t,
+                                       nullptr, x.lt, o, st); break;
+      case E_PCT: e = launch_threshold(imgs[x.img]->data + (size_t)x.ch * H * pitch, pitch, g, 0.f,
+                                       static_cast<float*>(pct->ptr) + x.pct_slot, x.lt, o, st); break;
+      case E_NOT: e = launch_not(val[x.a], g, o, st); break;
+      case E_AND: e = launch_and(val[x.a], val[x.b], g, o, st); break;
+      case E_OR: e = launch_or(val[x.a], val[x.b], g, o, st); break;
+      case E_ANDNOT: e = launch_andnot(val[x.a], val[x.b], g, o, st); break;
+      case E_NEAR: e = launch_near(val[x.a], g, P.conn, o, st); break;
+      case E_COPY: e = cudaMemcpyAsync(o, val[x.a], mask_bytes, cudaMemcpyDeviceToDevice, st); break;
+      case E_RZ: e = launch_rz(val[x.a], val[x.b], g, P.conn, sc, o, status, st); break;
+      default: return set_err(ctx, VL_ERR_INTERNAL, "plain form: unknown node");
+    }
+    if (e) return cuda_err(ctx, e, "launching a plain operator");
+    auto release = [&](int v) {
+      if (v >= 0 && --uses[v] == 0 && own[v]) { own[v].reset(); }
+    };
+    const bool bin = x.op == E_AND || x.op == E_OR || x.op == E_ANDNOT || x.op == E_RZ;
+    const bool un = x.op == E_NOT || x.op == E_NEAR || x.op == E_COPY;
+    if (un || bin) release(x.a);
+    if (bin) release(x.b);
+  }
+  auto* r = new vl_result();
+  r->ctx = ctx;
+  r->H = H; r->W = W; r->Wp = Wp;
+  r->n_roots = P.n_roots;
+  for (int q = 0; q < P.n_roots; ++q) r->roots.push_back(root_buf(P.root_slot[q]));
+  r->status = status;
+  r->stream = st;
+  r->keep.push_back(persist);
+  r->done = std::make_shared<EventHolder>();
+  if ((e = cudaEventCreateWithFlags(&r->done->ev, cudaEventDisableTiming)) ||
+      (e = cudaEventRecord(r->done->ev, st))) {
+    delete r;
+    return cuda_err(ctx, e, "recording an event");
+  }
+  *out = r;
+  return VL_OK;
+}
+
+}  // namespace
+
+// ================================================================= ABI ==
+
+extern "C" {
+
+VL_API void vl_config_default(vl_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->exec_mode = VL_EXEC_FUSED;
+  cfg->use_graphs = 1;
+}
+
+VL_API vl_status vl_context_create(const vl_config* cfg, vl_context** out) {
+  if (!out) return VL_ERR_ARG;
+  *out = nullptr;
+  auto* c = new vl_context();
+  vl_config_default(&c->cfg);
+  if (cfg) c->cfg = *cfg;
+  c->device = c->cfg.device;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e) { delete c; cudaGetLastError(); return VL_ERR_CUDA; }
+  cudaDeviceProp prop{};
+  if ((e = cudaGetDeviceProperties(&prop, c->device))) { delete c; return VL_ERR_CUDA; }
+  c->sm_count = prop.multiProcessorCount;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  c->gth = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 32;
+  c->gtww = c->cfg.tile_words > 0 ? c->cfg.tile_words : 32;
+  c->hmax = 8;
+  const int bh = c->gth + 2 * c->hmax, bw = c->gtww + 2;
+  const size_t budget = std::max<size_t>(ccl_smem_bytes(), 64 * 1024);
+  c->nb = (int)std::min<size_t>(64, budget / ((size_t)bh * bw * 4));
+  if (c->nb < 4) { delete c; return VL_ERR_ARG; }
+  c->pp.group_buffers = c->nb;
+  c->pp.hmax = c->hmax;
+  c->exec_smem = exec_smem_bytes(c->nb, bh, bw);
+  if ((e = exec_configure(c->exec_smem, &c->ctas_per_sm))) { delete c; cudaGetLastError(); return VL_ERR_CUDA; }
+  if (c->ctas_per_sm < 1) c->ctas_per_sm = 1;
+  if ((e = cudaMalloc(&c->ccl_status, sizeof(int32_t)))) { delete c; cudaGetLastError(); return VL_ERR_OOM; }
+  if ((e = cudaMemset(c->ccl_status, 0, sizeof(int32_t)))) { cudaFree(c->ccl_status); delete c; return VL_ERR_CUDA; }
+  *out = c;
+  return VL_OK;
+}
+
+VL_API const char* vl_last_error(vl_context* ctx) {
+  if (!valid(ctx, TAG_CTX)) return "invalid context";
+  std::lock_guard<std::mutex> g(ctx->err_mu);
+  return ctx->err.c_str();
+}
+
+VL_API void vl_free(void* h) {
+  if (!h) return;
+  const uint32_t tag = *reinterpret_cast<uint32_t*>(h);
+  switch (tag) {
+    case TAG_CTX: {
+      auto* c = static_cast<vl_context*>(h);
+      DeviceGuard dg(c->device);
+      if (c->ccl_status) cudaFree(c->ccl_status);
+      c->tag = TAG_DEAD;
+      delete c;
+      break;
+    }
+    case TAG_IMG: {
+      auto* im = static_cast<vl_image*>(h);
+      DeviceGuard dg(im->ctx->device);
+      im->tag = TAG_DEAD;
+      delete im;
+      break;
+    }
+    case TAG_FML: {
+      auto* f = static_cast<vl_formula*>(h);
+      f->tag = TAG_DEAD;
+      delete f;
+      break;
+    }
+    case TAG_RES: {
+      auto* r = static_cast<vl_result*>(h);
+      if (r->borrowed) return;  // owned by its batch
+      DeviceGuard dg(r->ctx->device);
+      r->tag = TAG_DEAD;
+      delete r;
+      break;
+    }
+    case TAG_BAT: {
+      auto* b = static_cast<vl_batch*>(h);
+      DeviceGuard dg(b->ctx->device);
+      batch_destroy(b);
+      break;
+    }
+    case TAG_SRV:
+      server_destroy(static_cast<vl_server*>(h));
+      break;
+    default:
+      break;
+  }
+}
+
+// ---------------------------------------------------------------- images
+
+static vl_status image_common(vl_context* ctx, int32_t h, int32_t w, int32_t c) {
+  if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
+  if (h < 1 || w < 1 || c < 1 || h > 65535 || w > 65535 || c > 4096)
+    return set_err(ctx, VL_ERR_ARG, "image sides must be in [1, 65535], channels in [1, 4096]");
+  if ((long long)h * w > 0x7FFFFFFFLL)
+    return set_err(ctx, VL_ERR_ARG, "image has more than 2^31 - 1 pixels");
+  return VL_OK;
+}
+
+VL_API vl_status vl_image_create(vl_context* ctx, int32_t h, int32_t w, int32_t channels,
+                                 const float* data, int32_t data_on_device, void* stream,
+                                 vl_image** out) {
+  vl_status s = image_common(ctx, h, w, channels);
+  if (s != VL_OK) return s;
+  if (!data || !out) return set_err(ctx, VL_ERR_ARG, "null data or output");
+  DeviceGuard dg(ctx->device);
+  auto im = std::make_unique<vl_image>();
+  im->ctx = ctx;
+  im->H = h; im->W = w; im->C = channels;
+  im->Wp = words_per_row(w);
+  im->pitch = 32 * im->Wp;
+  const size_t bytes = (size_t)channels * h * im->pitch * sizeof(float);
+  cudaError_t e = dev_alloc(ctx, bytes, S(stream), &im->block);
+  if (e) return cuda_err(ctx, e, "allocating an image");
+  im->data = static_cast<float*>(im->block->ptr);
+  if (im->pitch != w && (e = cudaMemsetAsync(im->data, 0, bytes, S(stream))))
+    return cuda_err(ctx, e, "clearing image padding");
+  e = cudaMemcpy2DAsync(im->data, (size_t)im->pitch * 4, data, (size_t)w * 4, (size_t)w * 4,
+                        (size_t)channels * h,
+                        data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        S(stream));
+  if (e) return cuda_err(ctx, e, "copying an image");
+  *out = im.release();
+  return VL_OK;
+}
+
+VL_API vl_status vl_mask_create(vl_context* ctx, int32_t h, int32_t w, const uint8_t* data,
+                                int32_t data_on_device, void* stream, vl_image** out) {
+  vl_status s = image_common(ctx, h, w, 1);
+  if (s != VL_OK) return s;
+  if (!data || !out) return set_err(ctx, VL_ERR_ARG, "null data or output");
+  DeviceGuard dg(ctx->device);
+  auto im = std::make_unique<vl_image>();
+  im->ctx = ctx;
+  im->H = h; im->W = w; im->C = 1; im->is_mask = 1;
+  im->Wp = words_per_row(w);
+  im->pitch = 32 * im->Wp;
+  cudaError_t e = dev_alloc(ctx, (size_t)h * im->Wp * 4, S(stream), &im->block);
+  if (e) return cuda_err(ctx, e, "allocating a mask");
+  im->mask = static_cast<uint32_t*>(im->block->ptr);
+  const uint8_t* src = data;
+  DevBlockPtr tmp;
+  if (!data_on_device) {
+    if ((e = dev_alloc(ctx, (size_t)h * w, S(stream), &tmp))) return cuda_err(ctx, e, "allocating staging");
+    if ((e = cudaMemcpyAsync(tmp->ptr, data, (size_t)h * w, cudaMemcpyHostToDevice, S(stream))))
+      return cuda_err(ctx, e, "copying a mask");
+    src = static_cast<const uint8_t*>(tmp->ptr);
+  }
+  if ((e = launch_pack_u8(src, MaskGeom{h, w, im->Wp}, im->mask, S(stream))))
+    return cuda_err(ctx, e, "packing a mask");
+  *out = im.release();
+  return VL_OK;
+}
+
+VL_API vl_status vl_mask_create_packed(vl_context* ctx, int32_t h, int32_t w, const uint32_t* words,
+                                       int32_t data_on_device, void* stream, vl_image** out) {
+  vl_status s = image_common(ctx, h, w, 1);
+  if (s != VL_OK) return s;
+  if (!words || !out) return set_err(ctx, VL_ERR_ARG, "null data or output");
+  DeviceGuard dg(ctx->device);
+  auto im = std::make_unique<vl_image>();
+  im->ctx = ctx;
+  im->H = h; im->W = w; im->C = 1; im->is_mask = 1;
+  im->Wp = words_per_row(w);
+  im->pitch = 32 * im->Wp;
+  const size_t bytes = (size_t)h * im->Wp * 4;
+  cudaError_t e = dev_alloc(ctx, bytes, S(stream), &im->block);
+  if (e) return cuda_err(ctx, e, "allocating a mask");
+  im->mask = static_cast<uint32_t*>(im->block->ptr);
+  if ((e = cudaMemcpyAsync(im->mask, words, bytes,
+                           data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           S(stream))))
+    return cuda_err(ctx, e, "copying a mask");
+  if ((e = launch_clear_padding(im->mask, MaskGeom{h, w, im->Wp}, S(stream))))
+    return cuda_err(ctx, e, "clearing mask padding");
+  *out = im.release();
+  return VL_OK;
+}
+
+VL_API vl_status vl_image_info(const vl_image* img, int32_t* h, int32_t* w, int32_t* channels,
+                               int32_t* is_mask) {
+  if (!valid(img, TAG_IMG)) return VL_ERR_ARG;
+  if (h) *h = img->H;
+  if (w) *w = img->W;
+  if (channels) *channels = img->C;
+  if (is_mask) *is_mask = img->is_mask;
+  return VL_OK;
+}
+
+// -------------------------------------------------------------- formulas
+
+static PlanParams default_plan_params() {
+  // the tile configuration of a default context: 32 x 32-word group tiles,
+  // halo budget 8, buffers that fit the labelling footprint
+  PlanParams pp;
+  pp.hmax = 8;
+  const int bh = 32 + 2 * pp.hmax, bw = 32 + 2;
+  const size_t budget = std::max<size_t>(ccl_smem_bytes(), 64 * 1024);
+  pp.group_buffers = (int)std::min<size_t>(64, budget / ((size_t)bh * bw * 4));
+  return pp;
+}
+
+VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes, int32_t n_nodes,
+                                    const int32_t* roots, int32_t n_roots, int32_t connectivity,
+                                    vl_formula** out) {
+  if (ctx && !valid(ctx, TAG_CTX)) return VL_ERR_ARG;
+  if (!out) return set_err(ctx, VL_ERR_ARG, "null output");
+  auto f = std::make_unique<vl_formula>();
+  f->ctx = ctx;
+  f->pp = ctx ? ctx->pp : default_plan_params();
+  std::string err;
+  int rc = compile_formula(nodes, n_nodes, roots, n_roots, connectivity, f->pp, &f->plan, &err);
+  if (rc != VL_OK) return set_err(ctx, (vl_status)rc, err);
+  *out = f.release();
+  return VL_OK;
+}
+
+VL_API vl_status vl_formula_plan(const vl_formula* f, vl_plan_sizes* sizes, vl_plan_step* steps,
+                                 vl_plan_insn* insns, vl_plan_select* selects, vl_plan_pct* pct,
+                                 int32_t* root_slots, int32_t* mask_slot_images) {
+  if (!valid(f, TAG_FML)) return VL_ERR_ARG;
+  const Plan& P = f->plan;
+  if (sizes) {
+    sizes->n_steps = (int32_t)P.steps.size();
+    sizes->n_insns = (int32_t)P.insns.size();
+    sizes->n_selects = (int32_t)P.rz.size();
+    sizes->n_pct = (int32_t)P.pct.size();
+    sizes->n_inter_slots = P.n_inter_slots;
+    sizes->n_root_slots = P.n_root_slots;
+    sizes->n_mask_slots = P.n_mask_slots;
+    sizes->n_roots = P.n_roots;
+  }
+  static_assert(sizeof(vl_plan_step) == sizeof(StepDesc), "step layout");
+  static_assert(sizeof(vl_plan_insn) == sizeof(Insn), "insn layout");
+  static_assert(sizeof(vl_plan_select) == sizeof(RzDesc), "select layout");
+  static_assert(sizeof(vl_plan_pct) == sizeof(PctDesc), "pct layout");
+  if (steps && !P.steps.empty()) std::memcpy(steps, P.steps.data(), sizeof(StepDesc) * P.steps.size());
+  if (insns && !P.insns.empty()) std::memcpy(insns, P.insns.data(), sizeof(Insn) * P.insns.size());
+  if (selects && !P.rz.empty()) std::memcpy(selects, P.rz.data(), sizeof(RzDesc) * P.rz.size());
+  if (pct && !P.pct.empty()) std::memcpy(pct, P.pct.data(), sizeof(PctDesc) * P.pct.size());
+  if (root_slots) for (int r = 0; r < P.n_roots; ++r) root_slots[r] = P.root_slot[r];
+  if (mask_slot_images)
+    for (int k = 0; k < P.n_mask_slots; ++k) mask_slot_images[k] = P.mask_slot_image[k];
+  return VL_OK;
+}
+
+VL_API vl_status vl_formula_info(const vl_formula* f, int64_t* n_primitive, int64_t* n_reach,
+                                 int32_t* n_roots, int32_t* n_images) {
+  if (!valid(f, TAG_FML)) return VL_ERR_ARG;
+  if (n_primitive) *n_primitive = f->plan.n_primitive;
+  if (n_reach) *n_reach = f->plan.n_reach;
+  if (n_roots) *n_roots = f->plan.n_roots;
+  if (n_images) *n_images = (int32_t)f->plan.img_kind.size();
+  return VL_OK;
+}
+
+VL_API vl_status vl_formula_stats_get(const vl_formula* f, vl_formula_stats* st) {
+  if (!valid(f, TAG_FML) || !st) return VL_ERR_ARG;
+  const Plan& P = f->plan;
+  std::memset(st, 0, sizeof(*st));
+  st->n_primitive = P.n_primitive;
+  st->n_reach = P.n_reach;
+  st->n_threshold = P.n_thr;
+  st->n_not = P.n_not;
+  st->n_and = P.n_and;
+  st->n_near = P.n_near;
+  st->n_roots = P.n_roots;
+  st->n_images = (int32_t)P.img_kind.size();
+  st->n_steps = (int32_t)P.steps.size();
+  for (const StepDesc& s : P.steps) st->n_groups += s.kind == SK_GROUP;
+  st->n_selects = (int32_t)P.rz.size();
+  std::map<std::pair<int, int>, int> ch;
+  for (const ENode& e : P.exec)
+    if (e.op == E_THR || e.op == E_PCT) ch[{e.img, e.ch}] = 1;
+  st->n_channels_read = (int32_t)ch.size();
+  for (const Insn& in : P.insns) {
+    if (in.op == I_STORE) st->mask_writes++;
+    if (in.op == I_LOAD) st->mask_reads++;
+  }
+  st->mask_writes += (int64_t)P.rz.size();  // each select writes Z
+  st->max_halo = P.max_group_halo;
+  return VL_OK;
+}
+
+// ------------------------------------------------------------ evaluation
+
+VL_API vl_status vl_eval_mode(vl_context* ctx, const vl_formula* f, vl_image* const* imgs,
+                              int32_t n_imgs, int32_t exec_mode, void* stream, vl_result** out) {
+  if (!valid(ctx, TAG_CTX) || !out) return VL_ERR_ARG;
+  if (!valid(f, TAG_FML)) return set_err(ctx, VL_ERR_ARG, "bad formula handle");
+  *out = nullptr;
+  if (f->pp.group_buffers != ctx->pp.group_buffers || f->pp.hmax != ctx->pp.hmax)
+    return set_err(ctx, VL_ERR_ARG, "formula was planned for another tile configuration");
+  DeviceGuard dg(ctx->device);
+  if (exec_mode == VL_EXEC_PLAIN) return eval_plain(ctx, f, imgs, n_imgs, S(stream), out);
+  if (exec_mode != VL_EXEC_FUSED) return set_err(ctx, VL_ERR_ARG, "unknown execution form");
+  vl_job job{f, imgs, n_imgs, 0};
+  vl_batch* b = nullptr;
+  vl_status s = batch_build(ctx, &job, 1, S(stream), &b);
+  if (s != VL_OK) return s;
+  s = batch_run(b, S(stream));
+  if (s == VL_OK) batch_release_results(b, out);
+  batch_destroy(b);
+  return s;
+}
+
+VL_API vl_status vl_eval(vl_context* ctx, const vl_formula* f, vl_image* const* imgs, int32_t n_imgs,
+                         void* stream, vl_result** out) {
+  if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
+  return vl_eval_mode(ctx, f, imgs, n_imgs, ctx->cfg.exec_mode, stream, out);
+}
+
+VL_API vl_status vl_eval_batch(vl_context* ctx, const vl_job* jobs, int32_t n_jobs, void* stream,
+                               vl_result** outs) {
+  if (!valid(ctx, TAG_CTX) || !outs) return VL_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  vl_batch* b = nullptr;
+  vl_status s = batch_build(ctx, jobs, n_jobs, S(stream), &b);
+  if (s != VL_OK) return s;
+  s = batch_run(b, S(stream));
+  if (s == VL_OK) batch_release_results(b, outs);
+  batch_destroy(b);
+  return s;
+}
+
+VL_API vl_status vl_batch_prepare(vl_context* ctx, const vl_job* jobs, int32_t n_jobs, void* stream,
+                                  vl_batch** out) {
+  if (!valid(ctx, TAG_CTX) || !out) return VL_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  return batch_build(ctx, jobs, n_jobs, S(stream), out);
+}
+
+VL_API vl_status vl_batch_run(vl_batch* b, void* stream) {
+  if (!valid(b, TAG_BAT)) return VL_ERR_ARG;
+  DeviceGuard dg(b->ctx->device);
+  return batch_run(b, S(stream));
+}
+
+VL_API vl_status vl_batch_result(vl_batch* b, int32_t job, vl_result** out) {
+  if (!valid(b, TAG_BAT) || !out || b->released) return VL_ERR_ARG;
+  if (job < 0 || job >= (int)b->results.size()) return set_err(b->ctx, VL_ERR_ARG, "job out of range");
+  *out = b->results[job];
+  return VL_OK;
+}
+
+VL_API vl_status vl_batch_info(const vl_batch* b, int64_t* n_items, int32_t* grid, int64_t* smem) {
+  if (!valid(b, TAG_BAT)) return VL_ERR_ARG;
+  if (n_items) *n_items = b->L.n_items;
+  if (grid) *grid = b->L.grid;
+  if (smem) *smem = (int64_t)exec_smem_bytes(b->L.group_buffers, b->L.group_bh, b->L.group_bw);
+  return VL_OK;
+}
+
+// --------------------------------------------------------------- results
+
+VL_API vl_status vl_result_sync(vl_result* r) {
+  if (!valid(r, TAG_RES)) return VL_ERR_ARG;
+  DeviceGuard dg(r->ctx->device);
+  cudaError_t e = r->done ? cudaEventSynchronize(r->done->ev) : cudaStreamSynchronize(r->stream);
+  if (e) return cuda_err(r->ctx, e, "waiting for a result");
+  int32_t st = 0;
+  if ((e = cudaMemcpy(&st, r->status, sizeof(int32_t), cudaMemcpyDeviceToHost)))
+    return cuda_err(r->ctx, e, "reading a status word");
+  if (st == ST_TIMEOUT) return set_err(r->ctx, VL_ERR_TIMEOUT, "a device-side wait ran out");
+  if (st != 0) return set_err(r->ctx, VL_ERR_INTERNAL, "a device-side consistency check failed");
+  return VL_OK;
+}
+
+VL_API vl_status vl_result_info(const vl_result* r, int32_t* h, int32_t* w, int32_t* wp,
+                                int32_t* n_roots) {
+  if (!valid(r, TAG_RES)) return VL_ERR_ARG;
+  if (h) *h = r->H;
+  if (w) *w = r->W;
+  if (wp) *wp = r->Wp;
+  if (n_roots) *n_roots = r->n_roots;
+  return VL_OK;
+}
+
+VL_API vl_status vl_result_mask(const vl_result* r, int32_t root, uint32_t* dst, int32_t dst_on_device,
+                                void* stream) {
+  if (!valid(r, TAG_RES) || !dst) return VL_ERR_ARG;
+  if (root < 0 || root >= r->n_roots) return set_err(r->ctx, VL_ERR_ARG, "root out of range");
+  DeviceGuard dg(r->ctx->device);
+  const size_t bytes = (size_t)r->H * r->Wp * 4;
+  cudaError_t e = cudaMemcpyAsync(dst, r->roots[root], bytes,
+                                  dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  S(stream));
+  if (!e && !dst_on_device) e = cudaStreamSynchronize(S(stream));
+  if (e) return cuda_err(r->ctx, e, "copying a result mask");
+  return VL_OK;
+}
+
+VL_API vl_status vl_result_masks(const vl_result* r, uint32_t* dst, int32_t dst_on_device,
+                                 void* stream) {
+  if (!valid(r, TAG_RES) || !dst) return VL_ERR_ARG;
+  DeviceGuard dg(r->ctx->device);
+  const size_t words = (size_t)r->H * r->Wp;
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < r->n_roots && !e; ++q)
+    e = cudaMemcpyAsync(dst + words * q, r->roots[q], words * 4,
+                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S(stream));
+  if (!e && !dst_on_device) e = cudaStreamSynchronize(S(stream));
+  if (e) return cuda_err(r->ctx, e, "copying result masks");
+  return VL_OK;
+}
+
+VL_API vl_status vl_result_mask_u8(const vl_result* r, int32_t root, uint8_t* dst, int32_t dst_on_device,
+                                   void* stream) {
+  if (!valid(r, TAG_RES) || !dst) return VL_ERR_ARG;
+  if (root < 0 || root >= r->n_roots) return set_err(r->ctx, VL_ERR_ARG, "root out of range");
+  DeviceGuard dg(r->ctx->device);
+  const MaskGeom g{r->H, r->W, r->Wp};
+  cudaError_t e;
+  if (dst_on_device) {
+    if ((e = launch_unpack_u8(r->roots[root], g, dst, S(stream)))) return cuda_err(r->ctx, e, "unpacking");
+    return VL_OK;
+  }
+  DevBlockPtr tmp;
+  if ((e = dev_alloc(r->ctx, (size_t)r->H * r->W, S(stream), &tmp))) return cuda_err(r->ctx, e, "staging");
+  if ((e = launch_unpack_u8(r->roots[root], g, static_cast<uint8_t*>(tmp->ptr), S(stream))) ||
+      (e = cudaMemcpyAsync(dst, tmp->ptr, (size_t)r->H * r->W, cudaMemcpyDeviceToHost, S(stream))) ||
+      (e = cudaStreamSynchronize(S(stream))))
+    return cuda_err(r->ctx, e, "unpacking a result mask");
+  return VL_OK;
+}
+
+VL_API vl_status vl_result_device_ptr(const vl_result* r, int32_t root, const uint32_t** ptr) {
+  if (!valid(r, TAG_RES) || !ptr) return VL_ERR_ARG;
+  if (root < 0 || root >= r->n_roots) return set_err(r->ctx, VL_ERR_ARG, "root out of range");
+  *ptr = r->roots[root];
+  return VL_OK;
+}
+
+// ------------------------------------------------------------------- ccl
+
+VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask, int32_t connectivity, int32_t* labels_dev,
+                        void* stream) {
+  if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
+  if (!valid(mask, TAG_IMG) || !mask->is_mask) return set_err(ctx, VL_ERR_ARG, "vl_ccl needs a mask image");
+  if (!labels_dev) return set_err(ctx, VL_ERR_ARG, "null labels buffer");
+  if (connectivity != 4 && connectivity != 8) return set_err(ctx, VL_ERR_ARG, "connectivity must be 4 or 8");
+  DeviceGuard dg(ctx->device);
+  cudaError_t e = cudaMemsetAsync(ctx->ccl_status, 0, sizeof(int32_t), S(stream));
+  if (!e) e = launch_ccl_labels(mask->mask, MaskGeom{mask->H, mask->W, mask->Wp}, connectivity,
+                                labels_dev, ctx->ccl_status, S(stream));
+  if (e) return cuda_err(ctx, e, "launching connected components");
+  return VL_OK;
+}
+
+VL_API vl_status vl_ccl_status(vl_context* ctx, void* stream) {
+  if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
+  DeviceGuard dg(ctx->device);
+  int32_t st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, ctx->ccl_status, sizeof(int32_t), cudaMemcpyDeviceToHost, S(stream));
+  if (!e) e = cudaStreamSynchronize(S(stream));
+  if (e) return cuda_err(ctx, e, "reading the labelling status");
+  if (st == ST_TIMEOUT) return VL_ERR_TIMEOUT;
+  return st ? VL_ERR_INTERNAL : VL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Host compiler: formula node array -> execution plan.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vl.h"
+#include "vl_internal.h"
+
+namespace vl {
+
+// Operators of the execution DAG (after expansion and lowering).
+enum EOp : int32_t {
+  E_TRUE, E_FALSE, E_THR, E_PCT, E_MASK, E_NOT, E_AND, E_OR, E_ANDNOT, E_NEAR,
+  E_RZ,   // component select: phi2-components meeting N phi1 (core of rho)
+  E_COPY  // identity (a root that is directly an input mask)
+};
+
+struct ENode {
+  int32_t op;
+  int32_t a, b;
+  int32_t img, ch;
+  int32_t lt;     // threshold direction: 1 for <, 0 for >
+  float t;
+  double q;
+  int32_t pct_slot;
+};
+
+struct PlanParams {
+  int group_buffers;  // shared-memory tile buffers per group
+  int hmax;           // maximum halo (N depth) inside a group
+};
+
+struct Plan {
+  int conn = 8;
+  int64_t n_primitive = 0;  // metric unit: primitive nodes after expansion + sharing
+  int64_t n_reach = 0;
+  int n_roots = 0;
+  std::vector<ENode> exec;       // execution DAG, topological
+  std::vector<int> exec_roots;   // exec node of each root
+  // materialised masks
+  int n_inter_slots = 0;         // reusable intermediate slots
+  int n_root_slots = 0;          // one per distinct root node
+  int n_mask_slots = 0;          // one per mask image index used
+  std::vector<int> root_slot;    // slot of each root
+  std::vector<int> mask_slot_image;  // image index of each mask slot
+  // steps
+  std::vector<StepDesc> steps;
+  std::vector<Insn> insns;
+  std::vector<RzDesc> rz;
+  std::vector<PctDesc> pct;
+  int n_pct_slots = 0;
+  int max_rz_batch = 0;
+  int max_group_halo = 0;
+  // image requirements: kind per image index (0 unused, 1 float, 2 mask)
+  std::vector<int> img_kind;
+  std::vector<int> img_channels;  // channels needed (max channel + 1)
+  PlanParams params{};
+  // accounting: primitive op counts by kind (threshold, not, and, N, rho, other)
+  int64_t n_thr = 0, n_not = 0, n_and = 0, n_near = 0, n_other = 0;
+};
+
+constexpr int MAX_RZ_BATCH = 4;
+
+// Returns VL_OK or an error code with a message in *err.
+int compile_formula(const vl_node* nodes, int n_nodes, const int32_t* roots, int n_roots,
+                    int conn, const PlanParams& pp, Plan* out, std::string* err);
+
+}  // namespace vl

@@ -1,0 +1,58 @@
+// Small device helpers shared by every kernel of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vl_internal.h"
+
+#define VL_DEV __device__ __forceinline__
+
+namespace vl {
+
+// Bits of word w (of a row of width W) that are real pixels.
+VL_DEV uint32_t vmask(int w, int W) {
+  int n = W - 32 * w;
+  return n >= 32 ? 0xFFFFFFFFu : (n <= 0 ? 0u : ((1u << n) - 1u));
+}
+
+// Mask of bits 0..b inclusive.
+VL_DEV uint32_t le_mask(int b) { return b >= 31 ? 0xFFFFFFFFu : ((2u << b) - 1u); }
+
+// Loads that bypass L1: data written by other CTAs of the same launch.
+VL_DEV uint32_t ldcg(const uint32_t* p) { return __ldcg(p); }
+VL_DEV int32_t ldcg(const int32_t* p) { return __ldcg(p); }
+VL_DEV float ldcg(const float* p) { return __ldcg(p); }
+VL_DEV uint8_t ldcg(const uint8_t* p) {
+  return (uint8_t)__ldcg((const unsigned char*)p);
+}
+
+// First error wins.
+VL_DEV void set_status(int32_t* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// Horizontal dilation of word c given its left/right neighbour words.
+VL_DEV uint32_t hdil(uint32_t l, uint32_t c, uint32_t r) {
+  return c | (c << 1) | (l >> 31) | (c >> 1) | (r << 31);
+}
+
+// Dilated word from a 3x3 neighbourhood of words (rows u, m, d; columns
+// left, centre, right).  conn 8: square; conn 4: cross.
+VL_DEV uint32_t near_word(uint32_t ul, uint32_t uc, uint32_t ur, uint32_t ml,
+                          uint32_t mc, uint32_t mr, uint32_t dl, uint32_t dc,
+                          uint32_t dr, int conn) {
+  if (conn == 8) return hdil(ul, uc, ur) | hdil(ml, mc, mr) | hdil(dl, dc, dr);
+  return uc | dc | hdil(ml, mc, mr);
+}
+
+// Order-preserving map float -> uint32 (for selects on float keys).
+VL_DEV uint32_t f2key(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+VL_DEV float key2f(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  return __uint_as_float(u);
+}
+
+}  // namespace vl

@@ -1,0 +1,182 @@
+// Persistent batched executor.
+//
+// One launch walks a device work list.  An item is a range of sub-items
+// (tiles, merge chunks, selects) of one step of one job; items are ordered
+// so that everything an item depends on comes earlier in the list.  CTAs pop
+// items with an atomic counter, so an item's dependencies were popped by
+// CTAs already running: the earliest unfinished item can always progress,
+// and the launch needs no co-residency guarantee.  Before running, an item
+// waits (bounded, with back-off) until every sub-item of its job's previous
+// step is done; a wait that runs out records VL_ERR_TIMEOUT in the job's
+// status word and the job's remaining items are skipped.  This replaces the
+// paper's host-side event chaining and host-checked CCL termination
+// (Sec. 3.2-3.3) with device-side counters: the host never waits.
+#include "dev_ccl.cuh"
+#include "dev_common.cuh"
+#include "dev_group.cuh"
+#include "dev_select.cuh"
+#include "kernels.h"
+
+namespace vl {
+
+namespace {
+
+VL_DEV int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
+                        unsigned char* smem, const ExecLaunch& L) {
+  const int cap = min(J.H * J.W + 64, 1 << 22);
+  switch (S.kind) {
+    case SK_PCT: {
+      SelectSmem& s = *reinterpret_cast<SelectSmem*>(smem);
+      const PctDesc d = J.pct[S.pct_off + sub];
+      const DevImage im = J.images[d.img];
+      const long long n = (long long)J.H * J.W;
+      const long long rank = (long long)(d.q * (double)(n - 1));
+      const float v = select_rank(s, im.data + (size_t)d.ch * J.H * J.pitch, J.H, J.W,
+                                  J.pitch, rank);
+      if (threadIdx.x == 0) J.pct_val[d.slot] = v;
+      break;
+    }
+    case SK_GROUP: {
+      GroupCtx c;
+      c.H = J.H; c.W = J.W; c.Wp = J.Wp; c.pitch = J.pitch;
+      const int ty = sub / J.g_tiles_x, tx = sub - ty * J.g_tiles_x;
+      c.r0 = ty * J.gth; c.w0 = tx * J.gtww;
+      c.th = min(J.gth, J.H - c.r0); c.tww = min(J.gtww, J.Wp - c.w0);
+      c.halo = S.halo;
+      c.bh = L.group_bh; c.bw = L.group_bw;
+      c.conn = J.conn;
+      c.buf = reinterpret_cast<uint32_t*>(smem);
+      c.images = J.images; c.slots = J.slots; c.pct_val = J.pct_val;
+      group_tile(c, J.insns + S.insn_off, S.insn_cnt);
+      break;
+    }
+    case SK_RZ_LOCAL:
+    case SK_RZ_FINAL: {
+      CclSmem& s = *reinterpret_cast<CclSmem*>(smem);
+      const int j = sub / per_rz, tile = sub - j * per_rz;
+      const RzDesc r = J.rz[S.rz_off + j];
+      const int k = r.scratch;
+      const CclGeom geo = ccl_geom(J.H, J.W, J.Wp, tile, J.c_tiles_x);
+      const uint32_t* phi1 = J.slots[r.phi1_slot];
+      const uint32_t* phi2 = J.slots[r.phi2_slot];
+      ccl_tile_label(s, phi2, phi1, geo, J.conn, J.status);
+      if (S.kind == SK_RZ_LOCAL) {
+        ccl_encode_roots(s, geo, ENC_PUBLISH, J.G[k], J.F[k], J.flist[k],
+                         J.fcount + S.rz_off + j, J.flist_cap, cap, J.status);
+        ccl_publish_border(s, geo, J.G[k]);
+      } else {
+        ccl_encode_roots(s, geo, ENC_SELECT, J.G[k], J.F[k], nullptr, nullptr, 0, cap,
+                         J.status);
+        ccl_write_select(s, geo, J.slots[r.z_slot]);
+      }
+      break;
+    }
+    case SK_RZ_MERGE: {
+      const int j = sub / per_rz, chunk = sub - j * per_rz;
+      const RzDesc r = J.rz[S.rz_off + j];
+      const int n = merge_items(J.H, J.Wp, J.c_tiles_y, J.c_tiles_x);
+      for (int i = chunk * blockDim.x + threadIdx.x; i < n; i += per_rz * blockDim.x)
+        ccl_merge_item(J.slots[r.phi2_slot], J.H, J.W, J.Wp, J.c_tiles_y, i, J.conn,
+                       J.G[r.scratch], cap, J.status);
+      break;
+    }
+    case SK_RZ_FLAGS: {
+      const int j = sub / per_rz, chunk = sub - j * per_rz;
+      const RzDesc r = J.rz[S.rz_off + j];
+      const int n = min(ldcg(J.fcount + S.rz_off + j), J.flist_cap);
+      int32_t* G = J.G[r.scratch];
+      uint8_t* F = J.F[r.scratch];
+      const int32_t* fl = J.flist[r.scratch];
+      for (int i = chunk * blockDim.x + threadIdx.x; i < n; i += per_rz * blockDim.x)
+        F[g_find(G, ldcg(fl + i), cap, J.status)] = 1;
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(EXEC_THREADS, 2) k_exec(ExecLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item, s_skip;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(L.head, 1);
+    __syncthreads();
+    const int idx = s_item;
+    if (idx >= L.n_items) break;
+    const WorkItem it = L.items[idx];
+    const DevJob& J = L.jobs[it.job];
+    const StepDesc S = J.steps[it.step];
+    const int ci = J.step_base + it.step;
+    if (threadIdx.x == 0) {
+      int skip = 0;
+      if (it.step > 0) {
+        const int32_t* ctr = L.done + ci - 1;
+        const int need = L.need[ci - 1];
+        long long spins = 0;
+        unsigned ns = 32;
+        // a negative limit makes every wait expire at once (tests of the
+        // timeout path); otherwise poll with back-off up to the limit
+        if (L.spin_limit < 0) {
+          set_status(J.status, ST_TIMEOUT);
+          skip = 1;
+        }
+        while (!skip && ld_acquire(ctr) < need) {
+          if (++spins > L.spin_limit) {
+            set_status(J.status, ST_TIMEOUT);
+            skip = 1;
+            break;
+          }
+          __nanosleep(ns);
+          if (ns < 1024) ns <<= 1;
+        }
+      }
+      if (ldcg(J.status) != 0) skip = 1;
+      s_skip = skip;
+    }
+    __syncthreads();
+    if (!s_skip) {
+      int per_rz = 1;
+      if (S.kind >= SK_RZ_LOCAL) per_rz = L.need[ci] / S.rz_cnt;
+      for (int k = 0; k < it.count; ++k) {
+        run_subitem(J, S, it.first + k, per_rz, smem_raw, L);
+        __syncthreads();
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(L.done + ci, it.count);
+  }
+}
+
+}  // namespace
+
+size_t exec_smem_bytes(int group_buffers, int group_bh, int group_bw) {
+  size_t g = (size_t)group_buffers * group_bh * group_bw * 4;
+  size_t m = sizeof(CclSmem);
+  if (sizeof(SelectSmem) > m) m = sizeof(SelectSmem);
+  if (g > m) m = g;
+  return (m + 15) & ~(size_t)15;
+}
+
+cudaError_t exec_configure(size_t smem_bytes, int* max_ctas_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_exec, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_ctas_per_sm, k_exec, EXEC_THREADS,
+                                                       smem_bytes);
+}
+
+cudaError_t launch_exec(const ExecLaunch& L, cudaStream_t st) {
+  const size_t sm = exec_smem_bytes(L.group_buffers, L.group_bh, L.group_bw);
+  k_exec<<<L.grid, EXEC_THREADS, sm, st>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace vl

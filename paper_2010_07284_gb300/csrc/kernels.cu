@@ -1,0 +1,307 @@
+// Plain per-operator kernels: one launch per primitive over a whole image.
+// They are the baseline execution form and the building blocks of vl_ccl.
+#include <algorithm>
+
+#include "dev_ccl.cuh"
+#include "dev_common.cuh"
+#include "dev_select.cuh"
+#include "kernels.h"
+
+namespace vl {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_for(long long items, int per_block, int cap = 152 * 32) {
+  long long b = (items + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// ------------------------------------------------------------ pointwise --
+
+__global__ void k_threshold(const float* __restrict__ plane, int pitch, MaskGeom g,
+                            float t, const float* t_dev, int lt, uint32_t* __restrict__ out) {
+  if (t_dev) t = *t_dev;
+  const int lane = threadIdx.x & 31;
+  const long long nwords = (long long)g.H * g.Wp;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nwords;
+       i += nwarps) {
+    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+    const float v = __ldg(plane + (size_t)y * pitch + 32 * w + lane);
+    const uint32_t word = __ballot_sync(FULL, lt ? (v < t) : (v > t)) & vmask(w, g.W);
+    if (lane == 0) out[i] = word;
+  }
+}
+
+template <int OP>  // 0 not, 1 and, 2 or, 3 const false, 4 const true, 5 and-not
+__global__ void k_pointwise(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                            MaskGeom g, uint32_t* __restrict__ out) {
+  const long long nwords = (long long)g.H * g.Wp;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(i % g.Wp);
+    uint32_t v;
+    if (OP == 0) v = ~__ldg(a + i) & vmask(w, g.W);
+    else if (OP == 1) v = __ldg(a + i) & __ldg(b + i);
+    else if (OP == 2) v = __ldg(a + i) | __ldg(b + i);
+    else if (OP == 3) v = 0u;
+    else if (OP == 5) v = __ldg(a + i) & ~__ldg(b + i);
+    else v = vmask(w, g.W);
+    out[i] = v;
+  }
+}
+
+__global__ void k_near(const uint32_t* __restrict__ a, MaskGeom g, int conn,
+                       uint32_t* __restrict__ out) {
+  const long long nwords = (long long)g.H * g.Wp;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+    uint32_t r[3][3];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int yy = y + dy - 1, ww = w + dx - 1;
+        r[dy][dx] = (yy >= 0 && yy < g.H && ww >= 0 && ww < g.Wp)
+                        ? __ldg(a + (size_t)yy * g.Wp + ww) : 0u;
+      }
+    out[i] = near_word(r[0][0], r[0][1], r[0][2], r[1][0], r[1][1], r[1][2], r[2][0],
+                       r[2][1], r[2][2], conn) & vmask(w, g.W);
+  }
+}
+
+// --------------------------------------------------------------- select --
+
+__global__ void __launch_bounds__(EXEC_THREADS) k_select(const float* plane, int pitch, int H,
+                                                         int W, long long rank, float* out) {
+  __shared__ SelectSmem s;
+  float v = select_rank(s, plane, H, W, pitch, rank);
+  if (threadIdx.x == 0) *out = v;
+}
+
+// ------------------------------------------------------------------ ccl --
+
+__global__ void __launch_bounds__(EXEC_THREADS, 2)
+k_ccl_local(const uint32_t* mask, const uint32_t* phi1, MaskGeom g, int tiles_x, int conn,
+            CclScratch sc, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
+  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
+  const int cap = min(g.H * g.W + 64, 1 << 22);
+  ccl_tile_label(s, mask, phi1, geo, conn, status);
+  ccl_encode_roots(s, geo, ENC_PUBLISH, sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap, cap,
+                   status);
+  ccl_publish_border(s, geo, sc.G);
+}
+
+__global__ void k_ccl_merge(const uint32_t* mask, MaskGeom g, int tiles_y, int tiles_x,
+                            int conn, int32_t* G, int32_t* status) {
+  const int n = merge_items(g.H, g.Wp, tiles_y, tiles_x);
+  const int cap = min(g.H * g.W + 64, 1 << 22);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    ccl_merge_item(mask, g.H, g.W, g.Wp, tiles_y, i, conn, G, cap, status);
+}
+
+__global__ void k_ccl_flags(int32_t* G, uint8_t* F, const int32_t* flist,
+                            const int32_t* fcount, int flist_cap, int cap, int32_t* status) {
+  const int n = min(*fcount, flist_cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    F[g_find(G, flist[i], cap, status)] = 1;
+}
+
+__global__ void __launch_bounds__(EXEC_THREADS, 2)
+k_ccl_final_labels(const uint32_t* mask, MaskGeom g, int tiles_x, int conn, int32_t* labels,
+                   int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
+  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
+  const int cap = min(g.H * g.W + 64, 1 << 22);
+  ccl_tile_label(s, mask, nullptr, geo, conn, status);
+  ccl_encode_roots(s, geo, ENC_LABEL, labels, nullptr, nullptr, nullptr, 0, cap, status);
+  ccl_write_labels(s, geo, labels);
+}
+
+__global__ void __launch_bounds__(EXEC_THREADS, 2)
+k_rz_final(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int tiles_x, int conn,
+           CclScratch sc, uint32_t* Z, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
+  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
+  const int cap = min(g.H * g.W + 64, 1 << 22);
+  ccl_tile_label(s, phi2, phi1, geo, conn, status);
+  ccl_encode_roots(s, geo, ENC_SELECT, sc.G, sc.F, nullptr, nullptr, 0, cap, status);
+  ccl_write_select(s, geo, Z);
+}
+
+// ----------------------------------------------------------- conversion --
+
+__global__ void k_pack_u8(const uint8_t* __restrict__ src, MaskGeom g, uint32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const long long nwords = (long long)g.H * g.Wp;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nwords;
+       i += nwarps) {
+    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+    const int x = 32 * w + lane;
+    const bool p = (x < g.W) && src[(size_t)y * g.W + x] != 0;
+    const uint32_t word = __ballot_sync(FULL, p);
+    if (lane == 0) out[i] = word;
+  }
+}
+
+__global__ void k_unpack_u8(const uint32_t* __restrict__ src, MaskGeom g, uint8_t* __restrict__ out) {
+  const long long n = (long long)g.H * g.W;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / g.W), x = (int)(i - (long long)y * g.W);
+    out[i] = (uint8_t)((__ldg(src + (size_t)y * g.Wp + (x >> 5)) >> (x & 31)) & 1u);
+  }
+}
+
+__global__ void k_clear_padding(uint32_t* m, MaskGeom g) {
+  const long long nwords = (long long)g.H * g.Wp;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
+       i += (long long)gridDim.x * blockDim.x)
+    m[i] &= vmask((int)(i % g.Wp), g.W);
+}
+
+}  // namespace
+
+// ============================================================ wrappers ==
+
+cudaError_t launch_threshold(const float* plane, int pitch, MaskGeom g, float t,
+                             const float* t_dev, bool lt, uint32_t* out, cudaStream_t st) {
+  long long nwords = (long long)g.H * g.Wp;
+  k_threshold<<<grid_for(nwords * 32, kThreads * 4), kThreads, 0, st>>>(plane, pitch, g, t,
+                                                                       t_dev, lt, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_not(const uint32_t* a, MaskGeom g, uint32_t* out, cudaStream_t st) {
+  k_pointwise<0><<<grid_for((long long)g.H * g.Wp, kThreads * 4), kThreads, 0, st>>>(a, nullptr,
+                                                                                    g, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_and(const uint32_t* a, const uint32_t* b, MaskGeom g, uint32_t* out,
+                       cudaStream_t st) {
+  k_pointwise<1><<<grid_for((long long)g.H * g.Wp, kThreads * 4), kThreads, 0, st>>>(a, b, g,
+                                                                                    out);
+  return cudaGetLastError();
+}
+cudaError_t launch_or(const uint32_t* a, const uint32_t* b, MaskGeom g, uint32_t* out,
+                      cudaStream_t st) {
+  k_pointwise<2><<<grid_for((long long)g.H * g.Wp, kThreads * 4), kThreads, 0, st>>>(a, b, g,
+                                                                                    out);
+  return cudaGetLastError();
+}
+cudaError_t launch_andnot(const uint32_t* a, const uint32_t* b, MaskGeom g, uint32_t* out,
+                          cudaStream_t st) {
+  k_pointwise<5><<<grid_for((long long)g.H * g.Wp, kThreads * 4), kThreads, 0, st>>>(a, b, g,
+                                                                                    out);
+  return cudaGetLastError();
+}
+cudaError_t launch_const(MaskGeom g, bool value, uint32_t* out, cudaStream_t st) {
+  if (value)
+    k_pointwise<4><<<grid_for((long long)g.H * g.Wp, kThreads * 4), kThreads, 0, st>>>(
+        nullptr, nullptr, g, out);
+  else
+    k_pointwise<3><<<grid_for((long long)g.H * g.Wp, kThreads * 4), kThreads, 0, st>>>(
+        nullptr, nullptr, g, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_near(const uint32_t* a, MaskGeom g, int conn, uint32_t* out,
+                        cudaStream_t st) {
+  k_near<<<grid_for((long long)g.H * g.Wp, kThreads * 2), kThreads, 0, st>>>(a, g, conn, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_select(const float* plane, int pitch, int H, int W, long long rank,
+                          float* out, cudaStream_t st) {
+  k_select<<<1, EXEC_THREADS, 0, st>>>(plane, pitch, H, W, rank, out);
+  return cudaGetLastError();
+}
+
+int ccl_tiles_y(int H) { return (H + CCL_TH - 1) / CCL_TH; }
+int ccl_tiles_x(int Wp) { return (Wp + CCL_TWW - 1) / CCL_TWW; }
+int ccl_flist_cap(int H, int Wp) {
+  return ccl_tiles_y(H) * ccl_tiles_x(Wp) * (2 * 32 * CCL_TWW + 2 * CCL_TH);
+}
+size_t ccl_smem_bytes() { return sizeof(CclSmem); }
+
+static cudaError_t ccl_set_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  const int sm = (int)sizeof(CclSmem);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_ccl_local, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_ccl_final_labels,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_rz_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+    return e;
+  done = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, int32_t* labels,
+                              int32_t* status, cudaStream_t st) {
+  cudaError_t e = ccl_set_attrs();
+  if (e) return e;
+  const int ty = ccl_tiles_y(g.H), tx = ccl_tiles_x(g.Wp);
+  const size_t sm = sizeof(CclSmem);
+  CclScratch sc{labels, nullptr, nullptr, nullptr, 0};
+  k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, nullptr, g, tx, conn, sc, status);
+  if ((e = cudaGetLastError())) return e;
+  const long long nm = (long long)(ty - 1) * g.Wp + (long long)(tx - 1) * g.H;
+  if (nm > 0) {
+    k_ccl_merge<<<grid_for(nm, kThreads), kThreads, 0, st>>>(mask, g, ty, tx, conn, labels,
+                                                             status);
+    if ((e = cudaGetLastError())) return e;
+  }
+  k_ccl_final_labels<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, g, tx, conn, labels, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int conn,
+                      CclScratch sc, uint32_t* Z, int32_t* status, cudaStream_t st) {
+  cudaError_t e = ccl_set_attrs();
+  if (e) return e;
+  const int ty = ccl_tiles_y(g.H), tx = ccl_tiles_x(g.Wp);
+  const size_t sm = sizeof(CclSmem);
+  const int cap = min(g.H * g.W + 64, 1 << 22);
+  if ((e = cudaMemsetAsync(sc.fcount, 0, sizeof(int32_t), st))) return e;
+  k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(phi2, phi1, g, tx, conn, sc, status);
+  if ((e = cudaGetLastError())) return e;
+  const long long nm = (long long)(ty - 1) * g.Wp + (long long)(tx - 1) * g.H;
+  if (nm > 0) {
+    k_ccl_merge<<<grid_for(nm, kThreads), kThreads, 0, st>>>(phi2, g, ty, tx, conn, sc.G,
+                                                             status);
+    if ((e = cudaGetLastError())) return e;
+  }
+  k_ccl_flags<<<grid_for(sc.flist_cap, kThreads), kThreads, 0, st>>>(
+      sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap, cap, status);
+  if ((e = cudaGetLastError())) return e;
+  k_rz_final<<<ty * tx, EXEC_THREADS, sm, st>>>(phi1, phi2, g, tx, conn, sc, Z, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_u8(const uint8_t* src, MaskGeom g, uint32_t* out, cudaStream_t st) {
+  k_pack_u8<<<grid_for((long long)g.H * g.Wp * 32, kThreads * 4), kThreads, 0, st>>>(src, g,
+                                                                                    out);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack_u8(const uint32_t* src, MaskGeom g, uint8_t* out, cudaStream_t st) {
+  k_unpack_u8<<<grid_for((long long)g.H * g.W, kThreads * 8), kThreads, 0, st>>>(src, g, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_clear_padding(uint32_t* m, MaskGeom g, cudaStream_t st) {
+  k_clear_padding<<<grid_for((long long)g.H * g.Wp, kThreads * 4), kThreads, 0, st>>>(m, g);
+  return cudaGetLastError();
+}
+
+}  // namespace vl

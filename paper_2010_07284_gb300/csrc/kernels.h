@@ -1,0 +1,74 @@
+// Host-side launch wrappers of the library's CUDA kernels (C++ linkage,
+// internal).  Every wrapper enqueues on `st` and returns the launch error.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vl_internal.h"
+
+namespace vl {
+
+struct MaskGeom {
+  int H, W, Wp;
+};
+
+// ---- plain per-operator kernels (one launch per primitive) ----
+cudaError_t launch_threshold(const float* plane, int pitch, MaskGeom g, float t,
+                             const float* t_dev, bool lt, uint32_t* out, cudaStream_t st);
+cudaError_t launch_not(const uint32_t* a, MaskGeom g, uint32_t* out, cudaStream_t st);
+cudaError_t launch_and(const uint32_t* a, const uint32_t* b, MaskGeom g, uint32_t* out,
+                       cudaStream_t st);
+cudaError_t launch_or(const uint32_t* a, const uint32_t* b, MaskGeom g, uint32_t* out,
+                      cudaStream_t st);
+cudaError_t launch_andnot(const uint32_t* a, const uint32_t* b, MaskGeom g, uint32_t* out,
+                          cudaStream_t st);
+cudaError_t launch_const(MaskGeom g, bool value, uint32_t* out, cudaStream_t st);
+cudaError_t launch_near(const uint32_t* a, MaskGeom g, int conn, uint32_t* out,
+                        cudaStream_t st);
+cudaError_t launch_select(const float* plane, int pitch, int H, int W, long long rank,
+                          float* out, cudaStream_t st);
+
+// ---- connected components (tile-local, merge, flags, final) ----
+struct CclScratch {
+  int32_t* G;       // H*W int32 (union-find by gid); may alias the labels
+  uint8_t* F;       // H*W bytes (component flags), rho only
+  int32_t* flist;   // flagged border roots, rho only
+  int32_t* fcount;  // its length (zeroed by the caller before the local pass)
+  int32_t flist_cap;
+};
+int ccl_tiles_y(int H);
+int ccl_tiles_x(int Wp);
+int ccl_flist_cap(int H, int Wp);
+size_t ccl_smem_bytes();
+
+// Labels: labels_dev doubles as the union-find array.
+cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, int32_t* labels,
+                              int32_t* status, cudaStream_t st);
+// Component select Z (rho core): Z = phi2-components meeting N phi1.
+cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int conn,
+                      CclScratch sc, uint32_t* Z, int32_t* status, cudaStream_t st);
+
+// ---- mask conversion ----
+cudaError_t launch_pack_u8(const uint8_t* src, MaskGeom g, uint32_t* out, cudaStream_t st);
+cudaError_t launch_unpack_u8(const uint32_t* src, MaskGeom g, uint8_t* out, cudaStream_t st);
+cudaError_t launch_clear_padding(uint32_t* m, MaskGeom g, cudaStream_t st);
+
+// ---- persistent executor ----
+struct ExecLaunch {
+  const DevJob* jobs;
+  const WorkItem* items;
+  int32_t n_items;
+  int32_t* head;           // work-queue head (zeroed before launch)
+  int32_t* done;           // per (job, step) finished sub-items (zeroed)
+  const int32_t* need;     // per (job, step) sub-items in total
+  int64_t spin_limit;
+  int32_t group_buffers;   // shared-memory buffers per group tile
+  int32_t group_bh;        // rows per buffer (gth + 2*HMAX)
+  int32_t group_bw;        // words per buffer (gtww + 2)
+  int32_t grid;            // CTAs
+};
+size_t exec_smem_bytes(int group_buffers, int group_bh, int group_bw);
+cudaError_t exec_configure(size_t smem_bytes, int* max_ctas_per_sm);
+cudaError_t launch_exec(const ExecLaunch& L, cudaStream_t st);
+
+}  // namespace vl

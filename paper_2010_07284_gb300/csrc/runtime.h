@@ -1,0 +1,112 @@
+// Runtime objects behind the C ABI handles (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/vl.h"
+#include "compiler.h"
+#include "kernels.h"
+#include "vl_internal.h"
+
+namespace vl {
+
+enum : uint32_t {
+  TAG_CTX = 0x5643544Bu,
+  TAG_IMG = 0x56494D47u,
+  TAG_FML = 0x56464D4Cu,
+  TAG_RES = 0x56524553u,
+  TAG_BAT = 0x56424154u,
+  TAG_SRV = 0x56535256u,
+  TAG_DEAD = 0xDEADDEADu,
+};
+
+// A device allocation released with cudaFreeAsync on `stream` when the last
+// owner drops it.
+struct DevBlock {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  ~DevBlock();
+};
+using DevBlockPtr = std::shared_ptr<DevBlock>;
+
+}  // namespace vl
+
+struct vl_context {
+  uint32_t tag = vl::TAG_CTX;
+  vl_config cfg{};
+  int device = 0;
+  int sm_count = 0;
+  int ctas_per_sm = 1;
+  size_t exec_smem = 0;
+  int gth = 32, gtww = 32, hmax = 8, nb = 14;
+  vl::PlanParams pp{};
+  int32_t* ccl_status = nullptr;  // device word of vl_ccl
+  std::string err;
+  std::mutex err_mu;  // guards err
+  std::mutex mu;      // serialises launches issued by the server thread
+};
+
+struct vl_image {
+  uint32_t tag = vl::TAG_IMG;
+  vl_context* ctx = nullptr;
+  int H = 0, W = 0, C = 0, Wp = 0, pitch = 0;
+  int is_mask = 0;
+  float* data = nullptr;
+  uint32_t* mask = nullptr;
+  vl::DevBlockPtr block;
+};
+
+struct vl_formula {
+  uint32_t tag = vl::TAG_FML;
+  vl_context* ctx = nullptr;
+  vl::PlanParams pp{};
+  vl::Plan plan;
+};
+
+namespace vl {
+struct EventHolder {
+  cudaEvent_t ev = nullptr;
+  ~EventHolder() { if (ev) cudaEventDestroy(ev); }
+};
+}  // namespace vl
+
+struct vl_result {
+  uint32_t tag = vl::TAG_RES;
+  vl_context* ctx = nullptr;
+  int H = 0, W = 0, Wp = 0;
+  int n_roots = 0;
+  bool borrowed = false;          // owned by a batch
+  std::vector<uint32_t*> roots;   // device mask per root
+  int32_t* status = nullptr;      // device status word
+  cudaStream_t stream = nullptr;
+  std::shared_ptr<vl::EventHolder> done;  // recorded after the work
+  std::vector<vl::DevBlockPtr> keep;  // memory this result keeps alive
+};
+
+struct vl_batch;
+
+namespace vl {
+
+// Helpers shared by api.cpp and server.cpp.
+vl_status set_err(vl_context* ctx, vl_status code, const std::string& msg);
+vl_status cuda_err(vl_context* ctx, cudaError_t e, const char* what);
+cudaError_t dev_alloc(vl_context* ctx, size_t bytes, cudaStream_t st, DevBlockPtr* out);
+
+// Build a batch (plans, tables, buffers, results) for `jobs`.
+vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStream_t st,
+                      vl_batch** out);
+vl_status batch_run(vl_batch* b, cudaStream_t st);
+// Hand the batch's results to the caller (they keep the batch memory alive).
+vl_status batch_release_results(vl_batch* b, vl_result** outs);
+int64_t batch_bytes(const vl_batch* b);
+void batch_destroy(vl_batch* b);
+void server_destroy(vl_server* s);
+
+}  // namespace vl

@@ -1,0 +1,137 @@
+// Internal data structures shared by the host compiler/runtime and the CUDA
+// kernels.  Plain structs only (no STL) so that device code can read them.
+#pragma once
+#include <stdint.h>
+
+namespace vl {
+
+// ----------------------------------------------------------------- geometry
+// Bit-packed masks: Wp = 4 * ceil(W / 128) words per row, LSB first.
+static inline int words_per_row(int w) { return ((w + 127) / 128) * 4; }
+
+// Connected-component tiles: up to CCL_TH rows x CCL_TWW words (1024 px).
+// One warp owns a row, one lane a 32-px word.
+constexpr int CCL_TH = 32;
+constexpr int CCL_TWW = 32;
+constexpr int CCL_MAXRUNS = CCL_TH * CCL_TWW * 16;  // alternating pixels
+
+constexpr int EXEC_THREADS = 512;  // threads per CTA of every tiled kernel
+constexpr int EXEC_WARPS = EXEC_THREADS / 32;
+
+// Device status word values (match vl_status where they overlap).
+constexpr int ST_OK = 0;
+constexpr int ST_TIMEOUT = 6;
+constexpr int ST_INTERNAL = 8;
+
+// --------------------------------------------------------- group bytecode
+// One instruction of a fused tile group.  Buffers are shared-memory tiles
+// of (th + 2*halo) rows x (tww + 2) words; `h` is the halo (in rows and
+// pixels) over which this node's value is needed.
+enum InsnOp : uint8_t {
+  I_NOP = 0,
+  I_THR = 1,     // dst = image[img].channel[ch] (> or <) t      (aux bit0: lt,
+                 //   bit1: t comes from the job's percentile slot `slot`)
+  I_LOAD = 2,    // dst = materialised mask slot `slot`
+  I_NOT = 3,     // dst = not a
+  I_AND = 4,     // dst = a and b
+  I_OR = 5,      // dst = a or b
+  I_NEAR = 6,    // dst = N a (connectivity of the formula)
+  I_CONST = 7,   // dst = all-false (aux 0) or all-true (aux 1)
+  I_STORE = 8,   // materialised mask slot `slot` = a   (core region only)
+  I_ANDNOT = 9,  // dst = a and not b
+};
+
+struct Insn {        // 16 bytes
+  uint8_t op;
+  uint8_t dst;
+  uint8_t a;
+  uint8_t b;
+  int16_t h;         // halo of this node within the group
+  int16_t slot;      // materialised-mask slot / percentile slot
+  int16_t img;       // image index (THR)
+  int16_t ch;        // channel (THR)
+  float t;           // threshold constant (THR)
+};
+static_assert(sizeof(Insn) == 16, "Insn layout");
+
+// -------------------------------------------------------------- plan steps
+enum StepKind : int32_t {
+  SK_PCT = 0,        // percentile selects: one item per percentile slot
+  SK_GROUP = 1,      // fused pointwise/N tile group: one item per tile
+  SK_RZ_LOCAL = 2,   // rho batch, tile-local labelling + publish: item = (rz, tile)
+  SK_RZ_MERGE = 3,   // rho batch, union across tile borders: item = (rz, chunk)
+  SK_RZ_FLAGS = 4,   // rho batch, flags to global roots: item = (rz, chunk)
+  SK_RZ_FINAL = 5,   // rho batch, relabel + write Z: item = (rz, tile)
+};
+
+struct StepDesc {
+  int32_t kind;
+  int32_t insn_off;  // groups: first instruction (into the formula's insns)
+  int32_t insn_cnt;
+  int32_t halo;      // groups: halo rows/px
+  int32_t rz_off;    // rho batches: first RZ entry
+  int32_t rz_cnt;
+  int32_t pct_off;   // percentile step: first PCT entry
+  int32_t pct_cnt;
+};
+
+// Component select Z = union of phi2-components meeting N phi1 (the core of
+// rho, Sec. 3.2); the compiler lowers rho phi1[phi2] to N(phi1 or Z).
+struct RzDesc {
+  int16_t phi1_slot;
+  int16_t phi2_slot;
+  int16_t z_slot;
+  int16_t scratch;   // index of the job's CCL scratch set used
+};
+
+struct PctDesc {
+  int16_t img;
+  int16_t ch;
+  int16_t slot;      // percentile slot written
+  int16_t pad;
+  double q;
+};
+
+// ----------------------------------------------------- executor job table
+struct DevImage {
+  const float* data;       // float images: channels planes of H x pitch
+  const uint32_t* mask;    // mask images: H x Wp words
+  int32_t channels;
+  int32_t is_mask;
+};
+
+struct DevJob {
+  int32_t H, W, Wp, pitch;      // pitch in floats = 32 * Wp
+  int32_t n_steps;
+  int32_t step_base;            // into the launch's step table
+  int32_t gth, gtww;            // group tile rows / words
+  int32_t g_tiles_y, g_tiles_x; // group tiles
+  int32_t c_tiles_y, c_tiles_x; // CCL tiles
+  int32_t conn;
+  int32_t n_images;
+  const DevImage* images;
+  uint32_t* const* slots;       // materialised mask slots
+  const Insn* insns;
+  const StepDesc* steps;        // this job's formula steps
+  const RzDesc* rz;
+  const PctDesc* pct;
+  float* pct_val;               // percentile values by slot
+  int32_t* G[4];                // CCL scratch sets: union-find over gids
+  uint8_t* F[4];                //   component flags by gid
+  int32_t* flist[4];            //   flagged boundary roots
+  int32_t* fcount;              // flagged-root count per select (zeroed per launch)
+  int32_t flist_cap;
+  int32_t pad0;
+  int32_t* status;              // device status word of this job
+};
+
+// One work item of the persistent executor: a range of `count` consecutive
+// sub-items (tiles, chunks, rz x tile) of one step of one job.
+struct WorkItem {
+  int32_t job;
+  int32_t step;        // step index within the job
+  int32_t first;       // first sub-item
+  int32_t count;       // sub-items in this item
+};
+
+}  // namespace vl

@@ -1,0 +1,147 @@
+"""Host logic of the library, on the CPU: the C ABI loads and exports what
+include/vl.h declares; the compiler counts primitives like the oracle, rejects
+malformed formulas, and its plans -- simulated tile by tile with garbage in
+every uncomputed halo row -- give the oracle's masks."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import plan_sim
+import workloads as wl
+import paper_2010_07284_gb300 as vg
+from paper_2010_07284_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"VL_API\s+[\w\s\*]+?\b(vl_\w+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = N.load()
+    declared = _declared_symbols()
+    assert len(declared) >= 30
+    for name in sorted(declared):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    bound = {s[0] for s in N.SIGNATURES}
+    assert declared <= bound | set(), f"unbound: {sorted(declared - bound)}"
+
+
+def _rec(f):
+    return wl.formula_to_records(f)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: wl.config1_formula(), lambda: wl.config4_formula(), lambda: wl.grow_spec_formula(),
+    lambda: wl.random_dag(300, seed=1), lambda: wl.random_dag(2000, seed=0),
+    lambda: wl.sequential_dag(200, seed=2)])
+def test_primitive_count_matches_oracle(make):
+    f = make()
+    F = vg.compile_formula(_rec(f), f.roots)
+    prim, _ = oracle.expand(_rec(f), f.roots)
+    assert F.info()["n_primitive"] == len(prim)
+    assert F.info()["n_reach"] == sum(1 for p in prim if p[0] == "REACH")
+
+
+@pytest.mark.parametrize("nodes,roots,conn,code", [
+    ([("NOT", 0, -1, 0, 0, 0, 0)], [0], 8, N.ERR_FORMULA),                       # self operand
+    ([("THR_GT", -1, -1, 0, 0, 0.5, 0), ("AND", 0, 5, 0, 0, 0, 0)], [1], 8, N.ERR_FORMULA),
+    ([("THR_GT", -1, -1, 0, 0, 0.5, 0)], [3], 8, N.ERR_FORMULA),                 # bad root
+    ([("PCT_GT", -1, -1, 0, 0, 0, 1.5)], [0], 8, N.ERR_FORMULA),                 # q > 1
+    ([("THR_GT", -1, -1, 0, 0, 0.5, 0)], [0], 6, N.ERR_ARG),                     # conn
+    ([(99, -1, -1, 0, 0, 0, 0)], [0], 8, N.ERR_FORMULA),                          # op code
+    ([("THR_GT", -1, -1, 0, 0, 0.5, 0), ("MASK", -1, -1, 0, 0, 0, 0),
+      ("AND", 0, 1, 0, 0, 0, 0)], [2], 8, N.ERR_FORMULA),                         # image kinds clash
+])
+def test_malformed_formulas_are_rejected(nodes, roots, conn, code):
+    with pytest.raises(N.VlError) as e:
+        vg.compile_formula(nodes, roots, conn)
+    assert e.value.code == code
+
+
+def _check_sim(f, images, masks=None, conn=8, seed=0):
+    masks = masks or {}
+    F = vg.compile_formula(_rec(f), f.roots, conn)
+    plan = F.plan()
+    got = plan_sim.simulate(plan, images, masks, conn, seed=seed)
+    mlist = [masks[k] for k in sorted(masks)] if masks else []
+    # the oracle indexes float images and masks separately
+    exp = oracle.evaluate(_rec(f), f.roots, [im for im in images if im is not None], mlist,
+                          conn=conn, shape=(next(iter(masks.values())).shape if masks else None)).masks
+    for r, (g, e) in enumerate(zip(got, exp)):
+        if not np.array_equal(g.astype(np.uint8), e):
+            bad = np.argwhere(g.astype(np.uint8) != e)
+            raise AssertionError(f"root {r}: {len(bad)} pixels differ, first {bad[:5].tolist()}")
+    return plan
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_plan_config1_shape(conn):
+    pytest.importorskip("scipy")
+    img = wl.gaussian_field_image(130, 200, seed=3)
+    _check_sim(wl.config1_formula(), [img], conn=conn)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_plan_random_dags(conn, seed):
+    pytest.importorskip("scipy")
+    f = wl.random_dag(400, seed=seed, max_depth=60)
+    img = wl.uniform_image(70, 1100, seed=seed)   # two tile rows+, two tile columns
+    _check_sim(f, [img], conn=conn, seed=seed)
+
+
+def test_plan_large_random_dag_is_split_and_correct():
+    pytest.importorskip("scipy")
+    f = wl.random_dag(2000, seed=0)
+    img = wl.uniform_image(40, 300, seed=5)
+    plan = _check_sim(f, [img], conn=8)
+    groups = [s for s in plan["steps"] if s["kind"] == 1]
+    assert len(groups) > 1
+    assert max(s["halo"] for s in groups) <= 8
+
+
+def test_plan_sequential_chain_hits_halo_budget():
+    pytest.importorskip("scipy")
+    nodes = [("THR_GT", -1, -1, 0, 0, 0.7, 0.0)]
+    for i in range(40):
+        nodes.append(("NEAR", len(nodes) - 1, -1, 0, 0, 0, 0))
+    f = wl.Formula([wl.Node(*n) for n in nodes], [len(nodes) - 1])
+    img = wl.uniform_image(90, 150, seed=9)
+    plan = _check_sim(f, [img], conn=8)
+    assert sum(1 for s in plan["steps"] if s["kind"] == 1) >= 5
+
+
+def test_plan_config4_formula_with_percentiles():
+    pytest.importorskip("scipy")
+    f = wl.config4_formula()
+    img = wl.mri_phantom_batch([(70, 90)], seed=4)[0]
+    for conn in (4, 8):
+        _check_sim(f, [img], conn=conn)
+
+
+def test_plan_mask_atoms_constants_and_mask_root():
+    pytest.importorskip("scipy")
+    rng = np.random.default_rng(7)
+    m0 = rng.random((50, 60)) < 0.5
+    m1 = rng.random((50, 60)) < 0.02
+    nodes = [("MASK", -1, -1, 0, 0, 0, 0), ("MASK", -1, -1, 1, 0, 0, 0),
+             ("REACH", 1, 0, 0, 0, 0, 0), ("TRUE", -1, -1, 0, 0, 0, 0),
+             ("AND", 2, 3, 0, 0, 0, 0), ("FALSE", -1, -1, 0, 0, 0, 0),
+             ("REACH", 0, 5, 0, 0, 0, 0), ("GROW", 1, 0, 0, 0, 0, 0),
+             ("REACH", 1, 3, 0, 0, 0, 0)]
+    f = wl.Formula([wl.Node(*n) for n in nodes], [4, 0, 6, 7, 8, 3])
+    for conn in (4, 8):
+        _check_sim(f, [None, None], masks={0: m0, 1: m1}, conn=conn)
