@@ -83,7 +83,8 @@ typedef struct {
   int32_t device;         /* CUDA device ordinal (default 0) */
   int32_t exec_mode;      /* vl_exec_mode for vl_eval (default FUSED) */
   int32_t use_graphs;     /* capture batched launches in CUDA graphs (1) */
-  int32_t reserved0;
+  int32_t trace;          /* record a device-side step timeline in batched
+                             launches (see vl_batch_trace); default 0 */
   int64_t spin_limit;     /* cap on polls of every device-side wait; 0 =
                              default (~2^22 polls with back-off, about a
                              second); a wait that runs out sets
@@ -305,6 +306,15 @@ VL_API vl_status vl_batch_prepare(vl_context* ctx, const vl_job* jobs, int32_t n
 VL_API vl_status vl_batch_run(vl_batch* b, void* stream);
 VL_API vl_status vl_batch_result(vl_batch* b, int32_t job, vl_result** out);
 
+/* Step timeline of the last run of a batch made by a context with `trace`
+ * set: for every (job, step) seven int64 values {job, step, kind, start_ns,
+ * end_ns, busy_ns, wait_ns} -- kind as in vl_plan_step, start/end from the
+ * device global timer, busy = summed time of its work items, wait = summed
+ * time its items spent waiting for the previous step.  Waits for the batch's
+ * work.  Writes up to max_entries entries; *n_entries gets the total. */
+VL_API vl_status vl_batch_trace(const vl_batch* b, int64_t* out, int64_t max_entries,
+                                int64_t* n_entries);
+
 /* Shape of a batch launch: work items, CTAs, dynamic shared memory. */
 VL_API vl_status vl_batch_info(const vl_batch* b, int64_t* n_items, int32_t* grid,
                                int64_t* smem_bytes);
@@ -312,6 +322,12 @@ VL_API vl_status vl_batch_info(const vl_batch* b, int64_t* n_items, int32_t* gri
 /* Wait for the result's work and return its device status word: VL_OK,
  * VL_ERR_TIMEOUT (a bounded device wait ran out) or VL_ERR_INTERNAL. */
 VL_API vl_status vl_result_sync(vl_result* res);
+
+/* Wait, then the raw device status word: 0, VL_ERR_TIMEOUT, or VL_ERR_INTERNAL
+ * in the low byte with the failed check in bits 8.. (1 global find bound,
+ * 2 global union bound, 3 flagged-root list overflow, 4 saved tile state out
+ * of range, 5 tile strip-run capacity, 6 shared union-find bound). */
+VL_API vl_status vl_result_status_word(vl_result* res, int32_t* word);
 
 /* Shape of a result (any pointer may be NULL); words_per_row = Wp. */
 VL_API vl_status vl_result_info(const vl_result* res, int32_t* h, int32_t* w,

@@ -33,7 +33,7 @@ class VlNode(C.Structure):
 
 class VlConfig(C.Structure):
     _fields_ = [("device", C.c_int32), ("exec_mode", C.c_int32), ("use_graphs", C.c_int32),
-                ("reserved0", C.c_int32), ("spin_limit", C.c_int64),
+                ("trace", C.c_int32), ("spin_limit", C.c_int64),
                 ("memory_budget", C.c_int64), ("tile_rows", C.c_int32),
                 ("tile_words", C.c_int32), ("reserved", C.c_int32 * 6)]
 
@@ -118,7 +118,9 @@ SIGNATURES = [
     ("vl_batch_run", C.c_int, [_P, _P]),
     ("vl_batch_result", C.c_int, [_P, _I32, _PP]),
     ("vl_batch_info", C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64)]),
+    ("vl_batch_trace", C.c_int, [_P, C.POINTER(_I64), _I64, C.POINTER(_I64)]),
     ("vl_result_sync", C.c_int, [_P]),
+    ("vl_result_status_word", C.c_int, [_P, C.POINTER(_I32)]),
     ("vl_result_info", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_result_mask", C.c_int, [_P, _I32, _P, _I32, _P]),
     ("vl_result_mask_u8", C.c_int, [_P, _I32, _P, _I32, _P]),

@@ -55,13 +55,15 @@ class _Handle:
 
 class Context(_Handle):
     def __init__(self, device: int = 0, exec_mode: str = "fused", use_graphs: bool = True,
-                 spin_limit: int = 0, tile_rows: int = 0, tile_words: int = 0):
+                 spin_limit: int = 0, tile_rows: int = 0, tile_words: int = 0,
+                 trace: bool = False):
         lib = N.load()
         cfg = N.VlConfig()
         lib.vl_config_default(C.byref(cfg))
         cfg.device = device
         cfg.exec_mode = N.EXEC_PLAIN if exec_mode == "plain" else N.EXEC_FUSED
         cfg.use_graphs = 1 if use_graphs else 0
+        cfg.trace = 1 if trace else 0
         cfg.spin_limit = spin_limit
         cfg.tile_rows = tile_rows
         cfg.tile_words = tile_words
@@ -276,6 +278,11 @@ class Result(_Handle):
     def check(self) -> None:
         self._check(self.sync())
 
+    def status_word(self) -> int:
+        w = C.c_int32()
+        self._check(N.load().vl_result_status_word(self._ptr, C.byref(w)))
+        return w.value
+
     def mask(self, root: int = 0, stream=None) -> np.ndarray:
         """Root mask as (H, W) uint8 on the host (unpacked by a device kernel)."""
         out = np.empty((self.h, self.w), dtype=np.uint8)
@@ -320,6 +327,17 @@ class Batch(_Handle):
         p = C.c_void_p()
         self._check(N.load().vl_batch_result(self._ptr, job, C.byref(p)))
         return Result(self.ctx, p.value, borrowed=True)
+
+    def trace(self) -> np.ndarray:
+        """Step timeline of the last run: rows {job, step, kind, start_ns,
+        end_ns, busy_ns, wait_ns}."""
+        lib = N.load()
+        n = C.c_int64()
+        self._check(lib.vl_batch_trace(self._ptr, None, 0, C.byref(n)))
+        out = np.zeros((n.value, 7), dtype=np.int64)
+        self._check(lib.vl_batch_trace(self._ptr, out.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       n.value, C.byref(n)))
+        return out
 
     def info(self) -> dict:
         n, g, s = C.c_int64(), C.c_int32(), C.c_int64()

@@ -129,6 +129,8 @@ struct vl_batch {
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   int64_t bytes = 0;
+  DevBlockPtr trace;                    // optional step timeline
+  std::vector<int32_t> trace_meta;      // {job, step, kind} per timeline entry
 };
 
 namespace vl {
@@ -143,7 +145,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     int H, W, Wp, pitch;
     int gty, gtx, cty, ctx_, ctiles;
     std::vector<int> need;
-    size_t off_images, off_slotptrs, off_pct, off_slots, off_scratch[MAX_RZ_BATCH * 3];
+    size_t off_images, off_slotptrs, off_pct, off_slots, off_scratch[MAX_RZ_BATCH * 5];
     size_t off_roots, off_status, off_fcount;
     int step_base, fcount_base;
     int flist_cap;
@@ -238,10 +240,13 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     const size_t P_px = (size_t)I.H * I.W;
     I.off_pct = take(sizeof(float) * std::max(1, P.n_pct_slots));
     I.off_slots = take(mask_bytes * P.n_inter_slots);
+    const size_t tstate = (size_t)I.ctiles * ccl_tile_cap_host(I.Wp);
     for (int k = 0; k < P.max_rz_batch; ++k) {
-      I.off_scratch[3 * k + 0] = take(P_px * 4);
-      I.off_scratch[3 * k + 1] = take(P_px);
-      I.off_scratch[3 * k + 2] = take((size_t)I.flist_cap * 4);
+      I.off_scratch[5 * k + 0] = take(P_px * 4);
+      I.off_scratch[5 * k + 1] = take(P_px);
+      I.off_scratch[5 * k + 2] = take((size_t)I.flist_cap * 4);
+      I.off_scratch[5 * k + 3] = take(tstate * 4);
+      I.off_scratch[5 * k + 4] = take(tstate);
     }
   }
   const size_t trans_bytes = align_up(off, 256);
@@ -310,12 +315,15 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     d.pct = reinterpret_cast<const PctDesc*>(tb + f_pct[k]);
     d.pct_val = reinterpret_cast<float*>(tb + I.off_pct);
     for (int s = 0; s < P.max_rz_batch; ++s) {
-      d.G[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[3 * s + 0]);
-      d.F[s] = reinterpret_cast<uint8_t*>(tb + I.off_scratch[3 * s + 1]);
-      d.flist[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[3 * s + 2]);
+      d.G[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[5 * s + 0]);
+      d.F[s] = reinterpret_cast<uint8_t*>(tb + I.off_scratch[5 * s + 1]);
+      d.flist[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[5 * s + 2]);
+      d.tpar[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[5 * s + 3]);
+      d.tflag[s] = reinterpret_cast<uint8_t*>(tb + I.off_scratch[5 * s + 4]);
     }
     d.fcount = counters_dev + 1 + total_steps + I.fcount_base;
     d.flist_cap = I.flist_cap;
+    d.tile_cap = ccl_tile_cap_host(I.Wp);
     d.status = status_dev + j;
     hj[j] = d;
     for (size_t s = 0; s < I.need.size(); ++s) hneed[I.step_base + s] = I.need[s];
@@ -341,6 +349,18 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   L.group_bh = ctx->gth + 2 * ctx->hmax;
   L.group_bw = ctx->gtww + 2;
   L.grid = std::max(1, std::min<int>(grid, (int)items.size()));
+  L.trace = nullptr;
+  if (ctx->cfg.trace) {
+    e = dev_alloc(ctx, sizeof(unsigned long long) * 4 * std::max(1, total_steps), st, &b->trace);
+    if (e) return cuda_err(ctx, e, "allocating the step timeline");
+    L.trace = static_cast<unsigned long long*>(b->trace->ptr);
+    for (int j = 0; j < n_jobs; ++j)
+      for (size_t s2 = 0; s2 < J[j].P->steps.size(); ++s2) {
+        b->trace_meta.push_back(j);
+        b->trace_meta.push_back((int32_t)s2);
+        b->trace_meta.push_back(J[j].P->steps[s2].kind);
+      }
+  }
   // ---- results
   b->done = std::make_shared<EventHolder>();
   e = cudaEventCreateWithFlags(&b->done->ev, cudaEventDisableTiming);
@@ -373,6 +393,12 @@ vl_status batch_run(vl_batch* b, cudaStream_t st) {
   char* tb = static_cast<char*>(b->trans->ptr);
   const bool graphs = ctx->cfg.use_graphs && st != nullptr && st != cudaStreamLegacy &&
                       st != cudaStreamPerThread;
+  if (b->trace) {  // timeline: start = +inf, the rest 0
+    const size_t n = b->trace->bytes / 32;
+    if ((e = cudaMemsetAsync(b->trace->ptr, 0, b->trace->bytes, st)) ||
+        (e = cudaMemset2DAsync(b->trace->ptr, 32, 0xFF, 8, n, st)))
+      return cuda_err(ctx, e, "clearing the step timeline");
+  }
   if (graphs && !b->gexec) {
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e) return cuda_err(ctx, e, "beginning graph capture");
@@ -468,15 +494,23 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
   if (!P.rz.empty()) {
     const size_t px = (size_t)H * W;
     const int cap = ccl_flist_cap(H, Wp);
-    const size_t bytes = align_up(px * 4, 256) + align_up(px, 256) + align_up((size_t)cap * 4, 256) + 256;
-    if ((e = dev_alloc(ctx, bytes, st, &scratch))) return cuda_err(ctx, e, "allocating select scratch");
+    const size_t tiles = (size_t)ccl_tiles_y(H) * ccl_tiles_x(Wp);
+    const int tcap = ccl_tile_cap_host(Wp);
+    size_t off = 0;
+    auto take = [&](size_t b) { off = align_up(off, 256); size_t o = off; off += b; return o; };
+    const size_t oG = take(px * 4), oF = take(px), oL = take((size_t)cap * 4), oC = take(4),
+                 oP = take(tiles * tcap * 4), oT = take(tiles * tcap);
+    if ((e = dev_alloc(ctx, align_up(off, 256), st, &scratch)))
+      return cuda_err(ctx, e, "allocating select scratch");
     char* p = static_cast<char*>(scratch->ptr);
-    sc.G = reinterpret_cast<int32_t*>(p);
-    sc.F = reinterpret_cast<uint8_t*>(p + align_up(px * 4, 256));
-    sc.flist = reinterpret_cast<int32_t*>(p + align_up(px * 4, 256) + align_up(px, 256));
-    sc.fcount = reinterpret_cast<int32_t*>(p + align_up(px * 4, 256) + align_up(px, 256) +
-                                           align_up((size_t)cap * 4, 256));
+    sc.G = reinterpret_cast<int32_t*>(p + oG);
+    sc.F = reinterpret_cast<uint8_t*>(p + oF);
+    sc.flist = reinterpret_cast<int32_t*>(p + oL);
+    sc.fcount = reinterpret_cast<int32_t*>(p + oC);
     sc.flist_cap = cap;
+    sc.tile_cap = tcap;
+    sc.tpar = reinterpret_cast<int32_t*>(p + oP);
+    sc.tflag = reinterpret_cast<uint8_t*>(p + oT);
   }
   const int N = (int)P.exec.size();
   std::vector<int> uses(N, 0), root_slot(N, -1);
@@ -901,6 +935,27 @@ VL_API vl_status vl_batch_result(vl_batch* b, int32_t job, vl_result** out) {
   return VL_OK;
 }
 
+VL_API vl_status vl_batch_trace(const vl_batch* b, int64_t* out, int64_t max_entries,
+                                int64_t* n_entries) {
+  if (!valid(b, TAG_BAT)) return VL_ERR_ARG;
+  if (!b->trace) return set_err(b->ctx, VL_ERR_ARG, "the batch's context was made without trace");
+  DeviceGuard dg(b->ctx->device);
+  const int64_t n = (int64_t)b->trace_meta.size() / 3;
+  if (n_entries) *n_entries = n;
+  if (!out) return VL_OK;
+  std::vector<unsigned long long> t(4 * (size_t)n);
+  cudaError_t e = cudaEventSynchronize(b->done->ev);
+  if (!e) e = cudaMemcpy(t.data(), b->trace->ptr, t.size() * 8, cudaMemcpyDeviceToHost);
+  if (e) return cuda_err(b->ctx, e, "reading the step timeline");
+  for (int64_t i = 0; i < std::min(n, max_entries); ++i) {
+    out[7 * i + 0] = b->trace_meta[3 * i + 0];
+    out[7 * i + 1] = b->trace_meta[3 * i + 1];
+    out[7 * i + 2] = b->trace_meta[3 * i + 2];
+    for (int k = 0; k < 4; ++k) out[7 * i + 3 + k] = (int64_t)t[4 * i + k];
+  }
+  return VL_OK;
+}
+
 VL_API vl_status vl_batch_info(const vl_batch* b, int64_t* n_items, int32_t* grid, int64_t* smem) {
   if (!valid(b, TAG_BAT)) return VL_ERR_ARG;
   if (n_items) *n_items = b->L.n_items;
@@ -920,7 +975,18 @@ VL_API vl_status vl_result_sync(vl_result* r) {
   if ((e = cudaMemcpy(&st, r->status, sizeof(int32_t), cudaMemcpyDeviceToHost)))
     return cuda_err(r->ctx, e, "reading a status word");
   if (st == ST_TIMEOUT) return set_err(r->ctx, VL_ERR_TIMEOUT, "a device-side wait ran out");
-  if (st != 0) return set_err(r->ctx, VL_ERR_INTERNAL, "a device-side consistency check failed");
+  if (st != 0)
+    return set_err(r->ctx, VL_ERR_INTERNAL,
+                   "a device-side consistency check failed (status word " + std::to_string(st) + ")");
+  return VL_OK;
+}
+
+VL_API vl_status vl_result_status_word(vl_result* r, int32_t* word) {
+  if (!valid(r, TAG_RES) || !word) return VL_ERR_ARG;
+  DeviceGuard dg(r->ctx->device);
+  cudaError_t e = r->done ? cudaEventSynchronize(r->done->ev) : cudaStreamSynchronize(r->stream);
+  if (!e) e = cudaMemcpy(word, r->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e) return cuda_err(r->ctx, e, "reading a status word");
   return VL_OK;
 }
 
@@ -998,9 +1064,19 @@ VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask, int32_t connectiv
   if (!labels_dev) return set_err(ctx, VL_ERR_ARG, "null labels buffer");
   if (connectivity != 4 && connectivity != 8) return set_err(ctx, VL_ERR_ARG, "connectivity must be 4 or 8");
   DeviceGuard dg(ctx->device);
-  cudaError_t e = cudaMemsetAsync(ctx->ccl_status, 0, sizeof(int32_t), S(stream));
+  const size_t tiles = (size_t)ccl_tiles_y(mask->H) * ccl_tiles_x(mask->Wp);
+  const int tcap = ccl_tile_cap_host(mask->Wp);
+  DevBlockPtr tmp;  // per-tile labelling state, released in stream order
+  cudaError_t e = dev_alloc(ctx, align_up(tiles * tcap * 4, 256) + tiles * tcap, S(stream), &tmp);
+  if (e) return cuda_err(ctx, e, "allocating labelling scratch");
+  CclScratch sc{};
+  sc.G = labels_dev;
+  sc.tile_cap = tcap;
+  sc.tpar = static_cast<int32_t*>(tmp->ptr);
+  sc.tflag = static_cast<uint8_t*>(tmp->ptr) + align_up(tiles * tcap * 4, 256);
+  e = cudaMemsetAsync(ctx->ccl_status, 0, sizeof(int32_t), S(stream));
   if (!e) e = launch_ccl_labels(mask->mask, MaskGeom{mask->H, mask->W, mask->Wp}, connectivity,
-                                labels_dev, ctx->ccl_status, S(stream));
+                                sc, ctx->ccl_status, S(stream));
   if (e) return cuda_err(ctx, e, "launching connected components");
   return VL_OK;
 }

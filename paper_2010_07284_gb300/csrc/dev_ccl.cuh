@@ -5,10 +5,9 @@
 // Design (sm_103a, union-find, no host round trips -- unlike the paper's
 // iterated pointer jumping with host-checked termination, Sec. 3.3):
 //   1. tile-local: one CTA labels a tile of CCL_TH rows x CCL_TWW words.
-//      Horizontal runs of foreground pixels are the union-find elements (run
-//      starts come from bit tricks on the packed words); runs of adjacent
-//      rows are united in shared memory with atomicMin.  Run ids follow the
-//      raster order, so a local root is the run holding the minimum pixel.
+//      The union-find elements are the connected pieces of two-row strips,
+//      found with bit operations on the packed words; strips are united in
+//      shared memory with atomicMin along a binary tree of strip boundaries.
 //   2. publish: every foreground pixel on the tile border, and every local
 //      root that reaches the border, gets an entry G[gid] in a global
 //      union-find array indexed by linear pixel id gid = y*W + x.
@@ -17,6 +16,8 @@
 //   4. final: each tile relabels again and resolves its border roots in G.
 // Labels are canonical: the minimum linear index of each component.
 #pragma once
+#include <climits>
+
 #include "dev_common.cuh"
 
 namespace vl {
@@ -24,14 +25,16 @@ namespace vl {
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 
 struct CclSmem {
-  uint32_t m[CCL_TH][CCL_TWW];
-  uint32_t st[CCL_TH][CCL_TWW];
-  int32_t pre[CCL_TH][CCL_TWW];
-  int32_t base[CCL_TH + 1];
+  uint32_t m[CCL_TH][CCL_TWW];   // rows of the tile
+  uint32_t u[CCL_NS][CCL_TWW];   // strip unions (row 2k | row 2k+1)
+  uint32_t st[CCL_NS][CCL_TWW];  // strip-run starts
+  int32_t pre[CCL_NS][CCL_TWW];  // starts before each word, per strip
+  int32_t qc[CCL_NS][CCL_TWW];   // boundary anchor entering each word
+  int32_t base[CCL_NS + 1];      // first strip-run id of each strip
   int32_t nruns;
   int32_t pad;
-  int32_t parent[CCL_MAXRUNS];
-  uint8_t flag[CCL_MAXRUNS];  // bit0 seed, bit1 on tile border, bit2 selected
+  int32_t parent[CCL_MAXRUNS];   // union-find; after labelling a root holds -(value + 2)
+  uint8_t flag[CCL_MAXRUNS];     // bit0 seed, bit1 on tile border, bit2 selected
 };
 
 struct CclGeom {
@@ -97,16 +100,31 @@ VL_DEV bool s_union(int32_t* par, int a, int b, int cap) {
 // unions).  The final relabelling pass must not compress: there, entries of
 // finished tiles already hold their final labels.
 VL_DEV int g_find(int32_t* G, int x, int cap, int32_t* status, bool compress = true) {
-  for (int it = 0; it < cap; ++it) {
-    int p = ldcg(&G[x]);
-    if (p == x) return x;
-    int r = ldcg(&G[p]);
-    if (r == p) return p;
-    if (compress) G[x] = r;
-    x = r;
+  int root = x;
+  int it = 0;
+  for (; it < cap; ++it) {
+    const int p = ldcg(&G[root]);
+    if (p == root) break;
+    root = p;
   }
-  set_status(status, ST_INTERNAL);
-  return x;
+  if (it == cap) {
+    set_status(status, ST_INTERNAL | RS_GFIND);
+    return root;
+  }
+  if (compress) {
+    // Point the path at the root.  Only nodes above the root are touched and
+    // a parent already at or below the root is left alone: parents then only
+    // ever move to ancestors with smaller ids (no cycles), and the root
+    // itself -- which a concurrent union may just have linked -- is never
+    // written.
+    for (int k = 0; k < it && x > root; ++k) {
+      const int p = ldcg(&G[x]);
+      if (p <= root) break;
+      G[x] = root;
+      x = p;
+    }
+  }
+  return root;
 }
 
 VL_DEV void g_union(int32_t* G, int a, int b, int cap, int32_t* status) {
@@ -119,27 +137,44 @@ VL_DEV void g_union(int32_t* G, int a, int b, int cap, int32_t* status) {
     if (old == a) return;
     a = old;
   }
-  set_status(status, ST_INTERNAL);
+  set_status(status, ST_INTERNAL | RS_GUNION);
 }
 
 // ------------------------------------------------------- tile labelling --
+//
+// Level 0 is bit-parallel: in a strip of two rows A (top) and B, the
+// components under 8-adjacency are exactly the runs of A | B (consecutive
+// set columns always touch, diagonally at least); under 4-adjacency they are
+// those runs cut where the set row switches from A-only to B-only (or back)
+// between two columns.  These "strip runs" are the union-find elements.
+// Strips are then merged across the CCL_NS - 1 strip boundaries in a
+// binary-tree order (boundary b at level = trailing ones of b, plus one), so
+// every level unites disjoint groups of strips and the trees stay shallow.
+// Across a boundary (rows A' = last row of the upper strip, B' = first row of
+// the lower one), the same two-row rule holds: every set pixel of A' and B'
+// inside one run of A' | B' (cut the same way for 4-adjacency) is connected,
+// so each row run starting inside it is united with the run's anchor.
 
-VL_DEV int run_id(const CclSmem& s, int row, int x) {
-  int w = x >> 5;
-  return s.base[row] + s.pre[row][w] + __popc(s.st[row][w] & le_mask(x & 31)) - 1;
+// Strip-run starts of a two-row strip (a, b) given the previous word's
+// (a, b) (0 at the tile's left edge).
+VL_DEV uint32_t strip_starts(uint32_t a, uint32_t b, uint32_t al, uint32_t bl, int conn) {
+  const uint32_t u = a | b, ul = al | bl;
+  uint32_t st = u & ~((u << 1) | (ul >> 31));
+  if (conn == 4) {
+    const uint32_t ao = a & ~b, bo = b & ~a, aol = al & ~bl, bol = bl & ~al;
+    st |= (((ao << 1) | (aol >> 31)) & bo) | (((bo << 1) | (bol >> 31)) & ao);
+  }
+  return st;
 }
 
-VL_DEV bool bit_at(const CclSmem& s, int row, int x) {
+// Strip run holding tile pixel x of strip k (x must be set in the strip).
+VL_DEV int sid(const CclSmem& s, int k, int x) {
+  const int w = x >> 5;
+  return s.base[k] + s.pre[k][w] + __popc(s.st[k][w] & le_mask(x & 31)) - 1;
+}
+
+VL_DEV bool mbit(const CclSmem& s, int row, int x) {
   return (s.m[row][x >> 5] >> (x & 31)) & 1u;
-}
-
-// Leftmost foreground pixel of `row` among the pixels adjacent to column x
-// (x-1..x+1 for 8-adjacency, x for 4), inside the tile; -1 if none.
-VL_DEV int window_hit(const CclSmem& s, int row, int x, int width, int conn) {
-  if (conn == 8 && x >= 1 && bit_at(s, row, x - 1)) return x - 1;
-  if (bit_at(s, row, x)) return x;
-  if (conn == 8 && x + 1 < width && bit_at(s, row, x + 1)) return x + 1;
-  return -1;
 }
 
 // Dilation of mask `a` at (image row y, image word w) for one warp whose
@@ -179,192 +214,396 @@ VL_DEV uint32_t warp_near_row(const uint32_t* a, int H, int W, int Wp, int y,
   return near_word(ul, u, ur, cl, c, cr, dl, d, dr, conn) & vmask(w, W);
 }
 
-// Label one tile in shared memory.  On return (after a block barrier):
-// s.m/st/pre/base describe the runs, s.parent[i] is the local root of run i,
-// s.flag[root] has bit0 set when a seed pixel lies in the component (if
-// phi1 != nullptr: seed = mask and N phi1), bit1 when the component reaches
-// the tile border.  Must be called by every thread of the block.
-VL_DEV void ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi1,
-                           const CclGeom& g, int conn, int32_t* status) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Anchor of the boundary run starting at tile pixel x of boundary b: the
+// strip run of its first pixel (upper strip if the upper row is set there).
+VL_DEV int anchor_at(const CclSmem& s, int b, int x) {
+  return mbit(s, 2 * b + 1, x) ? sid(s, b, x) : sid(s, b + 1, x);
+}
+
+// Root of strip run i once roots are encoded (parent[root] < 0).
+VL_DEV int root_of(const CclSmem& s, int i) {
+  const int p = s.parent[i];
+  return p >= 0 ? p : i;
+}
+
+// Label one tile in shared memory.  Returns false (uniformly, after a block
+// barrier) if the tile has more strip runs than the shared arrays hold, which
+// cannot happen for CCL_TH x CCL_TWW tiles; the caller then skips the tile.
+// On success: s.parent[i] of a non-root is its root (smallest id); a root
+// holds a negative value, with `min_pixel` -(component's minimum linear pixel
+// index + 2); s.flag[root] has bit0 when a seed pixel lies in the component
+// (seed = mask and N phi1, if phi1 is given) and bit1 when the component
+// reaches the tile border.  Must be called by every thread of the block.
+// Rows of the tile into shared memory, strip unions, strip-run starts and
+// their prefix counts.  Returns the number of strip runs (uniform, after a
+// block barrier).
+VL_DEV int ccl_tile_strips(CclSmem& s, const uint32_t* mask, const CclGeom& g, int conn) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nw = blockDim.x >> 5;
-  // 1. load, run starts, per-row prefix of run counts
-  for (int r = warp; r < g.th; r += nw) {
-    uint32_t m = 0;
-    if (lane < g.tww) m = ldcg(&mask[(size_t)(g.r0 + r) * g.Wp + g.w0 + lane]);
-    uint32_t left = __shfl_up_sync(FULL, m, 1);
-    if (lane == 0) left = 0;
-    uint32_t st = m & ~((m << 1) | (left >> 31));
-    int c = __popc(st);
-    int incl = warp_incl_scan(c, lane);
-    s.m[r][lane] = m;
-    s.st[r][lane] = st;
-    s.pre[r][lane] = incl - c;
-    if (lane == 31) s.base[r + 1] = incl;
+  const int ns = (g.th + 1) >> 1;
+  // 1. rows, strip unions, strip-run starts, per-strip prefix counts
+  for (int k = warp; k < ns; k += nw) {
+    const int r0 = 2 * k, r1 = 2 * k + 1;
+    uint32_t a = 0, b = 0;
+    if (lane < g.tww) {
+      a = ldcg(&mask[(size_t)(g.r0 + r0) * g.Wp + g.w0 + lane]);
+      if (r1 < g.th) b = ldcg(&mask[(size_t)(g.r0 + r1) * g.Wp + g.w0 + lane]);
+    }
+    uint32_t al = __shfl_up_sync(FULL, a, 1), bl = __shfl_up_sync(FULL, b, 1);
+    if (lane == 0) al = bl = 0;
+    const uint32_t st = strip_starts(a, b, al, bl, conn);
+    const int c = __popc(st);
+    const int incl = warp_incl_scan(c, lane);
+    s.m[r0][lane] = a;
+    s.m[r1][lane] = b;
+    s.u[k][lane] = a | b;
+    s.st[k][lane] = st;
+    s.pre[k][lane] = incl - c;
+    if (lane == 31) s.base[k + 1] = incl;
   }
   __syncthreads();
   if (warp == 0) {
-    int v = (lane < g.th) ? s.base[lane + 1] : 0;
-    int incl = warp_incl_scan(v, lane);
+    const int v = (lane < ns) ? s.base[lane + 1] : 0;
+    const int incl = warp_incl_scan(v, lane);
     __syncwarp();
-    if (lane < g.th) s.base[lane] = incl - v;
-    if (lane == 31) { s.base[g.th] = incl; s.nruns = incl; }
+    if (lane < ns) s.base[lane] = incl - v;
+    if (lane == 31) s.nruns = incl;
+    if (lane == 31) s.base[ns] = incl;
   }
   __syncthreads();
+  return s.nruns;
+}
+
+VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi1,
+                           const CclGeom& g, int conn, bool min_pixel, int32_t* status) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = blockDim.x >> 5;
+  const int ns = (g.th + 1) >> 1;
+  ccl_tile_strips(s, mask, g, conn);
   const int nruns = s.nruns;
-  for (int i = threadIdx.x; i < nruns; i += blockDim.x) {
+  if (nruns > CCL_MAXRUNS) {  // uniform: every thread reads the same count
+    set_status(status, ST_INTERNAL | RS_TRUNS);
+    return false;
+  }
+  for (int i = tid; i < nruns; i += blockDim.x) {
     s.parent[i] = i;
     s.flag[i] = 0;
   }
-  __syncthreads();
-  // 2. unite runs of adjacent rows: each run start looks at the window of
-  // the other row; the leftmost hit is enough (every overlapping pair of
-  // runs is met at the start of one of them).
-  const int width = 32 * g.tww;
-  const int cap = nruns + 64;
-  bool ok = true;
-  for (int r = 1 + warp; r < g.th; r += nw) {
-    if (lane < g.tww) {
-      uint32_t sc = s.st[r][lane];
-      while (sc) {
-        int b = __ffs(sc) - 1;
-        sc &= sc - 1;
-        int x = 32 * lane + b;
-        int p = window_hit(s, r - 1, x, width, conn);
-        if (p >= 0) ok &= s_union(s.parent, run_id(s, r, x), run_id(s, r - 1, p), cap);
-      }
-      uint32_t su = s.st[r - 1][lane];
-      while (su) {
-        int b = __ffs(su) - 1;
-        su &= su - 1;
-        int x = 32 * lane + b;
-        int p = window_hit(s, r, x, width, conn);
-        if (p >= 0) ok &= s_union(s.parent, run_id(s, r - 1, x), run_id(s, r, p), cap);
-      }
+  // 2. anchor of the boundary run entering each word from the left
+  for (int b = warp; b < ns - 1; b += nw) {
+    uint32_t A = 0, B = 0;
+    if (lane < g.tww) { A = s.m[2 * b + 1][lane]; B = s.m[2 * b + 2][lane]; }
+    uint32_t Al = __shfl_up_sync(FULL, A, 1), Bl = __shfl_up_sync(FULL, B, 1);
+    if (lane == 0) Al = Bl = 0;
+    const uint32_t qs = strip_starts(A, B, Al, Bl, conn);
+    int last = -1;
+    if (qs) last = anchor_at(s, b, 32 * lane + 31 - __clz(qs));
+    int idx = last >= 0 ? lane : -1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, idx, o);
+      if (lane >= o) idx = max(idx, t);
     }
+    int prev = __shfl_up_sync(FULL, idx, 1);
+    if (lane == 0) prev = -1;
+    const int carried = __shfl_sync(FULL, last, prev < 0 ? 0 : prev);
+    s.qc[b][lane] = prev < 0 ? -1 : carried;
   }
   __syncthreads();
-  // 3. flatten
-  for (int i = threadIdx.x; i < nruns; i += blockDim.x) {
+  // 3. unite across strip boundaries, one tree level at a time (boundary b
+  // belongs to level = trailing ones of b), so each level unites disjoint
+  // groups of strips.  Every thread takes a share of the row-run starts
+  // ("events") of one boundary word; the word's strip data sits in
+  // registers.  In each round the lanes of a warp whose roots form the same
+  // pair elect one leader to link them; a link that fails because its root
+  // was linked elsewhere leaves the follow-up union (old parent, lo) on the
+  // leader.  A flatten after every level keeps the next level's finds short.
+  const int cap = nruns + 64;
+  bool ok = true;
+  for (int level = 0; (1 << level) < ns; ++level) {
+    const int step = 2 << level, first = (1 << level) - 1;  // b = first + j * step
+    const int nb = (ns - 1 - first + step - 1) / step;
+    const int pairs = nb > 0 ? nb * g.tww : 0;
+    int T = 1;
+    while (pairs > 0 && T * 2 * pairs <= (int)blockDim.x) T *= 2;
+    const int pair = tid / T, sub = tid - (tid / T) * T;
+    const bool act = pair < pairs;
+    uint32_t A = 0, B = 0, qs = 0, evA = 0, evB = 0, stb = 0, stc = 0;
+    int b = 0, w = 0, bb = 0, bc = 0, carry = -1;
+    if (act) {
+      b = first + (pair / g.tww) * step;
+      w = pair - (pair / g.tww) * g.tww;
+      A = s.m[2 * b + 1][w];
+      B = s.m[2 * b + 2][w];
+      const uint32_t Al = w > 0 ? s.m[2 * b + 1][w - 1] : 0u;
+      const uint32_t Bl = w > 0 ? s.m[2 * b + 2][w - 1] : 0u;
+      qs = strip_starts(A, B, Al, Bl, conn);
+      stb = s.st[b][w];
+      stc = s.st[b + 1][w];
+      bb = s.base[b] + s.pre[b][w] - 1;
+      bc = s.base[b + 1] + s.pre[b + 1][w] - 1;
+      carry = s.qc[b][w];
+      // one event per (boundary run, strip run): drop a row-run start when
+      // neither a boundary-run start nor a strip-run start separates it
+      // from the previous one
+      const uint32_t ra_ = A & ~((A << 1) | (Al >> 31));
+      const uint32_t rb_ = B & ~((B << 1) | (Bl >> 31));
+      uint32_t t = ra_;
+      int q = -1;
+      while (t) {
+        const int p = __ffs(t) - 1;
+        t &= t - 1;
+        if (q < 0 || ((qs | stb) & le_mask(p) & ~le_mask(q))) evA |= 1u << p;
+        q = p;
+      }
+      t = rb_;
+      q = -1;
+      while (t) {
+        const int p = __ffs(t) - 1;
+        t &= t - 1;
+        if (q < 0 || ((qs | stc) & le_mask(p) & ~le_mask(q))) evB |= 1u << p;
+        q = p;
+      }
+    }
+    const int nA = __popc(evA), nE = nA + __popc(evB);
+    int j = sub;       // next event of this thread
+    int pu = -1, pv = -1;
+    for (int round = 0; round < 4 * CCL_MAXRUNS; ++round) {
+      const bool has = act && (pu >= 0 || j < nE);
+      if (!__any_sync(FULL, has)) break;
+      int ra = 0, rb = 0;
+      const bool from_event = has && pu < 0;
+      if (has) {
+        int u = pu, v = pv;
+        if (from_event) {
+          const bool isA = j < nA;
+          const int p = (int)__fns(isA ? evA : evB, 0, (isA ? j : j - nA) + 1);
+          u = isA ? bb + __popc(stb & le_mask(p)) : bc + __popc(stc & le_mask(p));
+          const uint32_t qq = qs & le_mask(p);
+          if (qq) {
+            const int q = 31 - __clz(qq);
+            v = ((A >> q) & 1u) ? bb + __popc(stb & le_mask(q)) : bc + __popc(stc & le_mask(q));
+          } else {
+            v = carry >= 0 ? carry : u;
+          }
+        }
+        ra = s_find(s.parent, u, cap);
+        rb = s_find(s.parent, v, cap);
+        if (ra < 0 || rb < 0) { ok = false; ra = rb = 0; }
+      }
+      const bool need = has && ra != rb;
+      const int hi = max(ra, rb), lo = min(ra, rb);
+      const unsigned long long key =
+          need ? (((unsigned long long)(unsigned)hi << 32) | (unsigned)lo) : ~0ull;
+      const unsigned peers = __match_any_sync(FULL, key);
+      const int leader = __ffs(peers) - 1;
+      int old = hi;
+      if (need && lane == leader) old = atomicMin(&s.parent[hi], lo);
+      if (has) {
+        if (from_event) j += T;
+        else pu = pv = -1;
+        if (need && lane == leader && old != hi) { pu = old; pv = lo; }
+      }
+    }
+    __syncthreads();
+    if ((2 << level) < ns) {  // flatten before the next level
+      for (int i = tid; i < nruns; i += blockDim.x) {
+        const int root = s_find(s.parent, i, cap);
+        if (root >= 0) s.parent[i] = root;
+        else ok = false;
+      }
+      __syncthreads();
+    }
+  }
+  // 4. flatten
+  for (int i = tid; i < nruns; i += blockDim.x) {
     int root = s_find(s.parent, i, cap);
     if (root < 0) { ok = false; root = i; }
     s.parent[i] = root;
   }
-  if (!ok) set_status(status, ST_INTERNAL);
+  if (!ok) set_status(status, ST_INTERNAL | RS_SUNION);
   __syncthreads();
-  // 4. seeds: components holding a pixel of mask and N phi1
+  // roots now hold their (to be minimised) representative, encoded negative
+  for (int i = tid; i < nruns; i += blockDim.x)
+    if (s.parent[i] == i) s.parent[i] = INT_MIN;
+  __syncthreads();
+  // 5. seeds: components holding a pixel of mask and N phi1
   if (phi1 != nullptr) {
     for (int r = warp; r < g.th; r += nw) {
       uint32_t z = warp_near_row(phi1, g.H, g.W, g.Wp, g.r0 + r, g.w0, lane, g.tww, conn);
-      uint32_t m = s.m[r][lane];
-      z &= m;
+      z &= s.m[r][lane];
       uint32_t zl = __shfl_up_sync(FULL, z, 1);
       if (lane == 0) zl = 0;
       uint32_t zs = z & ~((z << 1) | (zl >> 31));
       while (zs) {
-        int b = __ffs(zs) - 1;
+        const int p = __ffs(zs) - 1;
         zs &= zs - 1;
-        s.flag[s.parent[run_id(s, r, 32 * lane + b)]] = 1;
+        s.flag[root_of(s, sid(s, r >> 1, 32 * lane + p))] = 1;
       }
     }
     __syncthreads();
   }
-  // 5. components on the tile border
-  for (int r = warp; r < g.th; r += nw) {
+  // 6. components on the tile border (rows 0 and th-1, first/last column)
+  for (int k = warp; k < ns; k += nw) {
     if (lane < g.tww) {
-      uint32_t m = s.m[r][lane];
-      if (r == 0 || r == g.th - 1) {
-        uint32_t sc = s.st[r][lane];
-        while (sc) {
-          int b = __ffs(sc) - 1;
-          sc &= sc - 1;
-          int root = s.parent[run_id(s, r, 32 * lane + b)];
-          s.flag[root] |= 2;
+      for (int r = 2 * k; r <= 2 * k + 1; ++r) {
+        if (r != 0 && r != g.th - 1) continue;
+        const uint32_t m = s.m[r][lane];
+        uint32_t rs = m & ~((m << 1) | (lane > 0 ? (s.m[r][lane - 1] >> 31) : 0u));
+        while (rs) {
+          const int p = __ffs(rs) - 1;
+          rs &= rs - 1;
+          s.flag[root_of(s, sid(s, k, 32 * lane + p))] |= 2;
         }
       }
-      if (lane == 0 && (m & 1u)) s.flag[s.parent[s.base[r]]] |= 2;
-      if (lane == g.tww - 1 && (m >> 31)) s.flag[s.parent[s.base[r + 1] - 1]] |= 2;
+      const uint32_t u = s.u[k][lane];
+      if (lane == 0 && (u & 1u)) s.flag[root_of(s, s.base[k])] |= 2;
+      if (lane == g.tww - 1 && (u >> 31)) s.flag[root_of(s, s.base[k + 1] - 1)] |= 2;
+    }
+  }
+  // 7. minimum pixel of each component (for canonical labels): only strip
+  // runs in the component's first strip can hold it
+  if (min_pixel) {
+    for (int k = warp; k < ns; k += nw) {
+      if (lane >= g.tww) continue;
+      uint32_t sc = s.st[k][lane];
+      while (sc) {
+        const int p = __ffs(sc) - 1;
+        sc &= sc - 1;
+        const int x = 32 * lane + p;
+        const int S = sid(s, k, x);
+        const int R = root_of(s, S);
+        if (R < s.base[k]) continue;
+        // first pixel of the top row inside this strip run, else its start
+        int best = -1;
+        for (int ww = lane, pp = p; ww < g.tww; ++ww, pp = 0) {
+          const uint32_t from = ~(le_mask(pp) >> 1);  // bits >= pp
+          const uint32_t u = s.u[k][ww];
+          // the run ends at the first zero of u or the next run start
+          uint32_t stop = (~u | (s.st[k][ww] & ~(ww == lane ? le_mask(p) : 0u))) & from;
+          if (ww == lane) stop &= ~(1u << p);
+          const uint32_t ext = stop ? (from & ((stop & (0u - stop)) - 1u)) : from;
+          const uint32_t hit = s.m[2 * k][ww] & ext;
+          if (hit) { best = 32 * ww + __ffs(hit) - 1; break; }
+          if (stop) break;
+        }
+        const int row = best >= 0 ? 2 * k : 2 * k + 1;
+        const int col = best >= 0 ? best : x;
+        atomicMax(&s.parent[R], -((g.r0 + row) * g.W + 32 * g.w0 + col + 2));
+      }
     }
   }
   __syncthreads();
+  return true;
 }
 
-// Root of run rid after roots have been encoded (parent[root] < 0).
-VL_DEV int root_of(const CclSmem& s, int rid) {
-  int p = s.parent[rid];
-  return p >= 0 ? p : rid;
+// Per-tile storage between the local and the final pass: the encoded
+// union-find state (non-roots: their root; roots: -(representative + 2))
+// and the component flags.  The final pass rebuilds the strips from the mask
+// and reloads this instead of labelling the tile again.
+VL_DEV int ccl_tile_cap(int Wp) { return CCL_NS * min(CCL_TWW, Wp) * 32; }
+
+VL_DEV void ccl_tile_save(const CclSmem& s, int32_t* tpar, uint8_t* tflag) {
+  for (int i = threadIdx.x; i < s.nruns; i += blockDim.x) {
+    tpar[i] = s.parent[i];
+    tflag[i] = s.flag[i];
+  }
 }
-// Encoded value of the root of run rid (see ccl_encode_roots).
-VL_DEV int root_value(const CclSmem& s, int rid) {
-  int p = s.parent[rid];
+
+VL_DEV bool ccl_tile_load(CclSmem& s, const uint32_t* mask, const CclGeom& g, int conn,
+                          const int32_t* tpar, const uint8_t* tflag, int32_t* status) {
+  const int n = ccl_tile_strips(s, mask, g, conn);
+  if (n > CCL_MAXRUNS) {
+    set_status(status, ST_INTERNAL | RS_TRUNS);
+    return false;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int v = ldcg(tpar + i);
+    if (v >= n) {  // never written by a successful local pass: keep indexes in range
+      set_status(status, ST_INTERNAL | RS_TLOAD);
+      v = -2;
+    }
+    s.parent[i] = v;
+    s.flag[i] = ldcg(tflag + i);
+  }
+  __syncthreads();
+  return true;
+}
+
+// Encoded value of the root of strip run i (see ccl_encode_roots).
+VL_DEV int root_value(const CclSmem& s, int i) {
+  int p = s.parent[i];
   if (p >= 0) p = s.parent[p];
   return -p - 2;
 }
+// Value at tile pixel (row r, column x), which must be set.
+VL_DEV int pixel_value(const CclSmem& s, int r, int x) {
+  return root_value(s, sid(s, r >> 1, x));
+}
 
 // Modes of ccl_encode_roots.
-constexpr int ENC_PUBLISH = 0;  // value = root gid; publish border roots
+constexpr int ENC_PUBLISH = 0;  // value = representative; publish border roots
 constexpr int ENC_LABEL = 1;    // value = global label (border roots resolved in G)
-constexpr int ENC_SELECT = 2;   // flag bit2 = component selected (rho); value = gid
+constexpr int ENC_SELECT = 2;   // flag bit2 = component selected (rho)
 
 // Visit every local root once (at its start pixel) and replace parent[root]
-// by -(value + 2).  Block barrier at the end.
-VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, int32_t* G,
-                             uint8_t* F, int32_t* flist, int32_t* fcount,
-                             int flist_cap, int cap, int32_t* status) {
+// by -(value + 2).  The representative of a component is its minimum pixel
+// (`min_pixel`, for labels) or the first pixel of its root strip run.  Block
+// barrier at the end.
+VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, bool min_pixel, int32_t* G,
+                             uint8_t* F, int32_t* flist, int32_t* fcount, int flist_cap,
+                             int cap, int32_t* status) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  for (int r = warp; r < g.th; r += nw) {
+  const int ns = (g.th + 1) >> 1;
+  for (int k = warp; k < ns; k += nw) {
     if (lane >= g.tww) continue;
-    uint32_t sc = s.st[r][lane];
+    uint32_t sc = s.st[k][lane];
     while (sc) {
-      int b = __ffs(sc) - 1;
+      const int p = __ffs(sc) - 1;
       sc &= sc - 1;
-      int x = 32 * lane + b;
-      int rid = run_id(s, r, x);
-      if (s.parent[rid] != rid) continue;
-      int gid = (g.r0 + r) * g.W + 32 * g.w0 + x;
-      uint8_t fl = s.flag[rid];
-      int value = gid;
+      const int x = 32 * lane + p;
+      const int S = sid(s, k, x);
+      if (s.parent[S] >= 0) continue;  // not a root
+      const uint8_t fl = s.flag[S];
+      int v = min_pixel ? -s.parent[S] - 2
+                        : (g.r0 + (mbit(s, 2 * k, x) ? 2 * k : 2 * k + 1)) * g.W + 32 * g.w0 + x;
       if (mode == ENC_PUBLISH) {
         if (fl & 2) {
-          G[gid] = gid;
+          G[v] = v;
           if (F) {
-            F[gid] = fl & 1;
+            F[v] = fl & 1;
             if (fl & 1) {
-              int k = atomicAdd(fcount, 1);
-              if (k < flist_cap) flist[k] = gid;
-              else set_status(status, ST_INTERNAL);
+              const int q = atomicAdd(fcount, 1);
+              if (q < flist_cap) flist[q] = v;
+              else set_status(status, ST_INTERNAL | RS_FLIST);
             }
           }
         }
       } else if (mode == ENC_LABEL) {
-        if (fl & 2) value = g_find(G, gid, cap, status, false);
-      } else {  // ENC_SELECT
+        if (fl & 2) v = g_find(G, v, cap, status, false);
+      } else {
         uint8_t sel = fl & 1;
-        if (fl & 2) sel = ldcg(&F[g_find(G, gid, cap, status, false)]);
-        if (sel) s.flag[rid] = fl | 4;
+        if (fl & 2) sel = ldcg(&F[g_find(G, v, cap, status, false)]);
+        if (sel) s.flag[S] = fl | 4;
       }
-      s.parent[rid] = -(value + 2);
+      s.parent[S] = -(v + 2);
     }
   }
   __syncthreads();
 }
 
-// Border pixels of the tile point at their local root's gid in G.
+// Border pixels of the tile point at their component's representative in G.
 VL_DEV void ccl_publish_border(CclSmem& s, const CclGeom& g, int32_t* G) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
   const int width = 32 * g.tww;
-  for (int r = warp; r < g.th; r += nw) {
-    const int y = g.r0 + r;
-    if (r == 0 || r == g.th - 1) {
-      for (int x = lane; x < width; x += 32)
-        if (bit_at(s, r, x)) G[y * g.W + 32 * g.w0 + x] = root_value(s, run_id(s, r, x));
-    } else if (lane == 0) {
-      if (bit_at(s, r, 0)) G[y * g.W + 32 * g.w0] = root_value(s, s.base[r]);
-      int xr = width - 1;
-      if (bit_at(s, r, xr)) G[y * g.W + 32 * g.w0 + xr] = root_value(s, s.base[r + 1] - 1);
-    }
+  const int n = 2 * width + 2 * g.th;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int r, x;
+    if (i < width) { r = 0; x = i; }
+    else if (i < 2 * width) { r = g.th - 1; x = i - width; }
+    else if (i < 2 * width + g.th) { r = i - 2 * width; x = 0; }
+    else { r = i - 2 * width - g.th; x = width - 1; }
+    if (mbit(s, r, x)) G[(g.r0 + r) * g.W + 32 * g.w0 + x] = pixel_value(s, r, x);
   }
 }
 
@@ -375,8 +614,7 @@ VL_DEV void ccl_write_labels(const CclSmem& s, const CclGeom& g, int32_t* labels
   const int x_end = min(32 * g.tww, g.W - 32 * g.w0);
   for (int r = warp; r < g.th; r += nw) {
     int32_t* row = labels + (size_t)(g.r0 + r) * g.W + 32 * g.w0;
-    for (int x = lane; x < x_end; x += 32)
-      row[x] = bit_at(s, r, x) ? root_value(s, run_id(s, r, x)) : -1;
+    for (int x = lane; x < x_end; x += 32) row[x] = mbit(s, r, x) ? pixel_value(s, r, x) : -1;
   }
 }
 
@@ -384,20 +622,23 @@ VL_DEV void ccl_write_labels(const CclSmem& s, const CclGeom& g, int32_t* labels
 VL_DEV void ccl_write_select(const CclSmem& s, const CclGeom& g, uint32_t* Z) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  for (int r = warp; r < g.th; r += nw) {
+  const int ns = (g.th + 1) >> 1;
+  for (int k = warp; k < ns; k += nw) {
     if (lane >= g.tww) continue;
-    uint32_t m = s.m[r][lane], st = s.st[r][lane];
+    const uint32_t u = s.u[k][lane], st = s.st[k][lane];
     uint32_t f = 0, sc = st;
     while (sc) {
-      int b = __ffs(sc) - 1;
+      const int p = __ffs(sc) - 1;
       sc &= sc - 1;
-      if (s.flag[root_of(s, run_id(s, r, 32 * lane + b))] & 4) f |= 1u << b;
+      if (s.flag[root_of(s, sid(s, k, 32 * lane + p))] & 4) f |= 1u << p;
     }
-    if ((m & 1u) && !(st & 1u) && (s.flag[root_of(s, run_id(s, r, 32 * lane))] & 4)) f |= 1u;
-    // a carry entering at the first pixel of a run clears the run and sets
-    // the pixel after it, so ((m + f) ^ m) & m is exactly the selected runs
-    uint32_t z = ((m + f) ^ m) & m;
-    Z[(size_t)(g.r0 + r) * g.Wp + g.w0 + lane] = z;
+    // a run entering from the left word continues through bit 0
+    const uint32_t e = u & ~st;
+    const uint32_t inj = (f << 1) | ((e & 1u) && (s.flag[root_of(s, sid(s, k, 32 * lane))] & 4) ? 1u : 0u);
+    // carry through the continuation bits of each selected run
+    const uint32_t sel = f | (((e + inj) ^ e) & e);
+    for (int r = 2 * k; r <= 2 * k + 1 && r < g.th; ++r)
+      Z[(size_t)(g.r0 + r) * g.Wp + g.w0 + lane] = s.m[r][lane] & sel;
   }
 }
 
@@ -420,9 +661,22 @@ VL_DEV int g_window_hit(const uint32_t* m, int W, int Wp, int y, int x, int conn
   return -1;
 }
 
+// Unite the components of pixels a and b, skipping a pair already united by
+// this thread (border pixels hold their component representative in G, so a
+// plain read gives a key per component without a find).
+VL_DEV void merge_pair(int32_t* G, int a, int b, int& last_a, int& last_b, int cap,
+                       int32_t* status) {
+  const int ka = ldcg(&G[a]), kb = ldcg(&G[b]);
+  if (ka == kb || (ka == last_a && kb == last_b)) return;
+  last_a = ka;
+  last_b = kb;
+  g_union(G, ka, kb, cap, status);
+}
+
 VL_DEV void ccl_merge_item(const uint32_t* m, int H, int W, int Wp, int tiles_y,
                            int item, int conn, int32_t* G, int cap, int32_t* status) {
   const int nh = (tiles_y - 1) * Wp;
+  int la = -1, lb = -1;
   if (item < nh) {
     int k = item / Wp + 1, w = item - (k - 1) * Wp;
     int yd = k * CCL_TH, yu = yd - 1;
@@ -436,14 +690,14 @@ VL_DEV void ccl_merge_item(const uint32_t* m, int H, int W, int Wp, int tiles_y,
       sd &= sd - 1;
       int x = 32 * w + b;
       int p = g_window_hit(m, W, Wp, yu, x, conn);
-      if (p >= 0) g_union(G, yd * W + x, yu * W + p, cap, status);
+      if (p >= 0) merge_pair(G, yd * W + x, yu * W + p, la, lb, cap, status);
     }
     while (su) {
       int b = __ffs(su) - 1;
       su &= su - 1;
       int x = 32 * w + b;
       int p = g_window_hit(m, W, Wp, yd, x, conn);
-      if (p >= 0) g_union(G, yu * W + x, yd * W + p, cap, status);
+      if (p >= 0) merge_pair(G, yu * W + x, yd * W + p, la, lb, cap, status);
     }
   } else {
     int j = item - nh;
@@ -452,10 +706,10 @@ VL_DEV void ccl_merge_item(const uint32_t* m, int H, int W, int Wp, int tiles_y,
     if (x0 >= W) return;
     if (!bitw(m, Wp, y, x0 - 1)) return;
     int a = y * W + x0 - 1;
-    if (bitw(m, Wp, y, x0)) g_union(G, a, y * W + x0, cap, status);
+    if (bitw(m, Wp, y, x0)) merge_pair(G, a, y * W + x0, la, lb, cap, status);
     if (conn == 8) {
-      if (y > 0 && bitw(m, Wp, y - 1, x0)) g_union(G, a, (y - 1) * W + x0, cap, status);
-      if (y + 1 < H && bitw(m, Wp, y + 1, x0)) g_union(G, a, (y + 1) * W + x0, cap, status);
+      if (y > 0 && bitw(m, Wp, y - 1, x0)) merge_pair(G, a, (y - 1) * W + x0, la, lb, cap, status);
+      if (y + 1 < H && bitw(m, Wp, y + 1, x0)) merge_pair(G, a, (y + 1) * W + x0, la, lb, cap, status);
     }
   }
 }

@@ -45,16 +45,39 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
       const bool lt = (I.b & 1);
       uint32_t* d = gbuf(c, I.dst);
       const int nwords = rows * bw;
-      for (int idx = warp; idx < nwords; idx += nw) {
-        int i = i_lo + idx / bw, j = idx - (idx / bw) * bw;
-        int y = c.r0 - c.halo + i, wg = c.w0 - 1 + j;
-        uint32_t word = 0;
-        if (y >= 0 && y < c.H && wg >= 0 && wg < c.Wp) {
-          float v = __ldg(plane + (size_t)y * c.pitch + 32 * wg + lane);
-          bool p = lt ? (v < t) : (v > t);
-          word = __ballot_sync(0xFFFFFFFFu, p) & vmask(wg, c.W);
+      // one 16-byte load per lane covers 4 pixels: a warp reads 4 words
+      // (512 bytes) per load and keeps UNR loads in flight; the 8 lanes of a
+      // word merge their 4-bit pieces with three shuffles
+      constexpr int UNR = 2;
+      const int sub = lane & 7;
+      for (int base = warp * 4 * UNR; base < nwords; base += nw * 4 * UNR) {
+        float4 v[UNR];
+        uint32_t inm = 0;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          const int idx = base + 4 * u + (lane >> 3);
+          const int i = i_lo + idx / bw, wg = c.w0 - 1 + (idx - (idx / bw) * bw);
+          const int y = c.r0 - c.halo + i;
+          const bool in = idx < nwords && y >= 0 && y < c.H && wg >= 0 && wg < c.Wp;
+          v[u] = in ? __ldg(reinterpret_cast<const float4*>(plane + (size_t)y * c.pitch + 32 * wg) + sub)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          inm |= (in ? 1u : 0u) << u;
         }
-        if (lane == 0) d[i * bw + j] = word;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          uint32_t nib;
+          if (lt) nib = (v[u].x < t) | ((v[u].y < t) << 1) | ((v[u].z < t) << 2) | ((v[u].w < t) << 3);
+          else nib = (v[u].x > t) | ((v[u].y > t) << 1) | ((v[u].z > t) << 2) | ((v[u].w > t) << 3);
+          uint32_t word = nib << (4 * sub);
+          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+          const int idx = base + 4 * u + (lane >> 3);
+          if (sub == 0 && idx < nwords) {
+            const int i = i_lo + idx / bw, j = idx - (idx / bw) * bw;
+            d[i * bw + j] = ((inm >> u) & 1u) ? (word & vmask(c.w0 - 1 + j, c.W)) : 0u;
+          }
+        }
       }
     } else if (I.op == I_STORE) {
       const uint32_t* a = gbuf(c, I.a);

@@ -21,6 +21,12 @@ namespace vl {
 
 namespace {
 
+VL_DEV unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 VL_DEV int ld_acquire(const int32_t* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -65,13 +71,17 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       const CclGeom geo = ccl_geom(J.H, J.W, J.Wp, tile, J.c_tiles_x);
       const uint32_t* phi1 = J.slots[r.phi1_slot];
       const uint32_t* phi2 = J.slots[r.phi2_slot];
-      ccl_tile_label(s, phi2, phi1, geo, J.conn, J.status);
+      int32_t* tpar = J.tpar[k] + (size_t)tile * J.tile_cap;
+      uint8_t* tflag = J.tflag[k] + (size_t)tile * J.tile_cap;
       if (S.kind == SK_RZ_LOCAL) {
-        ccl_encode_roots(s, geo, ENC_PUBLISH, J.G[k], J.F[k], J.flist[k],
+        if (!ccl_tile_label(s, phi2, phi1, geo, J.conn, false, J.status)) break;
+        ccl_encode_roots(s, geo, ENC_PUBLISH, false, J.G[k], J.F[k], J.flist[k],
                          J.fcount + S.rz_off + j, J.flist_cap, cap, J.status);
         ccl_publish_border(s, geo, J.G[k]);
+        ccl_tile_save(s, tpar, tflag);
       } else {
-        ccl_encode_roots(s, geo, ENC_SELECT, J.G[k], J.F[k], nullptr, nullptr, 0, cap,
+        if (!ccl_tile_load(s, phi2, geo, J.conn, tpar, tflag, J.status)) break;
+        ccl_encode_roots(s, geo, ENC_SELECT, true, J.G[k], J.F[k], nullptr, nullptr, 0, cap,
                          J.status);
         ccl_write_select(s, geo, J.slots[r.z_slot]);
       }
@@ -114,7 +124,9 @@ __global__ void __launch_bounds__(EXEC_THREADS, 2) k_exec(ExecLaunch L) {
     const DevJob& J = L.jobs[it.job];
     const StepDesc S = J.steps[it.step];
     const int ci = J.step_base + it.step;
+    unsigned long long t_pop = 0, t_go = 0;
     if (threadIdx.x == 0) {
+      if (L.trace) t_pop = now_ns();
       int skip = 0;
       if (it.step > 0) {
         const int32_t* ctr = L.done + ci - 1;
@@ -139,6 +151,7 @@ __global__ void __launch_bounds__(EXEC_THREADS, 2) k_exec(ExecLaunch L) {
       }
       if (ldcg(J.status) != 0) skip = 1;
       s_skip = skip;
+      if (L.trace) t_go = now_ns();
     }
     __syncthreads();
     if (!s_skip) {
@@ -151,7 +164,17 @@ __global__ void __launch_bounds__(EXEC_THREADS, 2) k_exec(ExecLaunch L) {
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(L.done + ci, it.count);
+    if (threadIdx.x == 0) {
+      atomicAdd(L.done + ci, it.count);
+      if (L.trace) {
+        const unsigned long long t_end = now_ns();
+        unsigned long long* tr = L.trace + 4 * (size_t)ci;
+        atomicMin(tr + 0, t_go);
+        atomicMax(tr + 1, t_end);
+        atomicAdd(tr + 2, t_end - t_go);
+        atomicAdd(tr + 3, t_go - t_pop);
+      }
+    }
   }
 }
 

@@ -22,18 +22,39 @@ int grid_for(long long items, int per_block, int cap = 152 * 32) {
 
 // ------------------------------------------------------------ pointwise --
 
+// A lane loads 4 pixels (16 bytes); the 8 lanes of a 32-pixel word merge
+// their 4-bit pieces with three shuffles; each warp keeps two loads in flight.
 __global__ void k_threshold(const float* __restrict__ plane, int pitch, MaskGeom g,
                             float t, const float* t_dev, int lt, uint32_t* __restrict__ out) {
   if (t_dev) t = *t_dev;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, sub = lane & 7;
   const long long nwords = (long long)g.H * g.Wp;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nwords;
-       i += nwarps) {
-    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
-    const float v = __ldg(plane + (size_t)y * pitch + 32 * w + lane);
-    const uint32_t word = __ballot_sync(FULL, lt ? (v < t) : (v > t)) & vmask(w, g.W);
-    if (lane == 0) out[i] = word;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (long long base = wid * 8; base < nwords; base += nwarps * 8) {
+    float4 v[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const long long i = base + 4 * u + (lane >> 3);
+      if (i < nwords) {
+        const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+        v[u] = __ldg(reinterpret_cast<const float4*>(plane + (size_t)y * pitch + 32 * w) + sub);
+      } else {
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      uint32_t nib;
+      if (lt) nib = (v[u].x < t) | ((v[u].y < t) << 1) | ((v[u].z < t) << 2) | ((v[u].w < t) << 3);
+      else nib = (v[u].x > t) | ((v[u].y > t) << 1) | ((v[u].z > t) << 2) | ((v[u].w > t) << 3);
+      uint32_t word = nib << (4 * sub);
+      word |= __shfl_xor_sync(FULL, word, 1);
+      word |= __shfl_xor_sync(FULL, word, 2);
+      word |= __shfl_xor_sync(FULL, word, 4);
+      const long long i = base + 4 * u + (lane >> 3);
+      if (sub == 0 && i < nwords) out[i] = word & vmask((int)(i % g.Wp), g.W);
+    }
   }
 }
 
@@ -93,10 +114,13 @@ k_ccl_local(const uint32_t* mask, const uint32_t* phi1, MaskGeom g, int tiles_x,
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
   const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
   const int cap = min(g.H * g.W + 64, 1 << 22);
-  ccl_tile_label(s, mask, phi1, geo, conn, status);
-  ccl_encode_roots(s, geo, ENC_PUBLISH, sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap, cap,
-                   status);
+  const bool labels = sc.F == nullptr;  // full labelling: canonical minimum pixel
+  if (!ccl_tile_label(s, mask, phi1, geo, conn, labels, status)) return;
+  ccl_encode_roots(s, geo, ENC_PUBLISH, labels, sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap,
+                   cap, status);
   ccl_publish_border(s, geo, sc.G);
+  ccl_tile_save(s, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
+                sc.tflag + (size_t)blockIdx.x * sc.tile_cap);
 }
 
 __global__ void k_ccl_merge(const uint32_t* mask, MaskGeom g, int tiles_y, int tiles_x,
@@ -115,15 +139,17 @@ __global__ void k_ccl_flags(int32_t* G, uint8_t* F, const int32_t* flist,
 }
 
 __global__ void __launch_bounds__(EXEC_THREADS, 2)
-k_ccl_final_labels(const uint32_t* mask, MaskGeom g, int tiles_x, int conn, int32_t* labels,
+k_ccl_final_labels(const uint32_t* mask, MaskGeom g, int tiles_x, int conn, CclScratch sc,
                    int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
   const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
   const int cap = min(g.H * g.W + 64, 1 << 22);
-  ccl_tile_label(s, mask, nullptr, geo, conn, status);
-  ccl_encode_roots(s, geo, ENC_LABEL, labels, nullptr, nullptr, nullptr, 0, cap, status);
-  ccl_write_labels(s, geo, labels);
+  if (!ccl_tile_load(s, mask, geo, conn, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
+                     sc.tflag + (size_t)blockIdx.x * sc.tile_cap, status))
+    return;
+  ccl_encode_roots(s, geo, ENC_LABEL, true, sc.G, nullptr, nullptr, nullptr, 0, cap, status);
+  ccl_write_labels(s, geo, sc.G);
 }
 
 __global__ void __launch_bounds__(EXEC_THREADS, 2)
@@ -133,8 +159,10 @@ k_rz_final(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int tiles_x, 
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
   const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
   const int cap = min(g.H * g.W + 64, 1 << 22);
-  ccl_tile_label(s, phi2, phi1, geo, conn, status);
-  ccl_encode_roots(s, geo, ENC_SELECT, sc.G, sc.F, nullptr, nullptr, 0, cap, status);
+  if (!ccl_tile_load(s, phi2, geo, conn, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
+                     sc.tflag + (size_t)blockIdx.x * sc.tile_cap, status))
+    return;
+  ccl_encode_roots(s, geo, ENC_SELECT, true, sc.G, sc.F, nullptr, nullptr, 0, cap, status);
   ccl_write_select(s, geo, Z);
 }
 
@@ -177,8 +205,8 @@ __global__ void k_clear_padding(uint32_t* m, MaskGeom g) {
 cudaError_t launch_threshold(const float* plane, int pitch, MaskGeom g, float t,
                              const float* t_dev, bool lt, uint32_t* out, cudaStream_t st) {
   long long nwords = (long long)g.H * g.Wp;
-  k_threshold<<<grid_for(nwords * 32, kThreads * 4), kThreads, 0, st>>>(plane, pitch, g, t,
-                                                                       t_dev, lt, out);
+  k_threshold<<<grid_for(nwords * 4, kThreads * 4), kThreads, 0, st>>>(plane, pitch, g, t,
+                                                                      t_dev, lt, out);
   return cudaGetLastError();
 }
 
@@ -248,13 +276,19 @@ static cudaError_t ccl_set_attrs() {
   return cudaSuccess;
 }
 
-cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, int32_t* labels,
+int ccl_tile_cap_host(int Wp) { return CCL_NS * std::min(CCL_TWW, Wp) * 32; }
+
+cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScratch sc,
                               int32_t* status, cudaStream_t st) {
   cudaError_t e = ccl_set_attrs();
   if (e) return e;
   const int ty = ccl_tiles_y(g.H), tx = ccl_tiles_x(g.Wp);
   const size_t sm = sizeof(CclSmem);
-  CclScratch sc{labels, nullptr, nullptr, nullptr, 0};
+  sc.F = nullptr;
+  sc.flist = nullptr;
+  sc.fcount = nullptr;
+  sc.flist_cap = 0;
+  int32_t* labels = sc.G;
   k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, nullptr, g, tx, conn, sc, status);
   if ((e = cudaGetLastError())) return e;
   const long long nm = (long long)(ty - 1) * g.Wp + (long long)(tx - 1) * g.H;
@@ -263,7 +297,7 @@ cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, int32_
                                                              status);
     if ((e = cudaGetLastError())) return e;
   }
-  k_ccl_final_labels<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, g, tx, conn, labels, status);
+  k_ccl_final_labels<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, g, tx, conn, sc, status);
   return cudaGetLastError();
 }
 

@@ -35,14 +35,18 @@ struct CclScratch {
   int32_t* flist;   // flagged border roots, rho only
   int32_t* fcount;  // its length (zeroed by the caller before the local pass)
   int32_t flist_cap;
+  int32_t tile_cap; // per-tile capacity of tpar / tflag (ccl_tile_cap_host)
+  int32_t* tpar;    // tiles * tile_cap int32: saved tile union-find state
+  uint8_t* tflag;   // tiles * tile_cap bytes: saved tile flags
 };
 int ccl_tiles_y(int H);
 int ccl_tiles_x(int Wp);
 int ccl_flist_cap(int H, int Wp);
+int ccl_tile_cap_host(int Wp);
 size_t ccl_smem_bytes();
 
-// Labels: labels_dev doubles as the union-find array.
-cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, int32_t* labels,
+// Labels: sc.G is the labels array itself (it doubles as the union-find).
+cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScratch sc,
                               int32_t* status, cudaStream_t st);
 // Component select Z (rho core): Z = phi2-components meeting N phi1.
 cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int conn,
@@ -66,6 +70,7 @@ struct ExecLaunch {
   int32_t group_bh;        // rows per buffer (gth + 2*HMAX)
   int32_t group_bw;        // words per buffer (gtww + 2)
   int32_t grid;            // CTAs
+  unsigned long long* trace;  // optional: per (job, step) {start, end, busy, wait} in ns
 };
 size_t exec_smem_bytes(int group_buffers, int group_bh, int group_bw);
 cudaError_t exec_configure(size_t smem_bytes, int* max_ctas_per_sm);

@@ -9,11 +9,13 @@ namespace vl {
 // Bit-packed masks: Wp = 4 * ceil(W / 128) words per row, LSB first.
 static inline int words_per_row(int w) { return ((w + 127) / 128) * 4; }
 
-// Connected-component tiles: up to CCL_TH rows x CCL_TWW words (1024 px).
-// One warp owns a row, one lane a 32-px word.
+// Connected-component tiles: up to CCL_TH rows x CCL_TWW words (1024 px),
+// labelled as CCL_NS strips of two rows; one lane owns a 32-px word.
 constexpr int CCL_TH = 32;
 constexpr int CCL_TWW = 32;
-constexpr int CCL_MAXRUNS = CCL_TH * CCL_TWW * 16;  // alternating pixels
+constexpr int CCL_NS = CCL_TH / 2;
+// A strip run can start at every column under 4-adjacency (checkerboard).
+constexpr int CCL_MAXRUNS = CCL_NS * CCL_TWW * 32;
 
 constexpr int EXEC_THREADS = 512;  // threads per CTA of every tiled kernel
 constexpr int EXEC_WARPS = EXEC_THREADS / 32;
@@ -22,6 +24,14 @@ constexpr int EXEC_WARPS = EXEC_THREADS / 32;
 constexpr int ST_OK = 0;
 constexpr int ST_TIMEOUT = 6;
 constexpr int ST_INTERNAL = 8;
+// Which consistency check failed (bits 8.. of the status word, with
+// ST_INTERNAL in the low byte).
+constexpr int RS_GFIND = 1 << 8;     // global find ran past its bound
+constexpr int RS_GUNION = 2 << 8;    // global union ran past its bound
+constexpr int RS_FLIST = 3 << 8;     // flagged-root list overflow
+constexpr int RS_TLOAD = 4 << 8;     // saved tile state out of range
+constexpr int RS_TRUNS = 5 << 8;     // more strip runs than a tile holds
+constexpr int RS_SUNION = 6 << 8;    // shared union-find ran past its bound
 
 // --------------------------------------------------------- group bytecode
 // One instruction of a fused tile group.  Buffers are shared-memory tiles
@@ -120,8 +130,10 @@ struct DevJob {
   uint8_t* F[4];                //   component flags by gid
   int32_t* flist[4];            //   flagged boundary roots
   int32_t* fcount;              // flagged-root count per select (zeroed per launch)
+  int32_t* tpar[4];             //   saved tile union-find state, tiles x tile_cap
+  uint8_t* tflag[4];            //   saved tile flags
   int32_t flist_cap;
-  int32_t pad0;
+  int32_t tile_cap;
   int32_t* status;              // device status word of this job
 };
 

@@ -182,3 +182,37 @@ def test_bad_inputs_are_rejected():
         ctx.eval(G, [a, b])                    # shapes differ
     with pytest.raises(vg.VlError):
         ctx.eval(G, [a])                       # missing image
+
+
+# ------------------------------------------------------------ full sizes ---
+
+def test_config2_full_size_repeated_replays():
+    """2048 x 2048 uniform image, 2000-node random formula: the fused batch
+    replayed several times (graph replays reuse scratch memory) must keep a
+    clean status and equal the oracle on every root each time."""
+    torch = torch_cuda()
+    f = wl.random_dag(2000, seed=0)
+    rec = wl.formula_to_records(f)
+    img = wl.uniform_image(2048, 2048, seed=0)
+    exp = oracle.evaluate(rec, f.roots, [img], conn=8).masks
+    ctx = context()
+    F = ctx.compile(rec, f.roots, 8)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        im = ctx.image(img, s)
+        b = ctx.batch([(F, [im])], s)
+        for k in range(3):
+            b.run(s)
+            s.synchronize()
+            res = b.result(0)
+            assert res.status_word() == 0
+            words = np.empty((len(f.roots), 2048, 2048 // 32), dtype=np.uint32)
+            res.masks_into(words, on_device=False, stream=s)
+            got = np.unpackbits(words.view(np.uint8), axis=-1, bitorder="little")
+            for r in range(len(f.roots)):
+                if not np.array_equal(got[r], exp[r]):
+                    raise AssertionError(f"replay {k} root {r} differs")
+        plain = ctx.eval(F, [im], stream=s, mode="plain")
+        assert plain.sync() == 0
+        for r in range(0, len(f.roots), 50):
+            assert np.array_equal(plain.mask(r, s), exp[r])
