@@ -370,6 +370,34 @@ VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask,
  * on this context (VL_OK, VL_ERR_TIMEOUT, VL_ERR_INTERNAL). */
 VL_API vl_status vl_ccl_status(vl_context* ctx, void* stream);
 
+/* The same labelling for callers that cannot allocate device memory (the
+ * paper has no counterpart: this is an interface for library users).
+ * cudaMalloc synchronises the whole device, some applications reserve all
+ * device memory up front, and memory owned by another allocator must not
+ * grow behind its back; such callers pass their own buffers and this call
+ * allocates nothing, needs no context, and calls no allocating routine.
+ *   mask_dev   -- device, h * Wp packed words (layout at the top of this
+ *                 file); padding bits must be 0 (as vl_result_mask gives)
+ *   labels_dev -- device, h * w int32, written (minimum linear index per
+ *                 component, -1 background)
+ *   wait       -- 0: enqueue on `stream` and return; nonzero: wait for the
+ *                 stream and return the device status (VL_ERR_TIMEOUT,
+ *                 VL_ERR_INTERNAL) of this call
+ * Working memory is one fixed array inside the library (about 5 MiB, held
+ * by every GPU that loads the library until exit), shared by all calls on a
+ * device: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.  The
+ * array keeps the last call's contents; the call clears what must start at
+ * zero.  The first call on a device looks up the array's device address and
+ * must come before any stream capture on that device.
+ * Limit: ceil(h/32) * ceil(Wp/32) tiles of 16 * min(32, Wp) * 32 entries
+ * must fit in 2^20 entries -- any image up to 2048 x 1024 or 1024 x 2048,
+ * for example.  Larger images return VL_ERR_SHAPE; bad pointers or sizes
+ * VL_ERR_ARG. */
+VL_API vl_status vl_ccl_noalloc(const uint32_t* mask_dev, int32_t h, int32_t w,
+                                int32_t connectivity, int32_t* labels_dev,
+                                int32_t wait, void* stream);
+
 /* ----------------------------------------------------------------- serving */
 
 typedef struct {
