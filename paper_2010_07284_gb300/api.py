@@ -343,3 +343,45 @@ class Batch(_Handle):
         n, g, s = C.c_int64(), C.c_int32(), C.c_int64()
         self._check(N.load().vl_batch_info(self._ptr, C.byref(n), C.byref(g), C.byref(s)))
         return {"n_items": n.value, "grid": g.value, "smem_bytes": s.value}
+
+
+class Server(_Handle):
+    """Continuous-batching serving loop running on its own host thread."""
+
+    def __init__(self, ctx: Context, max_inflight_batches: int = 2, max_batch_jobs: int = 256,
+                 memory_budget: int = 0, batch_window_us: int = 200):
+        cfg = N.VlServerConfig()
+        cfg.max_inflight_batches = max_inflight_batches
+        cfg.max_batch_jobs = max_batch_jobs
+        cfg.memory_budget = memory_budget
+        cfg.batch_window_us = batch_window_us
+        out = C.c_void_p()
+        self.ctx = ctx
+        self._check(N.load().vl_server_create(ctx._ptr, C.byref(cfg), C.byref(out)))
+        self._ptr = out.value
+        self._keep = {}
+
+    def submit(self, formula: Formula, images: Sequence[Image]) -> int:
+        arr = (C.c_void_p * len(images))(*[im._ptr for im in images])
+        t = C.c_int64()
+        self._check(N.load().vl_server_submit(self._ptr, formula._ptr, arr, len(images), C.byref(t)))
+        self._keep[t.value] = (formula, list(images))
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """(status, Result or None); status 0 = done, ERR_BUSY = still running."""
+        out = C.c_void_p()
+        rc = N.load().vl_server_wait(self._ptr, ticket, timeout_us, C.byref(out))
+        if rc == N.ERR_BUSY:
+            return rc, None
+        keep = self._keep.pop(ticket, None)
+        res = Result(self.ctx, out.value, keep=keep) if out.value else None
+        return rc, res
+
+    def cancel(self, ticket: int) -> int:
+        return N.load().vl_server_cancel(self._ptr, ticket)
+
+    def stats(self) -> dict:
+        st = N.VlServerStats()
+        self._check(N.load().vl_server_stats_get(self._ptr, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in N.VlServerStats._fields_}

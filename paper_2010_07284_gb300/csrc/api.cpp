@@ -16,7 +16,13 @@ DevBlock::~DevBlock() {
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != device) cudaSetDevice(device);
-  cudaFreeAsync(ptr, stream);
+  if (cudaFreeAsync(ptr, stream) != cudaSuccess) {
+    // the stream is gone (its owner destroyed it): free synchronously, and
+    // leave no error behind for the caller's next check
+    cudaGetLastError();
+    cudaFree(ptr);
+    cudaGetLastError();
+  }
   if (cur != device && cur >= 0) cudaSetDevice(cur);
 }
 
@@ -48,6 +54,28 @@ cudaError_t dev_alloc(vl_context* ctx, size_t bytes, cudaStream_t st, DevBlockPt
   }
   *out = std::move(b);
   return cudaSuccess;
+}
+
+cudaError_t wait_images(vl_image* const* imgs, int n, cudaStream_t st) {
+  for (int i = 0; i < n; ++i)
+    if (imgs[i] && imgs[i]->ready && imgs[i]->ready->ev) {
+      const cudaError_t e = cudaStreamWaitEvent(st, imgs[i]->ready->ev, 0);
+      if (e) return e;
+    }
+  return cudaSuccess;
+}
+
+// Order reads of a result on `st` after the work that produced it.
+cudaError_t wait_result(const vl_result* r, cudaStream_t st) {
+  if (r->done && r->done->ev && st != r->stream) return cudaStreamWaitEvent(st, r->done->ev, 0);
+  return cudaSuccess;
+}
+
+cudaError_t record_ready(vl_image* im, cudaStream_t st) {
+  im->ready = std::make_shared<EventHolder>();
+  cudaError_t e = cudaEventCreateWithFlags(&im->ready->ev, cudaEventDisableTiming);
+  if (!e) e = cudaEventRecord(im->ready->ev, st);
+  return e;
 }
 
 }  // namespace vl
@@ -129,6 +157,7 @@ struct vl_batch {
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   int64_t bytes = 0;
+  std::vector<vl_image*> images;        // waited on before every run
   DevBlockPtr trace;                    // optional step timeline
   std::vector<int32_t> trace_meta;      // {job, step, kind} per timeline entry
 };
@@ -261,6 +290,10 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   auto b = std::make_unique<vl_batch>();
   b->ctx = ctx;
   b->n_jobs = n_jobs;
+  for (int j = 0; j < n_jobs; ++j)
+    for (int i = 0; i < jobs[j].n_images; ++i) b->images.push_back(jobs[j].images[i]);
+  std::sort(b->images.begin(), b->images.end());
+  b->images.erase(std::unique(b->images.begin(), b->images.end()), b->images.end());
   cudaError_t e = dev_alloc(ctx, trans_bytes, st, &b->trans);
   if (e) return cuda_err(ctx, e, "allocating batch tables and scratch");
   e = dev_alloc(ctx, align_up(poff, 256), st, &b->persist);
@@ -393,6 +426,8 @@ vl_status batch_run(vl_batch* b, cudaStream_t st) {
   char* tb = static_cast<char*>(b->trans->ptr);
   const bool graphs = ctx->cfg.use_graphs && st != nullptr && st != cudaStreamLegacy &&
                       st != cudaStreamPerThread;
+  if ((e = wait_images(b->images.data(), (int)b->images.size(), st)))
+    return cuda_err(ctx, e, "waiting for image uploads");
   if (b->trace) {  // timeline: start = +inf, the rest 0
     const size_t n = b->trace->bytes / 32;
     if ((e = cudaMemsetAsync(b->trace->ptr, 0, b->trace->bytes, st)) ||
@@ -467,6 +502,7 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
   const MaskGeom g{H, W, Wp};
   const size_t mask_bytes = (size_t)H * Wp * 4;
   cudaError_t e;
+  if ((e = wait_images(imgs, n_imgs, st))) return cuda_err(ctx, e, "waiting for image uploads");
   DevBlockPtr persist;
   if ((e = dev_alloc(ctx, align_up(sizeof(int32_t), 256) + mask_bytes * P.n_root_slots, st, &persist)))
     return cuda_err(ctx, e, "allocating results");
@@ -712,6 +748,7 @@ VL_API vl_status vl_image_create(vl_context* ctx, int32_t h, int32_t w, int32_t 
                         data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         S(stream));
   if (e) return cuda_err(ctx, e, "copying an image");
+  if ((e = record_ready(im.get(), S(stream)))) return cuda_err(ctx, e, "recording an event");
   *out = im.release();
   return VL_OK;
 }
@@ -740,6 +777,7 @@ VL_API vl_status vl_mask_create(vl_context* ctx, int32_t h, int32_t w, const uin
   }
   if ((e = launch_pack_u8(src, MaskGeom{h, w, im->Wp}, im->mask, S(stream))))
     return cuda_err(ctx, e, "packing a mask");
+  if ((e = record_ready(im.get(), S(stream)))) return cuda_err(ctx, e, "recording an event");
   *out = im.release();
   return VL_OK;
 }
@@ -765,6 +803,7 @@ VL_API vl_status vl_mask_create_packed(vl_context* ctx, int32_t h, int32_t w, co
     return cuda_err(ctx, e, "copying a mask");
   if ((e = launch_clear_padding(im->mask, MaskGeom{h, w, im->Wp}, S(stream))))
     return cuda_err(ctx, e, "clearing mask padding");
+  if ((e = record_ready(im.get(), S(stream)))) return cuda_err(ctx, e, "recording an event");
   *out = im.release();
   return VL_OK;
 }
@@ -1006,7 +1045,8 @@ VL_API vl_status vl_result_mask(const vl_result* r, int32_t root, uint32_t* dst,
   if (root < 0 || root >= r->n_roots) return set_err(r->ctx, VL_ERR_ARG, "root out of range");
   DeviceGuard dg(r->ctx->device);
   const size_t bytes = (size_t)r->H * r->Wp * 4;
-  cudaError_t e = cudaMemcpyAsync(dst, r->roots[root], bytes,
+  cudaError_t e = wait_result(r, S(stream));
+  if (!e) e = cudaMemcpyAsync(dst, r->roots[root], bytes,
                                   dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                   S(stream));
   if (!e && !dst_on_device) e = cudaStreamSynchronize(S(stream));
@@ -1019,7 +1059,7 @@ VL_API vl_status vl_result_masks(const vl_result* r, uint32_t* dst, int32_t dst_
   if (!valid(r, TAG_RES) || !dst) return VL_ERR_ARG;
   DeviceGuard dg(r->ctx->device);
   const size_t words = (size_t)r->H * r->Wp;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = wait_result(r, S(stream));
   for (int q = 0; q < r->n_roots && !e; ++q)
     e = cudaMemcpyAsync(dst + words * q, r->roots[q], words * 4,
                         dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S(stream));
@@ -1034,7 +1074,8 @@ VL_API vl_status vl_result_mask_u8(const vl_result* r, int32_t root, uint8_t* ds
   if (root < 0 || root >= r->n_roots) return set_err(r->ctx, VL_ERR_ARG, "root out of range");
   DeviceGuard dg(r->ctx->device);
   const MaskGeom g{r->H, r->W, r->Wp};
-  cudaError_t e;
+  cudaError_t e = wait_result(r, S(stream));
+  if (e) return cuda_err(r->ctx, e, "ordering after a result");
   if (dst_on_device) {
     if ((e = launch_unpack_u8(r->roots[root], g, dst, S(stream)))) return cuda_err(r->ctx, e, "unpacking");
     return VL_OK;
@@ -1074,7 +1115,9 @@ VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask, int32_t connectiv
   sc.tile_cap = tcap;
   sc.tpar = static_cast<int32_t*>(tmp->ptr);
   sc.tflag = static_cast<uint8_t*>(tmp->ptr) + align_up(tiles * tcap * 4, 256);
-  e = cudaMemsetAsync(ctx->ccl_status, 0, sizeof(int32_t), S(stream));
+  vl_image* mi = const_cast<vl_image*>(mask);
+  e = wait_images(&mi, 1, S(stream));
+  if (!e) e = cudaMemsetAsync(ctx->ccl_status, 0, sizeof(int32_t), S(stream));
   if (!e) e = launch_ccl_labels(mask->mask, MaskGeom{mask->H, mask->W, mask->Wp}, connectivity,
                                 sc, ctx->ccl_status, S(stream));
   if (e) return cuda_err(ctx, e, "launching connected components");

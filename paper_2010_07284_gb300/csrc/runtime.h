@@ -53,6 +53,15 @@ struct vl_context {
   std::mutex mu;      // serialises launches issued by the server thread
 };
 
+namespace vl {
+struct EventHolder {
+  cudaEvent_t ev = nullptr;
+  ~EventHolder() {
+    if (ev && cudaEventDestroy(ev) != cudaSuccess) cudaGetLastError();
+  }
+};
+}  // namespace vl
+
 struct vl_image {
   uint32_t tag = vl::TAG_IMG;
   vl_context* ctx = nullptr;
@@ -61,6 +70,7 @@ struct vl_image {
   float* data = nullptr;
   uint32_t* mask = nullptr;
   vl::DevBlockPtr block;
+  std::shared_ptr<vl::EventHolder> ready;  // recorded after the upload
 };
 
 struct vl_formula {
@@ -69,13 +79,6 @@ struct vl_formula {
   vl::PlanParams pp{};
   vl::Plan plan;
 };
-
-namespace vl {
-struct EventHolder {
-  cudaEvent_t ev = nullptr;
-  ~EventHolder() { if (ev) cudaEventDestroy(ev); }
-};
-}  // namespace vl
 
 struct vl_result {
   uint32_t tag = vl::TAG_RES;
@@ -98,6 +101,9 @@ namespace vl {
 vl_status set_err(vl_context* ctx, vl_status code, const std::string& msg);
 vl_status cuda_err(vl_context* ctx, cudaError_t e, const char* what);
 cudaError_t dev_alloc(vl_context* ctx, size_t bytes, cudaStream_t st, DevBlockPtr* out);
+// Make `st` wait until the uploads of these images are done (images may be
+// created on other streams than the one that reads them).
+cudaError_t wait_images(vl_image* const* imgs, int n, cudaStream_t st);
 
 // Build a batch (plans, tables, buffers, results) for `jobs`.
 vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStream_t st,

@@ -1,0 +1,97 @@
+"""Serving loop: queries admitted while others run on the GPU give exactly
+the masks they give alone; cancellation, rejection and a tight memory budget
+leave the other queries untouched."""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from gpu_util import context, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _pool(ctx, n=6, seed=0):
+    rng = np.random.default_rng(seed)
+    sides = [int(s) for s in rng.integers(96, 700, size=n)]
+    imgs = [wl.uniform_image(s, s + int(rng.integers(0, 300)), seed=seed + k) for k, s in enumerate(sides)]
+    return [ctx.image(im) for im in imgs]
+
+
+def _queries(ctx, handles, n, seed=0):
+    rng = np.random.default_rng(seed)
+    qs = []
+    for k in range(n):
+        size = int(np.exp(rng.uniform(np.log(10), np.log(300))))
+        f = wl.random_dag(size, seed=seed * 1000 + k, max_depth=min(500, size))
+        F = ctx.compile(wl.formula_to_records(f), f.roots, 8 if k % 3 else 4)
+        qs.append((F, handles[int(rng.integers(0, len(handles)))], len(f.roots)))
+    return qs
+
+
+def _alone(ctx, F, img, n_roots):
+    r = ctx.eval(F, [img])
+    assert r.sync() == 0
+    return [r.mask(q) for q in range(n_roots)]
+
+
+def test_results_in_the_mix_equal_results_alone():
+    torch_cuda()
+    import paper_2010_07284_gb300 as vg
+    ctx = context()
+    handles = _pool(ctx, seed=1)
+    qs = _queries(ctx, handles, 40, seed=1)
+    srv = vg.Server(ctx, max_inflight_batches=3, max_batch_jobs=8, batch_window_us=100)
+    tickets = []
+    for k, (F, img, _) in enumerate(qs):
+        tickets.append(srv.submit(F, [img]))
+        if k % 10 == 9:
+            time.sleep(0.002)   # let earlier batches start: later ones join the mix
+    for (F, img, nr), t in zip(qs, tickets):
+        st, res = srv.wait(t, timeout_us=60_000_000)
+        assert st == 0, f"ticket {t}: status {st}"
+        got = [res.mask(q) for q in range(nr)]
+        exp = _alone(ctx, F, img, nr)
+        for g, e in zip(got, exp):
+            assert np.array_equal(g, e)
+    stats = srv.stats()
+    assert stats["completed"] == len(qs)
+    assert stats["batches"] >= 2
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    srv.close()
+
+
+def test_cancel_reject_and_tight_budget():
+    torch_cuda()
+    import paper_2010_07284_gb300 as vg
+    ctx = context()
+    handles = _pool(ctx, n=3, seed=2)
+    qs = _queries(ctx, handles, 24, seed=2)
+    # a budget of one byte: only one query is admitted at a time, the rest queue
+    srv = vg.Server(ctx, max_inflight_batches=2, max_batch_jobs=4, memory_budget=1,
+                    batch_window_us=0)
+    tickets = [srv.submit(F, [img]) for F, img, _ in qs]
+    cancelled = set()
+    for t in tickets[-6:]:
+        if srv.cancel(t) == 0:
+            cancelled.add(t)
+    bad = ctx.compile([("THR_GT", -1, -1, 0, 0, 0.5, 0), ("THR_GT", -1, -1, 1, 0, 0.5, 0),
+                       ("AND", 0, 1, 0, 0, 0, 0)], [2])
+    with pytest.raises(vg.VlError):
+        srv.submit(bad, [handles[0], handles[1]])   # images of different shapes
+    for (F, img, nr), t in zip(qs, tickets):
+        st, res = srv.wait(t, timeout_us=60_000_000)
+        if t in cancelled:
+            assert st == 9  # VL_ERR_CANCELLED
+            continue
+        assert st == 0
+        exp = _alone(ctx, F, img, nr)
+        for q in range(nr):
+            assert np.array_equal(res.mask(q), exp[q])
+    stats = srv.stats()
+    assert stats["cancelled"] == len(cancelled)
+    assert stats["completed"] == len(qs) - len(cancelled)
+    srv.close()
