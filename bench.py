@@ -240,9 +240,10 @@ def main():
     ms_per_step = total_max / args.steps
 
     # roofline of the persistent executor (the only kernel of a step):
-    # algorithmic bytes of the whole DAG per launch, per the accounting of
-    # each channel read once, each materialised mask written and
-    # read back once per consumer, and 8.375 B/px per rho
+    # algorithmic bytes of the whole DAG per launch: each image channel read
+    # once, each materialised mask written once and read back once per
+    # consumer, and 8.375 B/px per rho (masks plus int32 labels written and
+    # read once)
     alg_bytes = (4.0 * P * info["n_channels_read"]
                  + P / 8.0 * (info["mask_writes"] + info["mask_reads"])
                  + P * (8.0 + 2.0 / 8.0) * info["n_selects"])
