@@ -198,6 +198,8 @@ def main():
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         image = ctx.image(dev_img, stream)
+        # the autotuner times every tile shape on this job and keeps the best
+        tune = ctx.autotune([(F, [image])], stream=stream, reps=3)
         batch = ctx.batch([(F, [image])], stream)
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         for _ in range(args.warmup):
@@ -263,7 +265,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": workload_config(world),
+            "data": "synthetic",
+            "config": dict(workload_config(world),
+                           tiles={k: tune["best"][k] for k in ("tile_rows", "tile_words", "ctas_per_sm")}),
             "gpu_launches": args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -272,7 +276,9 @@ def main():
             "clocks": clk,
             "formula": {"n_primitive": n_prim, "n_reach": info["n_reach"],
                         "n_steps": info["n_steps"], "n_groups": info["n_groups"],
-                        "n_roots": info["n_roots"]}}
+                        "n_roots": info["n_roots"]},
+            "autotune": [(t["tile_rows"], t["tile_words"], t["ctas_per_sm"], round(t["ms"], 3))
+                         for t in tune["trials"]]}
 
     if not args.no_extras:
         # ---- plain per-operator form, same workload and image

@@ -319,6 +319,46 @@ VL_API vl_status vl_batch_trace(const vl_batch* b, int64_t* out, int64_t max_ent
 VL_API vl_status vl_batch_info(const vl_batch* b, int64_t* n_items, int32_t* grid,
                                int64_t* smem_bytes);
 
+/* ---- Tile autotuning.  The paper runs one kernel per operator over whole
+ * images (Sec. 3.2) and has no tiles to tune; here the fused groups of a
+ * batch run on tiles of rows x 32-px words, and how many tiles a step has
+ * decides how well one launch fills the GPU (few large images want small
+ * tiles, thousands of small ones large tiles).  With tile_rows = tile_words
+ * = 0 in vl_config, every batch takes the shape this table gives for its
+ * signature (the set of formulas, and the number, total and largest sizes
+ * of its images, in powers of two), else a heuristic (the largest shape
+ * whose tiles per step reach the persistent grid). */
+typedef struct {
+  int32_t tile_rows;    /* rows per fused-group tile */
+  int32_t tile_words;   /* 32-px words per fused-group tile */
+  int32_t ctas_per_sm;  /* persistent CTAs per SM */
+  int32_t status;       /* VL_OK, or the status that ruled this shape out */
+  double ms;            /* mean time of one batched launch (-1: not timed) */
+} vl_tile_choice;
+
+/* Time `jobs` under every candidate tile shape and CTAs-per-SM count that
+ * fits (reps timed launches each, after one untimed launch whose device
+ * status must be VL_OK), keep the fastest in the context's table for the
+ * batch's signature and return it in *best.  trials (host, max_trials
+ * entries, may be NULL) receives every candidate; *n_trials their count.
+ * Runs on `stream` and synchronises it; the jobs' results are computed and
+ * discarded.  VL_ERR_ARG if the context has a fixed tile shape. */
+VL_API vl_status vl_autotune(vl_context* ctx, const vl_job* jobs, int32_t n_jobs, void* stream,
+                             int32_t reps, vl_tile_choice* trials, int32_t max_trials,
+                             int32_t* n_trials, vl_tile_choice* best);
+
+/* The shape vl_batch_prepare would use for `jobs` now; *tuned = 1 when it
+ * comes from a measurement (vl_autotune or vl_tune_load), 0 otherwise. */
+VL_API vl_status vl_tile_shape(vl_context* ctx, const vl_job* jobs, int32_t n_jobs,
+                               vl_tile_choice* out, int32_t* tuned);
+
+/* Write / merge the context's table of measured shapes to / from a text
+ * file (one "signature rows words ctas_per_sm ms" line per entry).  Entries
+ * are specific to the GPU model they were measured on; load refuses a file
+ * whose header names another SM count (VL_ERR_ARG). */
+VL_API vl_status vl_tune_save(vl_context* ctx, const char* path);
+VL_API vl_status vl_tune_load(vl_context* ctx, const char* path);
+
 /* Wait for the result's work and return its device status word: VL_OK,
  * VL_ERR_TIMEOUT (a bounded device wait ran out) or VL_ERR_INTERNAL. */
 VL_API vl_status vl_result_sync(vl_result* res);
@@ -388,8 +428,7 @@ VL_API vl_status vl_ccl_status(vl_context* ctx, void* stream);
  * device: calls whose work overlaps on the GPU (different streams, or
  * different host threads) race and must be serialised by the caller.  The
  * array keeps the last call's contents; the call clears what must start at
- * zero.  The first call on a device looks up the array's device address and
- * must come before any stream capture on that device.
+ * zero.
  * Limit: ceil(h/32) * ceil(Wp/32) tiles of 16 * min(32, Wp) * 32 entries
  * must fit in 2^20 entries -- any image up to 2048 x 1024 or 1024 x 2048,
  * for example.  Larger images return VL_ERR_SHAPE; bad pointers or sizes

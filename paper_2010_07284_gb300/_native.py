@@ -92,6 +92,11 @@ class VlServerStats(C.Structure):
                 ("peak_bytes", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
 
 
+class VlTileChoice(C.Structure):
+    _fields_ = [("tile_rows", C.c_int32), ("tile_words", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("status", C.c_int32), ("ms", C.c_double)]
+
+
 # (name, restype, argtypes)
 _P = C.c_void_p
 _PP = C.POINTER(C.c_void_p)
@@ -119,6 +124,12 @@ SIGNATURES = [
     ("vl_batch_result", C.c_int, [_P, _I32, _PP]),
     ("vl_batch_info", C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64)]),
     ("vl_batch_trace", C.c_int, [_P, C.POINTER(_I64), _I64, C.POINTER(_I64)]),
+    ("vl_autotune", C.c_int, [_P, C.POINTER(VlJob), _I32, _P, _I32, C.POINTER(VlTileChoice),
+                              _I32, C.POINTER(_I32), C.POINTER(VlTileChoice)]),
+    ("vl_tile_shape", C.c_int, [_P, C.POINTER(VlJob), _I32, C.POINTER(VlTileChoice),
+                                C.POINTER(_I32)]),
+    ("vl_tune_save", C.c_int, [_P, C.c_char_p]),
+    ("vl_tune_load", C.c_int, [_P, C.c_char_p]),
     ("vl_result_sync", C.c_int, [_P]),
     ("vl_result_status_word", C.c_int, [_P, C.POINTER(_I32)]),
     ("vl_result_info", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),

@@ -182,6 +182,43 @@ class Context(_Handle):
         self._check(rc)
         return Batch(self, out.value, len(jobs), keep=list(jobs))
 
+    # ---------------------------------------------------------- autotune
+    @staticmethod
+    def _choice(c) -> dict:
+        return {"tile_rows": c.tile_rows, "tile_words": c.tile_words,
+                "ctas_per_sm": c.ctas_per_sm, "status": c.status, "ms": c.ms}
+
+    def autotune(self, jobs: Sequence[Tuple["Formula", Sequence["Image"]]], stream=None,
+                 reps: int = 3) -> dict:
+        """Time every candidate tile shape on these jobs; the fastest becomes
+        the shape of later batches with the same signature."""
+        lib = N.load()
+        cj, arrs = self._jobs(jobs)
+        trials = (N.VlTileChoice * 32)()
+        n = C.c_int32()
+        best = N.VlTileChoice()
+        rc = lib.vl_autotune(self._ptr, cj, len(jobs), _stream_handle(stream), reps, trials, 32,
+                             C.byref(n), C.byref(best))
+        self._check(rc)
+        return {"best": self._choice(best),
+                "trials": [self._choice(trials[k]) for k in range(min(32, n.value))]}
+
+    def tile_shape(self, jobs: Sequence[Tuple["Formula", Sequence["Image"]]]) -> dict:
+        """The shape a batch of these jobs would use now (and whether it was measured)."""
+        cj, arrs = self._jobs(jobs)
+        out = N.VlTileChoice()
+        tuned = C.c_int32()
+        self._check(N.load().vl_tile_shape(self._ptr, cj, len(jobs), C.byref(out), C.byref(tuned)))
+        d = self._choice(out)
+        d["tuned"] = bool(tuned.value)
+        return d
+
+    def save_tuning(self, path: str) -> None:
+        self._check(N.load().vl_tune_save(self._ptr, str(path).encode()))
+
+    def load_tuning(self, path: str) -> None:
+        self._check(N.load().vl_tune_load(self._ptr, str(path).encode()))
+
     # --------------------------------------------------------------- ccl
     def ccl(self, mask: "Image", labels, conn: int = 8, stream=None) -> None:
         """Labels into a caller-owned int32 CUDA tensor of H*W elements."""

@@ -167,7 +167,7 @@ namespace vl {
 int64_t batch_bytes(const vl_batch* b) { return b ? b->bytes : 0; }
 
 vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStream_t st,
-                      vl_batch** out) {
+                      vl_batch** out, const TileShape* force) {
   if (n_jobs < 1 || !jobs) return set_err(ctx, VL_ERR_ARG, "empty batch");
   struct JobInfo {
     const Plan* P;
@@ -210,16 +210,19 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     f_rz[k] = take(sizeof(RzDesc) * std::max<size_t>(1, P->rz.size()));
     f_pct[k] = take(sizeof(PctDesc) * std::max<size_t>(1, P->pct.size()));
   }
+  const TileShape ts = force ? *force : pick_tile_shape(ctx, jobs, n_jobs);
+  if (!tile_shape_fits(ctx, ts)) return set_err(ctx, VL_ERR_ARG, "tile shape does not fit shared memory");
+  const int cps = ts.ctas_per_sm > 0 ? std::min(ts.ctas_per_sm, ctx->ctas_per_sm) : ctx->ctas_per_sm;
   int total_steps = 0, total_rz = 0;
   std::vector<WorkItem> items;
-  const int grid = std::max(1, ctx->sm_count * ctx->ctas_per_sm);
+  const int grid = std::max(1, ctx->sm_count * cps);
   for (int j = 0; j < n_jobs; ++j) {
     JobInfo& I = J[j];
     const Plan& P = *I.P;
     I.Wp = words_per_row(I.W);
     I.pitch = 32 * I.Wp;
-    I.gty = (I.H + ctx->gth - 1) / ctx->gth;
-    I.gtx = (I.Wp + ctx->gtww - 1) / ctx->gtww;
+    I.gty = (I.H + ts.rows - 1) / ts.rows;
+    I.gtx = (I.Wp + ts.words - 1) / ts.words;
     I.cty = ccl_tiles_y(I.H);
     I.ctx_ = ccl_tiles_x(I.Wp);
     I.ctiles = I.cty * I.ctx_;
@@ -321,7 +324,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     d.H = I.H; d.W = I.W; d.Wp = I.Wp; d.pitch = I.pitch;
     d.n_steps = (int)P.steps.size();
     d.step_base = I.step_base;
-    d.gth = ctx->gth; d.gtww = ctx->gtww;
+    d.gth = ts.rows; d.gtww = ts.words;
     d.g_tiles_y = I.gty; d.g_tiles_x = I.gtx;
     d.c_tiles_y = I.cty; d.c_tiles_x = I.ctx_;
     d.conn = P.conn;
@@ -379,8 +382,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   L.need = reinterpret_cast<const int32_t*>(tb + off_need);
   L.spin_limit = ctx->cfg.spin_limit != 0 ? ctx->cfg.spin_limit : (1LL << 22);
   L.group_buffers = ctx->nb;
-  L.group_bh = ctx->gth + 2 * ctx->hmax;
-  L.group_bw = ctx->gtww + 2;
+  L.group_bh = ts.rows + 2 * ctx->hmax;
+  L.group_bw = ts.words + 2;
   L.grid = std::max(1, std::min<int>(grid, (int)items.size()));
   L.trace = nullptr;
   if (ctx->cfg.trace) {
@@ -471,6 +474,18 @@ vl_status batch_release_results(vl_batch* b, vl_result** outs) {
   }
   b->results.clear();
   b->released = true;
+  return VL_OK;
+}
+
+vl_status batch_read_status(vl_batch* b, cudaStream_t st, int32_t* first_nonzero) {
+  std::vector<int32_t> w(b->n_status);
+  cudaError_t e = cudaMemcpyAsync(w.data(), b->status_base, sizeof(int32_t) * w.size(),
+                                  cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return cuda_err(b->ctx, e, "reading batch status words");
+  *first_nonzero = 0;
+  for (int32_t v : w)
+    if (v) { *first_nonzero = v; break; }
   return VL_OK;
 }
 
@@ -642,6 +657,13 @@ VL_API vl_status vl_context_create(const vl_config* cfg, vl_context** out) {
   if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  // a fixed tile shape needs both sides; with neither the autotuner picks
+  // per batch among shapes that fit the buffers sized for 32 x 32
+  if ((c->cfg.tile_rows > 0) != (c->cfg.tile_words > 0) || c->cfg.tile_rows < 0 ||
+      c->cfg.tile_words < 0 || c->cfg.tile_rows > 1024 || c->cfg.tile_words > 256) {
+    delete c;
+    return VL_ERR_ARG;
   }
   c->gth = c->cfg.tile_rows > 0 ? c->cfg.tile_rows : 32;
   c->gtww = c->cfg.tile_words > 0 ? c->cfg.tile_words : 32;
@@ -842,6 +864,7 @@ VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes, int32
   std::string err;
   int rc = compile_formula(nodes, n_nodes, roots, n_roots, connectivity, f->pp, &f->plan, &err);
   if (rc != VL_OK) return set_err(ctx, (vl_status)rc, err);
+  f->plan_hash = plan_hash(f->plan);
   *out = f.release();
   return VL_OK;
 }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -36,6 +37,12 @@ struct DevBlock {
 };
 using DevBlockPtr = std::shared_ptr<DevBlock>;
 
+// Shape of the fused-group tiles of one batch and the persistent grid:
+// rows x words (32-px words) per tile, CTAs per SM (0 = as many as fit).
+struct TileShape {
+  int rows = 32, words = 32, ctas_per_sm = 0;
+};
+
 }  // namespace vl
 
 struct vl_context {
@@ -51,6 +58,8 @@ struct vl_context {
   std::string err;
   std::mutex err_mu;  // guards err
   std::mutex mu;      // serialises launches issued by the server thread
+  std::mutex tune_mu;                       // guards tuned
+  std::map<uint64_t, vl::TileShape> tuned;  // batch signature -> measured best
 };
 
 namespace vl {
@@ -78,6 +87,7 @@ struct vl_formula {
   vl_context* ctx = nullptr;
   vl::PlanParams pp{};
   vl::Plan plan;
+  uint64_t plan_hash = 0;  // of the compiled plan: keys the tuning table
 };
 
 struct vl_result {
@@ -105,13 +115,24 @@ cudaError_t dev_alloc(vl_context* ctx, size_t bytes, cudaStream_t st, DevBlockPt
 // created on other streams than the one that reads them).
 cudaError_t wait_images(vl_image* const* imgs, int n, cudaStream_t st);
 
-// Build a batch (plans, tables, buffers, results) for `jobs`.
+// Build a batch (plans, tables, buffers, results) for `jobs`, with the tile
+// shape `force` if given, else the one pick_tile_shape chooses.
 vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStream_t st,
-                      vl_batch** out);
+                      vl_batch** out, const TileShape* force = nullptr);
+// Autotuner (autotune.cpp): the tile shape for a batch -- the fixed shape of
+// the context's configuration, else the measured best for the batch's
+// signature, else a heuristic.  *tuned is set to 1 when a measurement chose it.
+TileShape pick_tile_shape(vl_context* ctx, const vl_job* jobs, int n_jobs, int* tuned = nullptr);
+// Whether the group buffers of this shape fit the executor's shared memory.
+bool tile_shape_fits(const vl_context* ctx, const TileShape& t);
+uint64_t plan_hash(const Plan& P);
 vl_status batch_run(vl_batch* b, cudaStream_t st);
 // Hand the batch's results to the caller (they keep the batch memory alive).
 vl_status batch_release_results(vl_batch* b, vl_result** outs);
 int64_t batch_bytes(const vl_batch* b);
+// Copy the batch's status words to the host (synchronises `st`); the first
+// nonzero one, or 0, goes to *first_nonzero.
+vl_status batch_read_status(vl_batch* b, cudaStream_t st, int32_t* first_nonzero);
 void batch_destroy(vl_batch* b);
 void server_destroy(vl_server* s);
 

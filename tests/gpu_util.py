@@ -58,11 +58,11 @@ def assert_same(got, exp, what=""):
                                  f"first {bad[:6].tolist()}")
 
 
-def check_formula(records, roots, images=(), masks=(), conn=8, modes=("fused", "plain")):
+def check_formula(records, roots, images=(), masks=(), conn=8, modes=("fused", "plain"), ctx=None):
     exp = oracle.evaluate(records, roots, list(images), list(masks), conn=conn,
                           shape=(masks[0].shape if masks and not images else None)).masks
     recs = shift_mask_images(records, len(images))
     for mode in modes:
-        got, _ = gpu_eval(context(), recs, roots, images, masks, conn, mode=mode)
+        got, _ = gpu_eval(ctx or context(), recs, roots, images, masks, conn, mode=mode)
         assert_same(got, exp, f"{mode} conn={conn}")
     return exp
