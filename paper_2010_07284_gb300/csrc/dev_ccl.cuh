@@ -95,10 +95,13 @@ VL_DEV bool s_union(int32_t* par, int a, int b, int cap) {
 
 // ---------------------------------------------------------- global u-f --
 
-// Root of x in G.  With `compress`, path halving rewrites G[x] to its
-// grandparent (an ancestor, so the forest stays valid under concurrent
-// unions).  The final relabelling pass must not compress: there, entries of
-// finished tiles already hold their final labels.
+// Root of x in G.  With `compress`, every node on the path from x gets the
+// root as its parent.  This is safe because a node's parent only ever moves
+// to one of its ancestors: g_union links a node only while it is a root
+// (compare-and-swap), and nodes on the path from x, and the root found, all
+// lie on x's single chain of ancestors, the root above them (ids decrease
+// along the chain).  The final relabelling pass must not compress: there,
+// entries of finished tiles already hold their final labels.
 VL_DEV int g_find(int32_t* G, int x, int cap, int32_t* status, bool compress = true) {
   int root = x;
   int it = 0;
@@ -112,11 +115,6 @@ VL_DEV int g_find(int32_t* G, int x, int cap, int32_t* status, bool compress = t
     return root;
   }
   if (compress) {
-    // Point the path at the root.  Only nodes above the root are touched and
-    // a parent already at or below the root is left alone: parents then only
-    // ever move to ancestors with smaller ids (no cycles), and the root
-    // itself -- which a concurrent union may just have linked -- is never
-    // written.
     for (int k = 0; k < it && x > root; ++k) {
       const int p = ldcg(&G[x]);
       if (p <= root) break;
@@ -127,15 +125,20 @@ VL_DEV int g_find(int32_t* G, int x, int cap, int32_t* status, bool compress = t
   return root;
 }
 
+// Unite the sets of a and b: the larger root is linked under the smaller,
+// by compare-and-swap so that only a node that is still a root is ever
+// re-pointed.  (An atomicMin on a root that was linked meanwhile would move
+// its whole tree to the other set for a moment; a concurrent compression
+// following that fresh link could then carry a node of the other set into
+// this one and strand the rest of that set.)  A failed swap retries from
+// fresh roots.
 VL_DEV void g_union(int32_t* G, int a, int b, int cap, int32_t* status) {
   for (int it = 0; it < cap; ++it) {
     a = g_find(G, a, cap, status);
     b = g_find(G, b, cap, status);
     if (a == b) return;
     if (a < b) { int t = a; a = b; b = t; }
-    int old = atomicMin(&G[a], b);
-    if (old == a) return;
-    a = old;
+    if (atomicCAS(&G[a], a, b) == a) return;
   }
   set_status(status, ST_INTERNAL | RS_GUNION);
 }
