@@ -130,8 +130,9 @@ vl_status check_job_images(vl_context* ctx, const Plan& P, vl_image* const* imgs
 }
 
 int ccl_merge_chunks(int H, int Wp) {
-  const long long n = (long long)(ccl_tiles_y(H) - 1) * Wp + (long long)(ccl_tiles_x(Wp) - 1) * H;
-  return (int)std::max<long long>(1, (n + EXEC_THREADS - 1) / EXEC_THREADS);
+  const long long n = ccl_merge_units(H, Wp);  // one warp each
+  const int warps = EXEC_THREADS / 32;
+  return (int)std::max<long long>(1, (n + warps - 1) / warps);
 }
 int ccl_flag_chunks(int H, int Wp) {
   return std::max(1, std::min(64, ccl_tiles_y(H) * ccl_tiles_x(Wp) / 4));

@@ -646,74 +646,99 @@ VL_DEV void ccl_write_select(const CclSmem& s, const CclGeom& g, uint32_t* Z) {
 }
 
 // --------------------------------------------------------- border merge --
-// Work items of the merge: one per word of each horizontal tile border, one
-// per row of each vertical tile border.
-VL_DEV int merge_items(int H, int Wp, int tiles_y, int tiles_x) {
-  return (tiles_y - 1) * Wp + (tiles_x - 1) * H;
+// Merge units: one per word of each horizontal tile border (its 32 columns)
+// and one per 32 rows of each vertical tile border.  A warp takes a unit,
+// one lane per column (or row), so the unions of a unit run side by side
+// instead of one after another.
+VL_DEV int merge_units(int H, int Wp, int tiles_y, int tiles_x) {
+  return (tiles_y - 1) * Wp + (tiles_x - 1) * ((H + 31) >> 5);
 }
 
-VL_DEV uint32_t bitw(const uint32_t* m, int Wp, int y, int x) {
-  return (ldcg(&m[(size_t)y * Wp + (x >> 5)]) >> (x & 31)) & 1u;
+// Which of columns x-1, x, x+1 (8-adjacency) or x (4-adjacency) of a row is
+// set, leftmost first, as an offset -1/0/1 (2: none).  The row is given by
+// the words left of, at, and right of x's word (0 outside the image), and
+// b = x mod 32.
+VL_DEV int window_hit(uint32_t l, uint32_t c, uint32_t r, int b, int conn) {
+  if (conn == 8) {
+    const uint32_t left = b > 0 ? (c >> (b - 1)) & 1u : (l >> 31);
+    if (left) return -1;
+    if ((c >> b) & 1u) return 0;
+    const uint32_t right = b < 31 ? (c >> (b + 1)) & 1u : (r & 1u);
+    return right ? 1 : 2;
+  }
+  return ((c >> b) & 1u) ? 0 : 2;
 }
 
-// Leftmost foreground pixel of row y among the columns adjacent to x.
-VL_DEV int g_window_hit(const uint32_t* m, int W, int Wp, int y, int x, int conn) {
-  if (conn == 8 && x >= 1 && bitw(m, Wp, y, x - 1)) return x - 1;
-  if (bitw(m, Wp, y, x)) return x;
-  if (conn == 8 && x + 1 < W && bitw(m, Wp, y, x + 1)) return x + 1;
-  return -1;
+// Every lane offers at most one pixel pair (a, b) across a tile border.  The
+// pairs become pairs of component keys (border pixels hold their component's
+// representative in G, so a plain read gives a key without a find); equal
+// key pairs in the warp are united once, by the lowest lane holding them.
+// Must be called by the whole warp.
+VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int cap, int32_t* status) {
+  int ka = 0, kb = 0;
+  if (valid) {
+    ka = ldcg(&G[a]);
+    kb = ldcg(&G[b]);
+    valid = ka != kb;
+  }
+  const unsigned long long key =
+      valid ? (((unsigned long long)(unsigned)max(ka, kb) << 32) | (unsigned)min(ka, kb)) : ~0ull;
+  const unsigned peers = __match_any_sync(FULL, key);
+  if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) g_union(G, ka, kb, cap, status);
 }
 
-// Unite the components of pixels a and b, skipping a pair already united by
-// this thread (border pixels hold their component representative in G, so a
-// plain read gives a key per component without a find).
-VL_DEV void merge_pair(int32_t* G, int a, int b, int& last_a, int& last_b, int cap,
-                       int32_t* status) {
-  const int ka = ldcg(&G[a]), kb = ldcg(&G[b]);
-  if (ka == kb || (ka == last_a && kb == last_b)) return;
-  last_a = ka;
-  last_b = kb;
-  g_union(G, ka, kb, cap, status);
-}
-
-VL_DEV void ccl_merge_item(const uint32_t* m, int H, int W, int Wp, int tiles_y,
-                           int item, int conn, int32_t* G, int cap, int32_t* status) {
+// Unite the components that touch across the tile border of merge unit
+// `unit`.  A horizontal border is covered by checking each row-run start of
+// both border rows against the 1- or 3-pixel window of the other row: two
+// runs that touch always have a start of one run inside the other's window.
+// A vertical border pairs each set pixel left of it with the pixel right of
+// it, or, for 8-adjacency when that one is clear, with its diagonal
+// neighbours.  Must be called by the whole warp.
+VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y, int unit,
+                           int conn, int32_t* G, int cap, int32_t* status) {
+  const int lane = threadIdx.x & 31;
   const int nh = (tiles_y - 1) * Wp;
-  int la = -1, lb = -1;
-  if (item < nh) {
-    int k = item / Wp + 1, w = item - (k - 1) * Wp;
-    int yd = k * CCL_TH, yu = yd - 1;
-    uint32_t md = ldcg(&m[(size_t)yd * Wp + w]), mu = ldcg(&m[(size_t)yu * Wp + w]);
-    uint32_t mdl = w > 0 ? ldcg(&m[(size_t)yd * Wp + w - 1]) : 0u;
-    uint32_t mul = w > 0 ? ldcg(&m[(size_t)yu * Wp + w - 1]) : 0u;
-    uint32_t sd = md & ~((md << 1) | (mdl >> 31));
-    uint32_t su = mu & ~((mu << 1) | (mul >> 31));
-    while (sd) {
-      int b = __ffs(sd) - 1;
-      sd &= sd - 1;
-      int x = 32 * w + b;
-      int p = g_window_hit(m, W, Wp, yu, x, conn);
-      if (p >= 0) merge_pair(G, yd * W + x, yu * W + p, la, lb, cap, status);
+  if (unit < nh) {
+    const int k = unit / Wp + 1, w = unit - (k - 1) * Wp;
+    const int yd = k * CCL_TH, yu = yd - 1;
+    uint32_t v = 0;
+    if (lane < 6) {
+      const int ww = w - 1 + lane % 3;
+      if (ww >= 0 && ww < Wp) v = ldcg(&m[(size_t)(lane < 3 ? yu : yd) * Wp + ww]);
     }
-    while (su) {
-      int b = __ffs(su) - 1;
-      su &= su - 1;
-      int x = 32 * w + b;
-      int p = g_window_hit(m, W, Wp, yd, x, conn);
-      if (p >= 0) merge_pair(G, yu * W + x, yd * W + p, la, lb, cap, status);
-    }
+    const uint32_t mul = __shfl_sync(FULL, v, 0), mu = __shfl_sync(FULL, v, 1),
+                   mur = __shfl_sync(FULL, v, 2), mdl = __shfl_sync(FULL, v, 3),
+                   md = __shfl_sync(FULL, v, 4), mdr = __shfl_sync(FULL, v, 5);
+    const uint32_t sd = md & ~((md << 1) | (mdl >> 31));
+    const uint32_t su = mu & ~((mu << 1) | (mul >> 31));
+    const int x = 32 * w + lane;
+    int dx = (sd >> lane) & 1u ? window_hit(mul, mu, mur, lane, conn) : 2;
+    warp_unite(G, dx != 2, yd * W + x, yu * W + x + dx, cap, status);
+    dx = (su >> lane) & 1u ? window_hit(mdl, md, mdr, lane, conn) : 2;
+    warp_unite(G, dx != 2, yu * W + x, yd * W + x + dx, cap, status);
   } else {
-    int j = item - nh;
-    int k = j / H + 1, y = j - (k - 1) * H;
-    int x0 = k * CCL_TWW * 32;
-    if (x0 >= W) return;
-    if (!bitw(m, Wp, y, x0 - 1)) return;
-    int a = y * W + x0 - 1;
-    if (bitw(m, Wp, y, x0)) merge_pair(G, a, y * W + x0, la, lb, cap, status);
-    if (conn == 8) {
-      if (y > 0 && bitw(m, Wp, y - 1, x0)) merge_pair(G, a, (y - 1) * W + x0, la, lb, cap, status);
-      if (y + 1 < H && bitw(m, Wp, y + 1, x0)) merge_pair(G, a, (y + 1) * W + x0, la, lb, cap, status);
+    const int nv = (H + 31) >> 5;
+    const int j = unit - nh;
+    const int kk = j / nv + 1;
+    const int y = (j - (kk - 1) * nv) * 32 + lane;
+    const int x0 = kk * CCL_TWW * 32;  // first column right of the border (< W)
+    const int wl = (x0 - 1) >> 5, wr = x0 >> 5;
+    uint32_t L = 0, R = 0, Ru = 0, Rd = 0;
+    if (y < H) {
+      L = ldcg(&m[(size_t)y * Wp + wl]) >> 31;
+      R = ldcg(&m[(size_t)y * Wp + wr]) & 1u;
     }
+    if (conn == 8) {
+      Ru = __shfl_up_sync(FULL, R, 1);
+      Rd = __shfl_down_sync(FULL, R, 1);
+      if (lane == 0) Ru = (y > 0 && y - 1 < H) ? ldcg(&m[(size_t)(y - 1) * Wp + wr]) & 1u : 0u;
+      if (lane == 31) Rd = (y + 1 < H) ? ldcg(&m[(size_t)(y + 1) * Wp + wr]) & 1u : 0u;
+    }
+    // (lane-dependent choices go into the arguments: every lane calls)
+    const int a = y * W + x0 - 1;
+    const bool straight = R || conn == 4;
+    warp_unite(G, L && (straight ? R : Ru), a, (straight ? y : y - 1) * W + x0, cap, status);
+    warp_unite(G, L && !straight && Rd, a, (y + 1) * W + x0, cap, status);
   }
 }
 

@@ -90,9 +90,10 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
     case SK_RZ_MERGE: {
       const int j = sub / per_rz, chunk = sub - j * per_rz;
       const RzDesc r = J.rz[S.rz_off + j];
-      const int n = merge_items(J.H, J.Wp, J.c_tiles_y, J.c_tiles_x);
-      for (int i = chunk * blockDim.x + threadIdx.x; i < n; i += per_rz * blockDim.x)
-        ccl_merge_item(J.slots[r.phi2_slot], J.H, J.W, J.Wp, J.c_tiles_y, i, J.conn,
+      const int n = merge_units(J.H, J.Wp, J.c_tiles_y, J.c_tiles_x);
+      const int nw = blockDim.x >> 5;
+      for (int u = chunk * nw + (threadIdx.x >> 5); u < n; u += per_rz * nw)
+        ccl_merge_unit(J.slots[r.phi2_slot], J.H, J.W, J.Wp, J.c_tiles_y, u, J.conn,
                        J.G[r.scratch], cap, J.status);
       break;
     }

@@ -125,10 +125,11 @@ k_ccl_local(const uint32_t* mask, const uint32_t* phi1, MaskGeom g, int tiles_x,
 
 __global__ void k_ccl_merge(const uint32_t* mask, MaskGeom g, int tiles_y, int tiles_x,
                             int conn, int32_t* G, int32_t* status) {
-  const int n = merge_items(g.H, g.Wp, tiles_y, tiles_x);
+  const int n = merge_units(g.H, g.Wp, tiles_y, tiles_x);
   const int cap = min(g.H * g.W + 64, 1 << 22);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    ccl_merge_item(mask, g.H, g.W, g.Wp, tiles_y, i, conn, G, cap, status);
+  const int wpb = blockDim.x >> 5;
+  for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n; u += gridDim.x * wpb)
+    ccl_merge_unit(mask, g.H, g.W, g.Wp, tiles_y, u, conn, G, cap, status);
 }
 
 __global__ void k_ccl_flags(int32_t* G, uint8_t* F, const int32_t* flist,
@@ -276,6 +277,9 @@ static cudaError_t ccl_set_attrs() {
   return cudaSuccess;
 }
 
+long long ccl_merge_units(int H, int Wp) {
+  return (long long)(ccl_tiles_y(H) - 1) * Wp + (long long)(ccl_tiles_x(Wp) - 1) * ((H + 31) / 32);
+}
 int ccl_tile_cap_host(int Wp) { return CCL_NS * std::min(CCL_TWW, Wp) * 32; }
 
 cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScratch sc,
@@ -291,7 +295,7 @@ cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScr
   int32_t* labels = sc.G;
   k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, nullptr, g, tx, conn, sc, status);
   if ((e = cudaGetLastError())) return e;
-  const long long nm = (long long)(ty - 1) * g.Wp + (long long)(tx - 1) * g.H;
+  const long long nm = ccl_merge_units(g.H, g.Wp) * 32LL;
   if (nm > 0) {
     k_ccl_merge<<<grid_for(nm, kThreads), kThreads, 0, st>>>(mask, g, ty, tx, conn, labels,
                                                              status);
@@ -311,7 +315,7 @@ cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, in
   if ((e = cudaMemsetAsync(sc.fcount, 0, sizeof(int32_t), st))) return e;
   k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(phi2, phi1, g, tx, conn, sc, status);
   if ((e = cudaGetLastError())) return e;
-  const long long nm = (long long)(ty - 1) * g.Wp + (long long)(tx - 1) * g.H;
+  const long long nm = ccl_merge_units(g.H, g.Wp) * 32LL;
   if (nm > 0) {
     k_ccl_merge<<<grid_for(nm, kThreads), kThreads, 0, st>>>(phi2, g, ty, tx, conn, sc.G,
                                                              status);

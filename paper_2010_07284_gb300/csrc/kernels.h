@@ -43,6 +43,9 @@ int ccl_tiles_y(int H);
 int ccl_tiles_x(int Wp);
 int ccl_flist_cap(int H, int Wp);
 int ccl_tile_cap_host(int Wp);
+// Border merge units (one warp each): words of horizontal tile borders and
+// 32-row pieces of vertical ones.
+long long ccl_merge_units(int H, int Wp);
 size_t ccl_smem_bytes();
 
 // Labels: sc.G is the labels array itself (it doubles as the union-find).
