@@ -200,16 +200,29 @@ VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes,
  * those lengths.  Steps run in order; a step of kind 1 (fused group) runs
  * its instructions on every tile; kinds 2-5 are the four passes of a batch
  * of component selects (tile labelling, border merge, flag propagation,
- * final select); kind 0 computes percentiles.  Instruction opcodes: 1
- * threshold, 2 load slot, 3 not, 4 and, 5 or, 6 N, 7 constant, 8 store
- * slot, 9 and-not.  Slots: [0, n_inter) intermediates, then one per
- * distinct root, then one per mask image. */
+ * final select); kind 0 computes percentiles; kind 6 computes rank codes
+ * (below).  Instruction opcodes: 1 threshold, 2 load slot, 3 not, 4 and,
+ * 5 or, 6 N, 7 constant, 8 store slot, 9 and-not, 10 threshold by rank
+ * code.  Slots: [0, n_inter) intermediates, then one per distinct root,
+ * then one per mask image.
+ *
+ * Rank codes (an evaluation strategy, not part of the logic): when many
+ * constant thresholds read one image channel, the compiler makes a table
+ * of their distinct values t_1 < ... < t_m, and a pixel value v gets the
+ * code c = 2 * #{k : t_k < v} + [v equals some t_k] (0 for NaN).  Then
+ * v > t_k exactly when c >= 2k, and v < t_k exactly when v is not NaN and
+ * c < 2k - 1; an opcode-10 instruction holds the table (a), the bound
+ * (image, read as uint16), the code bits (channel) and the direction (b).
+ * The results are those of the strict float comparisons (Sec. 2 atoms). */
 typedef struct {
   int32_t n_steps, n_insns, n_selects, n_pct;
   int32_t n_inter_slots, n_root_slots, n_mask_slots, n_roots;
+  int32_t n_rank_tables, n_rank_values, n_rank_planes, reserved;
 } vl_plan_sizes;
 typedef struct {
   int32_t kind, insn_off, insn_cnt, halo, sel_off, sel_cnt, pct_off, pct_cnt;
+  int32_t rank_mask;  /* groups: rank tables their opcode-10 instructions read */
+  int32_t rank_halo;  /* groups: largest halo of those instructions */
 } vl_plan_step;
 typedef struct {
   uint8_t op, dst, a, b;   /* b: direction (1 = less-than) for thresholds, value for constants */
@@ -228,6 +241,16 @@ VL_API vl_status vl_formula_plan(const vl_formula* f, vl_plan_sizes* sizes,
                                  vl_plan_step* steps, vl_plan_insn* insns,
                                  vl_plan_select* selects, vl_plan_pct* pct,
                                  int32_t* root_slots, int32_t* mask_slot_images);
+
+/* Rank tables of a plan (n_rank_tables entries) and their sorted threshold
+ * values (n_rank_values floats; table k owns values [value_off, value_off +
+ * m)); planes [plane0, plane0 + nbits) hold code bits 0.., plane0 + nbits
+ * the NaN pixels.  Either array may be NULL. */
+typedef struct {
+  int32_t image, channel, m, nbits, value_off, plane0;
+} vl_plan_rank;
+VL_API vl_status vl_formula_rank_tables(const vl_formula* f, vl_plan_rank* tables,
+                                        float* values);
 
 /* Counts of a compiled formula (any pointer may be NULL):
  *   n_primitive -- primitive nodes (threshold, not, and, N, rho, constants,

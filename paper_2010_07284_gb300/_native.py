@@ -55,13 +55,16 @@ class VlFormulaStats(C.Structure):
 class VlPlanSizes(C.Structure):
     _fields_ = [("n_steps", C.c_int32), ("n_insns", C.c_int32), ("n_selects", C.c_int32),
                 ("n_pct", C.c_int32), ("n_inter_slots", C.c_int32), ("n_root_slots", C.c_int32),
-                ("n_mask_slots", C.c_int32), ("n_roots", C.c_int32)]
+                ("n_mask_slots", C.c_int32), ("n_roots", C.c_int32),
+                ("n_rank_tables", C.c_int32), ("n_rank_values", C.c_int32),
+                ("n_rank_planes", C.c_int32), ("reserved", C.c_int32)]
 
 
 class VlPlanStep(C.Structure):
     _fields_ = [("kind", C.c_int32), ("insn_off", C.c_int32), ("insn_cnt", C.c_int32),
                 ("halo", C.c_int32), ("sel_off", C.c_int32), ("sel_cnt", C.c_int32),
-                ("pct_off", C.c_int32), ("pct_cnt", C.c_int32)]
+                ("pct_off", C.c_int32), ("pct_cnt", C.c_int32),
+                ("rank_mask", C.c_int32), ("rank_halo", C.c_int32)]
 
 
 class VlPlanInsn(C.Structure):
@@ -78,6 +81,11 @@ class VlPlanSelect(C.Structure):
 class VlPlanPct(C.Structure):
     _fields_ = [("image", C.c_int16), ("channel", C.c_int16), ("slot", C.c_int16),
                 ("pad", C.c_int16), ("q", C.c_double)]
+
+
+class VlPlanRank(C.Structure):
+    _fields_ = [("image", C.c_int32), ("channel", C.c_int32), ("m", C.c_int32),
+                ("nbits", C.c_int32), ("value_off", C.c_int32), ("plane0", C.c_int32)]
 
 
 class VlServerConfig(C.Structure):
@@ -111,6 +119,7 @@ SIGNATURES = [
     ("vl_mask_create_packed", C.c_int, [_P, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_image_info", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_compile", C.c_int, [_P, C.POINTER(VlNode), _I32, C.POINTER(_I32), _I32, _I32, _PP]),
+    ("vl_formula_rank_tables", C.c_int, [_P, C.POINTER(VlPlanRank), C.POINTER(C.c_float)]),
     ("vl_formula_info", C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_stats_get", C.c_int, [_P, C.POINTER(VlFormulaStats)]),
     ("vl_formula_plan", C.c_int, [_P, C.POINTER(VlPlanSizes), C.POINTER(VlPlanStep),

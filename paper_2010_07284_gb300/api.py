@@ -281,7 +281,12 @@ class Formula(_Handle):
         masks = (C.c_int32 * max(1, sz.n_mask_slots))()
         self._check(lib.vl_formula_plan(self._ptr, C.byref(sz), steps, insns, sels, pct, roots, masks))
         rec = lambda x: {f: getattr(x, f) for f, _ in x._fields_}
+        rt = (N.VlPlanRank * max(1, sz.n_rank_tables))()
+        rv = (C.c_float * max(1, sz.n_rank_values))()
+        self._check(lib.vl_formula_rank_tables(self._ptr, rt, rv))
         return {
+            "rank_tables": [rec(rt[i]) for i in range(sz.n_rank_tables)],
+            "rank_values": np.array(rv[:sz.n_rank_values], dtype=np.float32),
             "sizes": rec(sz),
             "steps": [rec(steps[i]) for i in range(sz.n_steps)],
             "insns": [rec(insns[i]) for i in range(sz.n_insns)],

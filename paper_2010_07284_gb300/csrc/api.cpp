@@ -176,7 +176,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     int gty, gtx, cty, ctx_, ctiles;
     std::vector<int> need;
     size_t off_images, off_slotptrs, off_pct, off_slots, off_scratch[MAX_RZ_BATCH * 5];
-    size_t off_roots, off_status, off_fcount;
+    size_t off_roots, off_status, off_fcount, off_planes;
     int step_base, fcount_base;
     int flist_cap;
     int formula_idx;
@@ -203,13 +203,15 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   auto take = [&](size_t bytes, size_t a = 256) { off = align_up(off, a); size_t o = off; off += bytes; return o; };
   const size_t off_jobs = take(sizeof(DevJob) * n_jobs);
   std::vector<size_t> f_steps(formulas.size()), f_insns(formulas.size()), f_rz(formulas.size()),
-      f_pct(formulas.size());
+      f_pct(formulas.size()), f_rtab(formulas.size()), f_rvals(formulas.size());
   for (size_t k = 0; k < formulas.size(); ++k) {
     const Plan* P = formulas[k];
     f_steps[k] = take(sizeof(StepDesc) * std::max<size_t>(1, P->steps.size()));
     f_insns[k] = take(sizeof(Insn) * std::max<size_t>(1, P->insns.size()));
     f_rz[k] = take(sizeof(RzDesc) * std::max<size_t>(1, P->rz.size()));
     f_pct[k] = take(sizeof(PctDesc) * std::max<size_t>(1, P->pct.size()));
+    f_rtab[k] = take(sizeof(RankTab) * std::max<size_t>(1, P->rtab.size()));
+    f_rvals[k] = take(sizeof(float) * std::max<size_t>(1, P->rvals.size()));
   }
   const TileShape ts = force ? *force : pick_tile_shape(ctx, jobs, n_jobs);
   if (!tile_shape_fits(ctx, ts)) return set_err(ctx, VL_ERR_ARG, "tile shape does not fit shared memory");
@@ -240,6 +242,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
         case SK_RZ_LOCAL: case SK_RZ_FINAL: n = s.rz_cnt * I.ctiles; break;
         case SK_RZ_MERGE: n = s.rz_cnt * ccl_merge_chunks(I.H, I.Wp); break;
         case SK_RZ_FLAGS: n = s.rz_cnt * ccl_flag_chunks(I.H, I.Wp); break;
+        case SK_RANK: n = (int)P.rtab.size() * ((I.H + RANK_ROWS - 1) / RANK_ROWS); break;
       }
       I.need.push_back(std::max(1, n));
     }
@@ -272,6 +275,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     const size_t mask_bytes = (size_t)I.H * I.Wp * 4;
     const size_t P_px = (size_t)I.H * I.W;
     I.off_pct = take(sizeof(float) * std::max(1, P.n_pct_slots));
+    I.off_planes = take(mask_bytes * P.n_planes);
     I.off_slots = take(mask_bytes * P.n_inter_slots);
     const size_t tstate = (size_t)I.ctiles * ccl_tile_cap_host(I.Wp);
     for (int k = 0; k < P.max_rz_batch; ++k) {
@@ -313,6 +317,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     if (!P->insns.empty()) std::memcpy(&host[f_insns[k]], P->insns.data(), sizeof(Insn) * P->insns.size());
     if (!P->rz.empty()) std::memcpy(&host[f_rz[k]], P->rz.data(), sizeof(RzDesc) * P->rz.size());
     if (!P->pct.empty()) std::memcpy(&host[f_pct[k]], P->pct.data(), sizeof(PctDesc) * P->pct.size());
+    if (!P->rtab.empty()) std::memcpy(&host[f_rtab[k]], P->rtab.data(), sizeof(RankTab) * P->rtab.size());
+    if (!P->rvals.empty()) std::memcpy(&host[f_rvals[k]], P->rvals.data(), sizeof(float) * P->rvals.size());
   }
   DevJob* hj = reinterpret_cast<DevJob*>(&host[off_jobs]);
   int32_t* hneed = reinterpret_cast<int32_t*>(&host[off_need]);
@@ -351,6 +357,10 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     d.rz = reinterpret_cast<const RzDesc*>(tb + f_rz[k]);
     d.pct = reinterpret_cast<const PctDesc*>(tb + f_pct[k]);
     d.pct_val = reinterpret_cast<float*>(tb + I.off_pct);
+    d.rtab = reinterpret_cast<const RankTab*>(tb + f_rtab[k]);
+    d.rvals = reinterpret_cast<const float*>(tb + f_rvals[k]);
+    d.n_rtab = (int32_t)P.rtab.size();
+    d.planes = reinterpret_cast<uint32_t*>(tb + I.off_planes);
     for (int s = 0; s < P.max_rz_batch; ++s) {
       d.G[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[5 * s + 0]);
       d.F[s] = reinterpret_cast<uint8_t*>(tb + I.off_scratch[5 * s + 1]);
@@ -386,6 +396,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   L.group_bh = ts.rows + 2 * ctx->hmax;
   L.group_bw = ts.words + 2;
   L.grid = std::max(1, std::min<int>(grid, (int)items.size()));
+  L.smem_bytes = (int32_t)ctx->exec_smem;
   L.trace = nullptr;
   if (ctx->cfg.trace) {
     e = dev_alloc(ctx, sizeof(unsigned long long) * 4 * std::max(1, total_steps), st, &b->trace);
@@ -676,6 +687,19 @@ VL_API vl_status vl_context_create(const vl_config* cfg, vl_context** out) {
   c->pp.group_buffers = c->nb;
   c->pp.hmax = c->hmax;
   c->exec_smem = exec_smem_bytes(c->nb, bh, bw);
+  {
+    // room beside the group buffers for staging rank planes, as long as two
+    // CTAs still fit on an SM
+    int smem_sm = 0, reserved = 0, optin = 0;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device) ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, c->device) ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device)) {
+      cudaGetLastError();
+    } else {
+      const size_t two = ((size_t)(smem_sm / 2 - reserved)) & ~(size_t)15;
+      if (two > c->exec_smem && two <= (size_t)optin) c->exec_smem = two;
+    }
+  }
   if ((e = exec_configure(c->exec_smem, &c->ctas_per_sm))) { delete c; cudaGetLastError(); return VL_ERR_CUDA; }
   if (c->ctas_per_sm < 1) c->ctas_per_sm = 1;
   if ((e = cudaMalloc(&c->ccl_status, sizeof(int32_t)))) { delete c; cudaGetLastError(); return VL_ERR_OOM; }
@@ -884,6 +908,10 @@ VL_API vl_status vl_formula_plan(const vl_formula* f, vl_plan_sizes* sizes, vl_p
     sizes->n_root_slots = P.n_root_slots;
     sizes->n_mask_slots = P.n_mask_slots;
     sizes->n_roots = P.n_roots;
+    sizes->n_rank_tables = (int32_t)P.rtab.size();
+    sizes->n_rank_values = (int32_t)P.rvals.size();
+    sizes->n_rank_planes = P.n_planes;
+    sizes->reserved = 0;
   }
   static_assert(sizeof(vl_plan_step) == sizeof(StepDesc), "step layout");
   static_assert(sizeof(vl_plan_insn) == sizeof(Insn), "insn layout");
@@ -896,6 +924,16 @@ VL_API vl_status vl_formula_plan(const vl_formula* f, vl_plan_sizes* sizes, vl_p
   if (root_slots) for (int r = 0; r < P.n_roots; ++r) root_slots[r] = P.root_slot[r];
   if (mask_slot_images)
     for (int k = 0; k < P.n_mask_slots; ++k) mask_slot_images[k] = P.mask_slot_image[k];
+  return VL_OK;
+}
+
+VL_API vl_status vl_formula_rank_tables(const vl_formula* f, vl_plan_rank* tables,
+                                        float* values) {
+  if (!valid(f, TAG_FML)) return VL_ERR_ARG;
+  static_assert(sizeof(vl_plan_rank) == sizeof(RankTab), "rank table layout");
+  const Plan& P = f->plan;
+  if (tables && !P.rtab.empty()) std::memcpy(tables, P.rtab.data(), sizeof(RankTab) * P.rtab.size());
+  if (values && !P.rvals.empty()) std::memcpy(values, P.rvals.data(), sizeof(float) * P.rvals.size());
   return VL_OK;
 }
 
@@ -1023,7 +1061,7 @@ VL_API vl_status vl_batch_info(const vl_batch* b, int64_t* n_items, int32_t* gri
   if (!valid(b, TAG_BAT)) return VL_ERR_ARG;
   if (n_items) *n_items = b->L.n_items;
   if (grid) *grid = b->L.grid;
-  if (smem) *smem = (int64_t)exec_smem_bytes(b->L.group_buffers, b->L.group_bh, b->L.group_bw);
+  if (smem) *smem = (int64_t)b->L.smem_bytes;
   return VL_OK;
 }
 

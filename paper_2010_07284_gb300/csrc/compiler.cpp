@@ -579,6 +579,60 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
     for (int k = off; k < off + cnt; ++k) P.insns.push_back(pins[k].in);
     P.max_group_halo = std::max(P.max_group_halo, halo);
   }
+  // ---- 5. rank codes.  A channel read by many constant thresholds gets a
+  // table of its distinct thresholds; its thresholds become comparisons of
+  // the pixels' rank codes (one pass over the floats per formula instead of
+  // one per threshold and tile).  Thresholds from percentiles stay direct.
+  {
+    std::map<std::pair<int, int>, std::vector<float>> by_ch;
+    for (const Insn& in : P.insns)
+      if (in.op == I_THR && in.slot < 0 && !std::isnan(in.t)) by_ch[{in.img, in.ch}].push_back(in.t);
+    std::map<std::pair<int, int>, int> tab_of;
+    for (auto& kv : by_ch) {
+      if ((int)kv.second.size() < kRankMinThresholds || (int)P.rtab.size() >= kRankMaxTables) continue;
+      std::vector<float> v = kv.second;
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end(), [](float x, float y) { return x == y; }), v.end());
+      if ((int)v.size() > kRankMaxValues) continue;
+      RankTab t{};
+      t.img = kv.first.first;
+      t.ch = kv.first.second;
+      t.m = (int)v.size();
+      t.nbits = 0;
+      for (unsigned c = 2u * (unsigned)t.m + 1u; c; c >>= 1) t.nbits++;
+      t.val_off = (int)P.rvals.size();
+      t.plane0 = P.n_planes;
+      P.n_planes += t.nbits + 1;
+      P.rvals.insert(P.rvals.end(), v.begin(), v.end());
+      tab_of[kv.first] = (int)P.rtab.size();
+      P.rtab.push_back(t);
+    }
+    for (StepDesc& s : P.steps) {
+      if (s.kind != SK_GROUP) continue;
+      for (int k = s.insn_off; k < s.insn_off + s.insn_cnt; ++k) {
+        Insn& in = P.insns[k];
+        if (in.op != I_THR || in.slot >= 0 || std::isnan(in.t)) continue;
+        auto it = tab_of.find({in.img, in.ch});
+        if (it == tab_of.end()) continue;
+        const RankTab& t = P.rtab[it->second];
+        const float* v = P.rvals.data() + t.val_off;
+        const int pos = (int)(std::lower_bound(v, v + t.m, in.t) - v);  // v[pos] == t
+        const int kk = pos + 1;
+        const bool lt = in.b & 1;
+        in.op = I_RTHR;
+        in.a = (uint8_t)it->second;
+        in.img = (int16_t)(lt ? 2 * kk - 1 : 2 * kk);
+        in.ch = (int16_t)t.nbits;
+        s.rank_mask |= 1 << it->second;
+        s.rank_halo = std::max(s.rank_halo, (int)in.h);
+      }
+    }
+    if (!P.rtab.empty()) {
+      StepDesc r{};
+      r.kind = SK_RANK;
+      P.steps.insert(P.steps.begin(), r);
+    }
+  }
   for (RzDesc& r : P.rz) {
     r.phi1_slot = (int16_t)slot_of[r.phi1_slot];
     r.phi2_slot = (int16_t)slot_of[r.phi2_slot];

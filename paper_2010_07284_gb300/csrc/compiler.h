@@ -57,11 +57,22 @@ struct Plan {
   std::vector<int> img_kind;
   std::vector<int> img_channels;  // channels needed (max channel + 1)
   PlanParams params{};
+  // rank codes (see RankTab): tables, their sorted values, planes per job
+  std::vector<RankTab> rtab;
+  std::vector<float> rvals;
+  int n_planes = 0;
   // accounting: primitive op counts by kind (threshold, not, and, N, rho, other)
   int64_t n_thr = 0, n_not = 0, n_and = 0, n_near = 0, n_other = 0;
 };
 
 constexpr int MAX_RZ_BATCH = 4;
+// Rank codes: a channel gets a table when at least this many constant
+// thresholds read it; tables hold at most kRankMaxValues values (codes fit
+// 14 bits) and a formula at most kRankMaxTables tables (one bit each in a
+// group's rank_mask).
+constexpr int kRankMinThresholds = 4;
+constexpr int kRankMaxValues = 8191;
+constexpr int kRankMaxTables = 32;
 
 // Returns VL_OK or an error code with a message in *err.
 int compile_formula(const vl_node* nodes, int n_nodes, const int32_t* roots, int n_roots,

@@ -25,7 +25,57 @@ struct GroupCtx {
   const DevImage* images;
   uint32_t* const* slots;
   const float* pct_val;
+  // rank codes (I_RTHR): tables, the job's planes, and a shared-memory
+  // stage beside the buffers for the planes of the group's tables
+  const RankTab* rtab;
+  const uint32_t* planes;
+  size_t pstride;       // words per plane (H * Wp)
+  uint32_t* stage;
+  int stage_cap;        // words
+  int rank_mask, rank_halo;
 };
+
+VL_DEV void cp_async4(uint32_t* smem_dst, const uint32_t* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+VL_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+VL_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Words of the stage that the planes of the group's rank tables take (rows
+// of the core tile plus rank_halo above and below, all buffer words).
+VL_DEV int rank_stage_words(const GroupCtx& c, int upto_table) {
+  const int per_plane = (c.th + 2 * c.rank_halo) * c.bw;
+  int n = 0;
+  for (unsigned m = (unsigned)c.rank_mask; m; m &= m - 1) {
+    const int t = __ffs(m) - 1;
+    if (t >= upto_table) break;
+    n += (c.rtab[t].nbits + 1) * per_plane;
+  }
+  return n;
+}
+
+// Start copying the planes of the group's rank tables into the stage (each
+// thread its share of words, asynchronously); returns whether they fit.
+VL_DEV bool rank_stage_begin(const GroupCtx& c) {
+  if (!c.rank_mask || rank_stage_words(c, 32) > c.stage_cap) return false;
+  const int rows_s = c.th + 2 * c.rank_halo;
+  const int per_plane = rows_s * c.bw;
+  uint32_t* dst = c.stage;
+  for (unsigned m = (unsigned)c.rank_mask; m; m &= m - 1) {
+    const RankTab T = c.rtab[__ffs(m) - 1];
+    for (int p = 0; p <= T.nbits; ++p, dst += per_plane) {
+      const uint32_t* src = c.planes + (size_t)(T.plane0 + p) * c.pstride;
+      for (int idx = threadIdx.x; idx < per_plane; idx += blockDim.x) {
+        const int i = idx / c.bw, j = idx - (idx / c.bw) * c.bw;
+        const int y = c.r0 - c.rank_halo + i, wg = c.w0 - 1 + j;
+        if (y >= 0 && y < c.H && wg >= 0 && wg < c.Wp) cp_async4(dst + idx, src + (size_t)y * c.Wp + wg);
+      }
+    }
+  }
+  cp_async_commit();
+  return true;
+}
 
 VL_DEV uint32_t* gbuf(const GroupCtx& c, int b) { return c.buf + (size_t)b * c.bh * c.bw; }
 
@@ -33,12 +83,58 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   const int bw = c.bw;
+  // 0: planes read from global memory; 1: being staged; 2: staged
+  int stage = rank_stage_begin(c) ? 1 : 0;
   for (int k = 0; k < n_insn; ++k) {
     const Insn I = insns[k];
     const int h = I.h;
     const int i_lo = c.halo - h, i_hi = c.halo + c.th + h;  // buffer rows
     const int rows = i_hi - i_lo;
-    if (I.op == I_THR) {
+    if (I.op == I_RTHR) {
+      if (stage == 1) {  // uniform: every thread waits for its copies, then all
+        cp_async_wait_all();
+        __syncthreads();
+        stage = 2;
+      }
+      const RankTab T = c.rtab[I.a];
+      const int nb = I.ch;
+      const unsigned K = (uint16_t)I.img;
+      const bool lt = I.b & 1;
+      const int per_plane = (c.th + 2 * c.rank_halo) * bw;
+      const uint32_t* sp = c.stage + rank_stage_words(c, I.a);
+      const int s_row0 = c.halo - c.rank_halo;  // buffer row of stage row 0
+      uint32_t* d = gbuf(c, I.dst);
+      const int nwords = rows * bw;
+      for (int idx = tid; idx < nwords; idx += nthr) {
+        const int i = i_lo + idx / bw, j = idx - (idx / bw) * bw;
+        const int y = c.r0 - c.halo + i, wg = c.w0 - 1 + j;
+        uint32_t word = 0;
+        if (y >= 0 && y < c.H && wg >= 0 && wg < c.Wp) {
+          const uint32_t* s0 = sp + (size_t)(i - s_row0) * bw + j;
+          const uint32_t* g0 = c.planes + (size_t)T.plane0 * c.pstride + (size_t)y * c.Wp + wg;
+          // bit-sliced c >= K over the code planes, most significant first
+          uint32_t gt = 0, eq = 0xFFFFFFFFu;
+          for (int b = nb - 1; b >= 0; --b) {
+            const uint32_t pw = stage ? s0[(size_t)b * per_plane] : ldcg(g0 + (size_t)b * c.pstride);
+            if ((K >> b) & 1u) {
+              eq &= pw;
+            } else {
+              gt |= eq & pw;
+              eq &= ~pw;
+            }
+          }
+          const uint32_t ge = gt | eq;
+          if (lt) {
+            const uint32_t nan = stage ? s0[(size_t)nb * per_plane] : ldcg(g0 + (size_t)nb * c.pstride);
+            word = ~ge & ~nan;
+          } else {
+            word = ge;
+          }
+          word &= vmask(wg, c.W);
+        }
+        d[i * bw + j] = word;
+      }
+    } else if (I.op == I_THR) {
       const DevImage im = c.images[I.img];
       const float* plane = im.data + (size_t)I.ch * c.H * c.pitch;
       const float t = (I.slot >= 0) ? c.pct_val[I.slot] : I.t;
@@ -122,6 +218,7 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
     }
     __syncthreads();
   }
+  if (stage == 1) cp_async_wait_all();  // no copy may outlive the tile
 }
 
 }  // namespace vl

@@ -33,6 +33,37 @@ VL_DEV int ld_acquire(const int32_t* p) {
   return v;
 }
 
+// Rank codes of rows [y0, y1) of one channel against the sorted table tv
+// (see RankTab): one warp per 32-pixel word, one lane per pixel; code bit b
+// of the word's pixels is a ballot, written to plane b (lane b writes it).
+VL_DEV void rank_rows(const float* tv, const RankTab& T, const float* plane, int H, int W,
+                      int Wp, int pitch, int y0, int y1, uint32_t* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const size_t pstride = (size_t)H * Wp;
+  const int nwords = (y1 - y0) * Wp;
+  for (int idx = warp; idx < nwords; idx += nw) {
+    const int y = y0 + idx / Wp, w = idx - (idx / Wp) * Wp;
+    const int x = 32 * w + lane;
+    const bool in = x < W;
+    const float v = in ? plane[(size_t)y * pitch + x] : 0.f;
+    int lo = 0, hi = T.m;  // thresholds below v (none for NaN)
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (tv[mid] < v) lo = mid + 1;
+      else hi = mid;
+    }
+    const unsigned code = 2u * (unsigned)lo + ((lo < T.m && tv[lo] == v) ? 1u : 0u);
+    uint32_t mine = 0;
+    for (int b = 0; b < T.nbits; ++b) {
+      const uint32_t word = __ballot_sync(FULL, in && ((code >> b) & 1u));
+      if (lane == b) mine = word;
+    }
+    const uint32_t nan = __ballot_sync(FULL, in && v != v);
+    if (lane == T.nbits) mine = nan;
+    if (lane <= T.nbits) out[(size_t)lane * pstride + (size_t)y * Wp + w] = mine;
+  }
+}
+
 VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
                         unsigned char* smem, const ExecLaunch& L) {
   const int cap = min(J.H * J.W + 64, 1 << 22);
@@ -59,7 +90,23 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       c.conn = J.conn;
       c.buf = reinterpret_cast<uint32_t*>(smem);
       c.images = J.images; c.slots = J.slots; c.pct_val = J.pct_val;
+      c.rtab = J.rtab; c.planes = J.planes; c.pstride = (size_t)J.H * J.Wp;
+      c.stage = c.buf + (size_t)L.group_buffers * c.bh * c.bw;
+      c.stage_cap = L.smem_bytes / 4 - L.group_buffers * c.bh * c.bw;
+      c.rank_mask = S.rank_mask; c.rank_halo = S.rank_halo;
       group_tile(c, J.insns + S.insn_off, S.insn_cnt);
+      break;
+    }
+    case SK_RANK: {
+      const int per_tab = (J.H + RANK_ROWS - 1) / RANK_ROWS;
+      const int tab = sub / per_tab, rb = sub - tab * per_tab;
+      const RankTab T = J.rtab[tab];
+      float* tv = reinterpret_cast<float*>(smem);
+      for (int i = threadIdx.x; i < T.m; i += blockDim.x) tv[i] = J.rvals[T.val_off + i];
+      __syncthreads();
+      rank_rows(tv, T, J.images[T.img].data + (size_t)T.ch * J.H * J.pitch, J.H, J.W, J.Wp,
+                J.pitch, rb * RANK_ROWS, min(J.H, (rb + 1) * RANK_ROWS),
+                J.planes + (size_t)T.plane0 * J.H * J.Wp);
       break;
     }
     case SK_RZ_LOCAL:
@@ -198,8 +245,7 @@ cudaError_t exec_configure(size_t smem_bytes, int* max_ctas_per_sm) {
 }
 
 cudaError_t launch_exec(const ExecLaunch& L, cudaStream_t st) {
-  const size_t sm = exec_smem_bytes(L.group_buffers, L.group_bh, L.group_bw);
-  k_exec<<<L.grid, EXEC_THREADS, sm, st>>>(L);
+  k_exec<<<L.grid, EXEC_THREADS, (size_t)L.smem_bytes, st>>>(L);
   return cudaGetLastError();
 }
 

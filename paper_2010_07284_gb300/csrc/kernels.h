@@ -73,6 +73,8 @@ struct ExecLaunch {
   int32_t group_bh;        // rows per buffer (gth + 2*HMAX)
   int32_t group_bw;        // words per buffer (gtww + 2)
   int32_t grid;            // CTAs
+  int32_t smem_bytes;      // dynamic shared memory per CTA (groups stage rank
+                           // planes in what their buffers leave free)
   unsigned long long* trace;  // optional: per (job, step) {start, end, busy, wait} in ns
 };
 size_t exec_smem_bytes(int group_buffers, int group_bh, int group_bw);

@@ -49,6 +49,8 @@ enum InsnOp : uint8_t {
   I_CONST = 7,   // dst = all-false (aux 0) or all-true (aux 1)
   I_STORE = 8,   // materialised mask slot `slot` = a   (core region only)
   I_ANDNOT = 9,  // dst = a and not b
+  I_RTHR = 10,   // dst = threshold by rank code: table a, code bound K = img
+                 //   (as uint16), planes = ch; aux bit0: lt (see RankTab)
 };
 
 struct Insn {        // 16 bytes
@@ -72,7 +74,11 @@ enum StepKind : int32_t {
   SK_RZ_MERGE = 3,   // rho batch, union across tile borders: item = (rz, chunk)
   SK_RZ_FLAGS = 4,   // rho batch, flags to global roots: item = (rz, chunk)
   SK_RZ_FINAL = 5,   // rho batch, relabel + write Z: item = (rz, tile)
+  SK_RANK = 6,       // rank codes of threshold tables: item = (table, row block)
 };
+
+// Rows of one rank-code work item.
+constexpr int RANK_ROWS = 8;
 
 struct StepDesc {
   int32_t kind;
@@ -83,6 +89,23 @@ struct StepDesc {
   int32_t rz_cnt;
   int32_t pct_off;   // percentile step: first PCT entry
   int32_t pct_cnt;
+  int32_t rank_mask; // groups: rank tables (< 32) its I_RTHR read, one bit each
+  int32_t rank_halo; // groups: largest halo of those I_RTHR
+};
+
+// Rank codes of one image channel against the sorted distinct constant
+// thresholds t_1 < ... < t_m of a formula on that channel: a pixel value v
+// has code c = 2 * #{k : t_k < v} + [v equals some t_k] (0 for NaN), kept
+// as `nbits` bit planes (bit b of every pixel's code in plane plane0 + b)
+// plus a plane of NaN pixels (plane0 + nbits).  Then v > t_k exactly when
+// c >= 2k, and v < t_k exactly when c < 2k - 1 and v is not NaN, so every
+// threshold of the table becomes one bit-sliced comparison with a constant.
+struct RankTab {
+  int32_t img, ch;
+  int32_t m;         // thresholds in the table
+  int32_t nbits;     // code bits: bit length of 2m + 1
+  int32_t val_off;   // first threshold value in the formula's value array
+  int32_t plane0;    // first plane of the table in the job's plane array
 };
 
 // Component select Z = union of phi2-components meeting N phi1 (the core of
@@ -135,6 +158,11 @@ struct DevJob {
   int32_t flist_cap;
   int32_t tile_cap;
   int32_t* status;              // device status word of this job
+  const RankTab* rtab;          // rank tables of the formula
+  const float* rvals;           //   their sorted threshold values
+  int32_t n_rtab;
+  int32_t pad_;
+  uint32_t* planes;             // rank-code planes, H x Wp words each
 };
 
 // One work item of the persistent executor: a range of `count` consecutive

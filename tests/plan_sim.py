@@ -99,6 +99,16 @@ def simulate(plan: dict, images, masks_by_image: dict, conn: int, seed: int = 0,
                             t = pct[ins["slot"]] if ins["slot"] >= 0 else np.float32(ins["t"])
                             v = ch[rr][:, cc]
                             val = (v < t) if ins["b"] & 1 else (v > t)
+                        elif op == 10:  # threshold by rank code
+                            tab = plan["rank_tables"][ins["a"]]
+                            vals = plan["rank_values"][tab["value_off"]:tab["value_off"] + tab["m"]]
+                            v = images[tab["image"]][tab["channel"]][rr][:, cc]
+                            nan = np.isnan(v)
+                            below = np.searchsorted(vals, np.where(nan, 0, v), side="left")
+                            hit = vals[np.minimum(below, tab["m"] - 1)] == v
+                            code = np.where(nan, 0, 2 * below + ((below < tab["m"]) & hit))
+                            ge = code >= (ins["image"] & 0xFFFF)
+                            val = (~ge & ~nan) if ins["b"] & 1 else ge
                         elif op == 2:
                             src = slots[ins["slot"]]
                             if src is GARB:

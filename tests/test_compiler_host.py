@@ -145,3 +145,68 @@ def test_plan_mask_atoms_constants_and_mask_root():
     f = wl.Formula([wl.Node(*n) for n in nodes], [4, 0, 6, 7, 8, 3])
     for conn in (4, 8):
         _check_sim(f, [None, None], masks={0: m0, 1: m1}, conn=conn)
+
+
+# ------------------------------------------------------------- rank codes
+
+def test_rank_tables_encode_every_constant_threshold():
+    """Every constant threshold of a channel read by many becomes a rank
+    comparison whose bound points back at its own value in the table."""
+    f = wl.random_dag(2000, seed=0)
+    plan = vg.compile_formula(_rec(f), f.roots, 8).plan()
+    tabs, vals = plan["rank_tables"], plan["rank_values"]
+    assert len(tabs) == 1 and plan["steps"][0]["kind"] == 6
+    t = tabs[0]
+    v = vals[t["value_off"]:t["value_off"] + t["m"]]
+    assert np.all(np.diff(v) > 0)                       # sorted, distinct
+    assert t["nbits"] == int(2 * t["m"] + 1).bit_length()
+    thr = [n.t for n in f.nodes if n.op in ("THR_GT", "THR_LT")]
+    used = set()
+    n_rank = 0
+    for s in plan["steps"]:
+        if s["kind"] != 1:
+            continue
+        for ins in plan["insns"][s["insn_off"]:s["insn_off"] + s["insn_cnt"]]:
+            assert ins["op"] != 1, "a constant threshold was left direct"
+            if ins["op"] != 10:
+                continue
+            n_rank += 1
+            used.add(np.float32(ins["t"]))
+            K, lt = ins["image"] & 0xFFFF, ins["b"] & 1
+            assert K % 2 == (1 if lt else 0)
+            k = (K + 1) // 2 if lt else K // 2              # 1-based position of t
+            assert v[k - 1] == np.float32(ins["t"])
+            assert ins["channel"] == t["nbits"]
+            assert s["rank_mask"] & 1 and s["rank_halo"] >= ins["halo"]
+    assert n_rank >= len(thr) * 0.9
+    assert t["m"] == len(used)      # exactly the thresholds the plan still reads
+
+
+def test_few_thresholds_and_percentiles_stay_direct():
+    plan = vg.compile_formula(_rec(wl.config1_formula()), wl.config1_formula().roots, 8).plan()
+    assert plan["rank_tables"] == [] and all(s["kind"] != 6 for s in plan["steps"])
+    f = wl.config4_formula()
+    plan = vg.compile_formula(_rec(f), f.roots, 8).plan()
+    for ins in plan["insns"]:
+        if ins["op"] == 1 and ins["slot"] >= 0:
+            continue
+        assert ins["op"] != 10 or ins["slot"] < 0
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_rank_thresholds_with_ties_signed_zeros_and_nan(conn):
+    """Pixel values equal to thresholds, -0.0 against 0.0, NaN pixels: the
+    planned rank comparisons give exactly the strict float comparisons."""
+    pytest.importorskip("scipy")
+    ts = [0.0, -0.0, 0.25, 0.5, 0.5, 0.75, -1.0, 2.0]
+    nodes = []
+    for k, t in enumerate(ts):
+        nodes.append(("THR_GT" if k % 2 == 0 else "THR_LT", -1, -1, 0, 0, t, 0.0))
+    nodes.append(("AND", 0, 3, 0, 0, 0, 0))
+    nodes.append(("NEAR", 8, -1, 0, 0, 0, 0))
+    f = wl.Formula([wl.Node(*n) for n in nodes], list(range(len(nodes))))
+    rng = np.random.default_rng(11)
+    img = rng.choice(np.array([0.0, -0.0, 0.25, 0.5, 0.75, -1.0, 2.0, 0.3, np.nan, -5.0],
+                              dtype=np.float32), size=(1, 37, 140)).astype(np.float32)
+    plan = _check_sim(f, [img], conn=conn)
+    assert any(ins["op"] == 10 for ins in plan["insns"])

@@ -43,6 +43,21 @@ def test_thresholds_are_strict(conn):
     check_formula(nodes, [0, 1], [img], conn=conn)
 
 
+@pytest.mark.parametrize("conn", CONNS)
+def test_rank_thresholds_ties_signed_zeros_nan(conn):
+    """Eight thresholds on one channel take the rank-code path: pixel values
+    equal to thresholds, -0.0 against 0.0 and NaN pixels must give the strict
+    float comparisons exactly, in fused groups with halos and plain form."""
+    torch_cuda()
+    ts = [0.0, -0.0, 0.25, 0.5, 0.5, 0.75, -1.0, 2.0]
+    nodes = [_f("THR_GT" if k % 2 == 0 else "THR_LT", t=t) for k, t in enumerate(ts)]
+    nodes += [_f("AND", 0, 3), _f("NEAR", 8), _f("OR", 9, 5), _f("NEAR", 10)]
+    rng = np.random.default_rng(12)
+    vals = np.array([0.0, -0.0, 0.25, 0.5, 0.75, -1.0, 2.0, 0.3, np.nan, -5.0], dtype=np.float32)
+    img = rng.choice(vals, size=(1, 131, 1100)).astype(np.float32)
+    check_formula(nodes, list(range(len(nodes))), [img], conn=conn)
+
+
 @pytest.mark.parametrize("shape,p2", [((64, 64), 0.5), ((131, 1100), 0.45), ((300, 2100), 0.6),
                                       ((1, 3000), 0.7), ((2500, 3), 0.7)])
 @pytest.mark.parametrize("conn", CONNS)
