@@ -696,11 +696,17 @@ VL_API vl_status vl_context_create(const vl_config* cfg, vl_context** out) {
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device)) {
       cudaGetLastError();
     } else {
-      const size_t two = ((size_t)(smem_sm / 2 - reserved)) & ~(size_t)15;
+      // (less the executor's static shared words and some slack)
+      const size_t two = ((size_t)(smem_sm / 2 - reserved - 256)) & ~(size_t)127;
       if (two > c->exec_smem && two <= (size_t)optin) c->exec_smem = two;
     }
   }
   if ((e = exec_configure(c->exec_smem, &c->ctas_per_sm))) { delete c; cudaGetLastError(); return VL_ERR_CUDA; }
+  if (c->ctas_per_sm < 2 && c->exec_smem > exec_smem_bytes(c->nb, bh, bw)) {
+    // the widened size lost the second CTA on this GPU: fall back
+    c->exec_smem = exec_smem_bytes(c->nb, bh, bw);
+    if ((e = exec_configure(c->exec_smem, &c->ctas_per_sm))) { delete c; cudaGetLastError(); return VL_ERR_CUDA; }
+  }
   if (c->ctas_per_sm < 1) c->ctas_per_sm = 1;
   if ((e = cudaMalloc(&c->ccl_status, sizeof(int32_t)))) { delete c; cudaGetLastError(); return VL_ERR_OOM; }
   if ((e = cudaMemset(c->ccl_status, 0, sizeof(int32_t)))) { cudaFree(c->ccl_status); delete c; return VL_ERR_CUDA; }
