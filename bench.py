@@ -127,6 +127,143 @@ def oracle_sample(rows: int):
     return r.n_primitive * rows * W / dt / 1e9, dt, r.n_primitive
 
 
+def leg_mri_batch(ctx, stream, flush, n_images: int = 4096, reps: int = 5) -> dict:
+    """4096 MRI-shaped 4-channel images of uneven sizes, the fixed 40-primitive
+    segmentation formula with percentile thresholds, one persistent launch
+    (autotuned tiles, CUDA graph) per step; beside it the plain per-operator
+    form, one image at a time, on a sample of the same images."""
+    import torch
+    import workloads as wl
+    f = wl.config4_formula()
+    rec = wl.formula_to_records(f)
+    sides = wl.mri_side_lengths(n_images, seed=0)
+    imgs = wl.mri_phantom_batch_parallel(sides, seed=0)
+    F = ctx.compile(rec, f.roots, 8)
+    n_prim = F.info()["n_primitive"]
+    px = float(sum(int(im.shape[1]) * int(im.shape[2]) for im in imgs))
+    with torch.cuda.stream(stream):
+        handles = [ctx.image(im, stream) for im in imgs]
+        jobs = [(F, [h]) for h in handles]
+        tune = ctx.autotune(jobs, stream=stream, reps=1)
+        batch = ctx.batch(jobs, stream)
+        for _ in range(2):
+            batch.run(stream)
+        ev = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch.run(stream)
+            b.record(stream)
+            ev.append((a, b))
+        stream.synchronize()
+        bad = sum(1 for k in range(0, n_images, 97) if batch.result(k).status_word() != 0)
+        if bad:
+            raise SystemExit("MRI batch: device status set")
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        # plain per-operator form, one image at a time (a sample)
+        sample = list(range(0, n_images, n_images // 64))
+        spx = float(sum(int(imgs[k].shape[1]) * int(imgs[k].shape[2]) for k in sample))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in sample:
+            r = ctx.eval(F, [handles[k]], stream=stream, mode="plain")
+            if r.sync() != 0:
+                raise SystemExit("MRI plain form failed")
+            r.close()
+        plain_s = time.perf_counter() - t0
+    batch.close()
+    for h in handles:
+        h.close()
+    val = n_prim * px / (float(np.mean(ms)) / 1e3) / 1e9
+    plain = n_prim * spx / plain_s / 1e9
+    return {"workload": f"{n_images} MRI-shaped images 160-512 px (median 240), 4 channels, "
+                        "40-primitive formula with percentile thresholds, 8-adjacency",
+            "value": val, "unit": "Gpixel-ops/s", "images_per_s": n_images / (float(np.mean(ms)) / 1e3),
+            "ms_per_launch": float(np.mean(ms)), "p99_ms": float(np.percentile(ms, 99)),
+            "tiles": {k: tune["best"][k] for k in ("tile_rows", "tile_words", "ctas_per_sm")},
+            "plain_one_at_a_time": {"value": plain, "unit": "Gpixel-ops/s",
+                                    "images": len(sample), "wall_s": plain_s},
+            "batched_over_plain": val / plain}
+
+
+def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formulas: int = 48,
+                load: float = 0.8) -> dict:
+    """Query stream: square U[0,1) images with sides log-uniform over
+    [128, 4096] resident in HBM, formulas of 10-2000 nodes drawn like the
+    random formula; first all queries at once (saturated throughput), then
+    Poisson arrivals at `load` x that rate (latency), then the plain form one
+    query at a time on a sample."""
+    import torch
+    import paper_2010_07284_gb300 as vg
+    import workloads as wl
+    from workloads.streams import pool_sides
+    rng = np.random.default_rng(5)
+    sides = pool_sides(n_images, seed=1)
+    with torch.cuda.stream(stream):
+        pool = [ctx.image(wl.uniform_image(int(sd), int(sd), seed=100 + k), stream)
+                for k, sd in enumerate(sides)]
+        stream.synchronize()
+    sizes = np.rint(np.exp(np.log(10) + rng.random(n_formulas) * (np.log(2000) - np.log(10)))).astype(int)
+    forms = []
+    for k, n in enumerate(sizes):
+        fd = wl.random_dag(int(n), seed=1000 + k, max_depth=min(500, int(n)))
+        forms.append(ctx.compile(wl.formula_to_records(fd), fd.roots, 8))
+    prims = [F.info()["n_primitive"] for F in forms]
+    qi = rng.integers(0, n_images, size=n_queries)
+    qf = rng.integers(0, n_formulas, size=n_queries)
+    work = float(sum(prims[f] * int(sides[i]) ** 2 for i, f in zip(qi, qf)))
+
+    def run(arrivals):
+        srv = vg.Server(ctx, max_inflight_batches=3, max_batch_jobs=64, batch_window_us=200)
+        t0 = time.perf_counter()
+        tickets = []
+        for k in range(n_queries):
+            if arrivals is not None:
+                dt = arrivals[k] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append(srv.submit(forms[qf[k]], [pool[qi[k]]]))
+        for t in tickets:
+            st, res = srv.wait(t, timeout_us=120_000_000)
+            if st != 0:
+                raise SystemExit(f"serving: query status {st}")
+            res.close()
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        return wall, stats
+
+    wall_sat, st_sat = run(None)
+    rate = n_queries / wall_sat
+    gaps = rng.exponential(1.0 / (load * rate), size=n_queries)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    wall_p, st_p = run(arrivals)
+    # plain form, one query at a time, on a sample
+    sample = range(0, n_queries, max(1, n_queries // 100))
+    swork = float(sum(prims[qf[k]] * int(sides[qi[k]]) ** 2 for k in sample))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in sample:
+        r = ctx.eval(forms[qf[k]], [pool[qi[k]]], mode="plain")
+        if r.sync() != 0:
+            raise SystemExit("serving plain form failed")
+        r.close()
+    plain_s = time.perf_counter() - t0
+    for im in pool:
+        im.close()
+    return {"workload": f"{n_queries} queries over {n_images} resident images (sides log-uniform "
+                        f"128-4096), {n_formulas} formulas of 10-2000 nodes, 8-adjacency",
+            "saturated": {"queries_per_s": rate, "value": work / wall_sat / 1e9,
+                          "unit": "Gpixel-ops/s", "p50_ms": st_sat["p50_ms"], "p99_ms": st_sat["p99_ms"],
+                          "batches": st_sat["batches"]},
+            "poisson": {"load": load, "rate_per_s": load * rate, "queries_per_s": n_queries / wall_p,
+                        "value": work / wall_p / 1e9, "unit": "Gpixel-ops/s",
+                        "p50_ms": st_p["p50_ms"], "p99_ms": st_p["p99_ms"], "batches": st_p["batches"]},
+            "plain_one_at_a_time": {"queries": len(sample), "queries_per_s": len(sample) / plain_s,
+                                    "value": swork / plain_s / 1e9, "unit": "Gpixel-ops/s"}}
+
+
 def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
         return
@@ -348,6 +485,9 @@ def main():
                        "h2d_bytes_per_step": int(host_img.nbytes),
                        "d2h_bytes_per_step": int(res_words * 4),
                        "ms_per_step": 1e3 * float(np.mean(e2e))}
+        # ---- MRI-shaped batch and the serving stream
+        line["mri_batch"] = leg_mri_batch(ctx, stream, flush)
+        line["serving"] = leg_serving(ctx, stream)
         # ---- CPU oracle on a bounded sample (rank 0 only)
         if rank == 0:
             v, dt, _ = oracle_sample(CPU_ROWS_BASE)

@@ -249,19 +249,54 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.off_images = take(sizeof(DevImage) * jobs[j].n_images);
     I.off_slotptrs = take(sizeof(uint32_t*) * std::max(1, P.n_inter_slots + P.n_root_slots + P.n_mask_slots));
   }
-  // work items: step-major across jobs so that dependencies come first
-  int max_steps = 0;
-  for (auto& I : J) max_steps = std::max(max_steps, (int)I.need.size());
-  for (int s = 0; s < max_steps; ++s)
+  // work items, in list-scheduling order: every (job, step) gets the time
+  // its step could start if the job ran alone on the whole GPU (the sum of
+  // estimated latencies of its earlier steps), and pairs are emitted in the
+  // order of those times.  A job's steps keep their order (latencies are
+  // positive), so everything an item waits for comes earlier in the list;
+  // jobs of very different sizes interleave by their progress instead of
+  // step index.  Steps split into items of about a tile each, at most
+  // 4 x grid items per step.
+  {
+    struct Pair { double t; int j, s; };
+    std::vector<Pair> pairs;
     for (int j = 0; j < n_jobs; ++j) {
-      if (s >= (int)J[j].need.size()) continue;
-      const int n = J[j].need[s];
-      int chunk = 1;
-      if ((long long)n_jobs * 2 >= grid) chunk = n;
-      else chunk = std::max(1, (int)((long long)n * n_jobs / (2LL * grid)));
-      for (int first = 0; first < n; first += chunk)
-        items.push_back(WorkItem{j, s, first, std::min(chunk, n - first)});
+      const Plan& P = *J[j].P;
+      double t = 0;
+      for (size_t s = 0; s < J[j].need.size(); ++s) {
+        pairs.push_back(Pair{t, j, (int)s});
+        const int n = J[j].need[s];
+        const double waves = std::ceil((double)n / grid);
+        switch (P.steps[s].kind) {
+          case SK_GROUP: t += waves * (5.0 + 1.0 * P.steps[s].insn_cnt); break;
+          case SK_RZ_LOCAL: t += waves * 50.0; break;
+          case SK_RZ_MERGE: t += 30.0; break;
+          case SK_RZ_FLAGS: t += 8.0; break;
+          case SK_RZ_FINAL: t += waves * 25.0; break;
+          case SK_RANK: t += 20.0 + waves * 5.0; break;
+          default: t += 100.0; break;
+        }
+      }
     }
+    std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& a, const Pair& b) { return a.t < b.t; });
+    // with work for many waves (thousands of small images), items of short
+    // tiles are merged up to ~40 us so that popping stays cheap beside work
+    long long subitems = 0;
+    for (const Pair& p : pairs) subitems += J[p.j].need[p.s];
+    const bool plenty = subitems > 32LL * grid;
+    for (const Pair& p : pairs) {
+      const int n = J[p.j].need[p.s];
+      int chunk = std::max(1, (n + 4 * grid - 1) / (4 * grid));
+      if (plenty) {
+        const StepDesc& sd = J[p.j].P->steps[p.s];
+        const double tile_us = sd.kind == SK_GROUP ? 5.0 + 1.0 * sd.insn_cnt
+                               : sd.kind == SK_RZ_FINAL ? 20.0 : 40.0;
+        chunk = std::max(chunk, std::min(n, (int)std::ceil(40.0 / tile_us)));
+      }
+      for (int first = 0; first < n; first += chunk)
+        items.push_back(WorkItem{p.j, p.s, first, std::min(chunk, n - first)});
+    }
+  }
   const size_t off_items = take(sizeof(WorkItem) * std::max<size_t>(1, items.size()));
   const size_t off_need = take(sizeof(int32_t) * std::max(1, total_steps));
   // counters: head, done[steps], fcount[rz] -- zeroed before every run

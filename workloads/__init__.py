@@ -17,7 +17,8 @@ from .formulas import (Node, Formula, OPS, PRIMITIVE_OPS, DERIVED_OPS,
                        formula_to_records)
 from .images import (gaussian_field_image, uniform_image, bernoulli_mask,
                      spiral_mask, checkerboard_mask, rings_mask, rings_count,
-                     mri_phantom_batch, mri_side_lengths, seed_mask)
+                     mri_phantom_batch, mri_phantom_batch_parallel, mri_side_lengths,
+                     seed_mask)
 from .streams import poisson_queries
 
 __all__ = [
@@ -25,5 +26,5 @@ __all__ = [
     "sequential_dag", "config1_formula", "config4_formula", "grow_spec_formula",
     "formula_to_records", "gaussian_field_image", "uniform_image", "bernoulli_mask",
     "spiral_mask", "checkerboard_mask", "rings_mask", "rings_count",
-    "mri_phantom_batch", "mri_side_lengths", "seed_mask", "poisson_queries",
+    "mri_phantom_batch", "mri_phantom_batch_parallel", "mri_side_lengths", "seed_mask", "poisson_queries",
 ]

@@ -197,3 +197,31 @@ def mri_phantom_batch(sides: Sequence[Sequence[int]], seed: int = 0) -> List[np.
         rng = np.random.default_rng([seed, i])
         out.append(mri_phantom(int(h), int(w), rng))
     return out
+
+
+def _phantom_chunk(args):
+    sides, seed, first = args
+    out = []
+    for k, (h, w) in enumerate(sides):
+        rng = np.random.default_rng([seed, first + k])
+        out.append(mri_phantom(int(h), int(w), rng))
+    return out
+
+
+def mri_phantom_batch_parallel(sides: Sequence[Sequence[int]], seed: int = 0,
+                               processes: int = 0) -> List[np.ndarray]:
+    """``mri_phantom_batch`` computed by a pool of spawned processes (safe
+    after a GPU context exists); identical output, image i from stream
+    (seed, i)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    n = len(sides)
+    procs = processes or min(16, os.cpu_count() or 1)
+    if procs <= 1 or n < 64:
+        return mri_phantom_batch(sides, seed)
+    step = (n + procs * 4 - 1) // (procs * 4)
+    chunks = [([tuple(map(int, s)) for s in sides[i:i + step]], seed, i) for i in range(0, n, step)]
+    with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_phantom_chunk, chunks))
+    return [im for part in parts for im in part]
