@@ -48,6 +48,20 @@ def workload_config(n_gpus: int) -> dict:
             "parallelism": f"replicas{n_gpus}"}
 
 
+def aggregate_throughput(total_ms: float, units_per_rank: float, world: int, device) -> tuple:
+    """Whole-job throughput of `world` replicas: every rank processed
+    `units_per_rank` units in its own `total_ms`; the job took the slowest
+    rank's time (max over ranks), so value = world * units / max time (s).
+    Returns (value, max_ms); needs an initialised process group if world > 1."""
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    return world * units_per_rank / (total_max / 1e3), total_max
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -370,12 +384,8 @@ def main():
         st = batch.result(0).sync()
         if st != 0:
             raise SystemExit(f"device status {st}: {ctx.last_error()}")
-    total_ms = float(step_ms.sum())
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_max = float(t.item())
-    value = world * args.steps * n_prim * P / (total_max / 1e3) / 1e9
+    value, total_max = aggregate_throughput(float(step_ms.sum()), args.steps * n_prim * P / 1e9,
+                                            world, "cuda")
     ms_per_step = total_max / args.steps
 
     # roofline of the persistent executor (the only kernel of a step):
