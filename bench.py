@@ -62,6 +62,20 @@ def aggregate_throughput(total_ms: float, units_per_rank: float, world: int, dev
     return world * units_per_rank / (total_max / 1e3), total_max
 
 
+def profiled_traffic(kernel: str, key: str):
+    """DRAM bytes that an ncu capture of the current kernel sources measured
+    (profiles/traffic.json), or None when the sources changed since."""
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tj = json.load(open(tfile))
+        from paper_2010_07284_gb300 import buildlib
+        if tj.get("source_hash") == buildlib.source_hash():
+            return tj.get(kernel, {}).get(key)
+    except Exception:
+        pass
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -139,6 +153,35 @@ def oracle_sample(rows: int):
     r = oracle.evaluate(rec, f.roots, [img], conn=CONN)
     dt = time.perf_counter() - t0
     return r.n_primitive * rows * W / dt / 1e9, dt, r.n_primitive
+
+
+def leg_ccl(ctx, stream, flush, peak: float, S: int = 8192, runs: int = 6) -> dict:
+    """Full connected-component labelling (int32 labels, 8-adjacency) of an
+    S x S Bernoulli(0.5) mask: 2 untimed runs, then CUDA events per run."""
+    import torch
+    m = torch.rand((S, S), device="cuda", generator=torch.Generator("cuda").manual_seed(3)) < 0.5
+    with torch.cuda.stream(stream):
+        mimg = ctx.mask(m.to(torch.uint8), stream)
+        labels = torch.empty(S * S, dtype=torch.int32, device="cuda")
+        ce = []
+        for k in range(runs):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.ccl(mimg, labels, 8, stream)
+            b.record(stream)
+            if k >= 2:
+                ce.append((a, b))
+        stream.synchronize()
+        if ctx.ccl_status(stream) != 0:
+            raise SystemExit("ccl failed: " + ctx.last_error())
+    cms = float(np.mean([a.elapsed_time(b) for a, b in ce]))
+    mimg.close()
+    return {"value": S * S / (cms / 1e3) / 1e9, "unit": "Gpix/s", "ms": cms,
+            "mask": f"{S}x{S} Bernoulli(0.5), 8-adjacency",
+            "achieved_GBps": 4.125 * S * S / (cms / 1e3) / 1e9,
+            "frac": 4.125 * S * S / (cms / 1e3) / 1e9 / peak,
+            "traffic": profiled_traffic("ccl", "dram_bytes_per_labelling") if S == 8192 else None}
 
 
 def leg_mri_batch(ctx, stream, flush, n_images: int = 4096, reps: int = 5) -> dict:
@@ -313,6 +356,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain/ccl/e2e/cpu legs")
+    ap.add_argument("--leg", default="", choices=["", "ccl"],
+                    help="run only this leg and print its figures (for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -337,6 +382,11 @@ def main():
             dist.barrier()
 
     ctx = vg.Context(device=local)
+    if args.leg == "ccl":
+        stream = torch.cuda.Stream()
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        print(json.dumps({"leg": "ccl", **leg_ccl(ctx, stream, flush, measured_peaks()[0])}), flush=True)
+        return
     f = wl.random_dag(N_NODES, seed=DAG_SEED)
     rec = wl.formula_to_records(f)
     F = ctx.compile(rec, f.roots, CONN)
@@ -398,16 +448,7 @@ def main():
                  + P * (8.0 + 2.0 / 8.0) * info["n_selects"])
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (float(np.mean(step_ms)) / 1e3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            tj = json.load(open(tfile))
-            from paper_2010_07284_gb300 import buildlib
-            if tj.get("source_hash") == buildlib.source_hash():
-                traffic = tj.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic("k_exec", "dram_bytes_per_launch")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
@@ -448,29 +489,7 @@ def main():
                          "launches_per_step": "one per primitive (4 per rho select + 2)"}
         line["batched_over_plain"] = line["value"] / world / line["plain"]["value"]
         # ---- full CCL on an 8192 x 8192 Bernoulli(0.5) mask
-        S = 8192
-        m = torch.rand((S, S), device="cuda", generator=torch.Generator("cuda").manual_seed(3)) < 0.5
-        with torch.cuda.stream(stream):
-            mimg = ctx.mask(m.to(torch.uint8), stream)
-            labels = torch.empty(S * S, dtype=torch.int32, device="cuda")
-            ce = []
-            for k in range(6):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                ctx.ccl(mimg, labels, 8, stream)
-                b.record(stream)
-                if k >= 2:
-                    ce.append((a, b))
-            stream.synchronize()
-            if ctx.ccl_status(stream) != 0:
-                raise SystemExit("ccl failed: " + ctx.last_error())
-        cms = float(np.mean([a.elapsed_time(b) for a, b in ce]))
-        line["ccl"] = {"value": S * S / (cms / 1e3) / 1e9, "unit": "Gpix/s", "ms": cms,
-                       "mask": "8192x8192 Bernoulli(0.5), 8-adjacency",
-                       "achieved_GBps": 4.125 * S * S / (cms / 1e3) / 1e9,
-                       "frac": 4.125 * S * S / (cms / 1e3) / 1e9 / peak}
-        del labels, m, mimg
+        line["ccl"] = leg_ccl(ctx, stream, flush, peak)
         # ---- end to end through the public API with host buffers
         import torch as _t
         pin_in = _t.from_numpy(host_img).pin_memory()
