@@ -175,7 +175,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     int H, W, Wp, pitch;
     int gty, gtx, cty, ctx_, ctiles;
     std::vector<int> need;
-    size_t off_images, off_slotptrs, off_pct, off_slots, off_scratch[MAX_RZ_BATCH * 5];
+    size_t off_images, off_slotptrs, off_pct, off_slots, off_rz, set_bytes, set_off[5];
     size_t off_roots, off_status, off_fcount, off_planes;
     int step_base, fcount_base;
     int flist_cap;
@@ -313,12 +313,17 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.off_planes = take(mask_bytes * P.n_planes);
     I.off_slots = take(mask_bytes * P.n_inter_slots);
     const size_t tstate = (size_t)I.ctiles * ccl_tile_cap_host(I.Wp);
-    for (int k = 0; k < P.max_rz_batch; ++k) {
-      I.off_scratch[5 * k + 0] = take(P_px * 4);
-      I.off_scratch[5 * k + 1] = take(P_px);
-      I.off_scratch[5 * k + 2] = take((size_t)I.flist_cap * 4);
-      I.off_scratch[5 * k + 3] = take(tstate * 4);
-      I.off_scratch[5 * k + 4] = take(tstate);
+    // select scratch sets: G, F, flist, tpar, tflag, each 256-byte aligned
+    {
+      size_t o = 0;
+      auto sub = [&](size_t bytes) { o = align_up(o, 256); size_t r = o; o += bytes; return r; };
+      I.set_off[0] = sub(P_px * 4);
+      I.set_off[1] = sub(P_px);
+      I.set_off[2] = sub((size_t)I.flist_cap * 4);
+      I.set_off[3] = sub(tstate * 4);
+      I.set_off[4] = sub(tstate);
+      I.set_bytes = align_up(o, 256);
+      I.off_rz = take(I.set_bytes * (size_t)P.max_rz_batch);
     }
   }
   const size_t trans_bytes = align_up(off, 256);
@@ -396,13 +401,12 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     d.rvals = reinterpret_cast<const float*>(tb + f_rvals[k]);
     d.n_rtab = (int32_t)P.rtab.size();
     d.planes = reinterpret_cast<uint32_t*>(tb + I.off_planes);
-    for (int s = 0; s < P.max_rz_batch; ++s) {
-      d.G[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[5 * s + 0]);
-      d.F[s] = reinterpret_cast<uint8_t*>(tb + I.off_scratch[5 * s + 1]);
-      d.flist[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[5 * s + 2]);
-      d.tpar[s] = reinterpret_cast<int32_t*>(tb + I.off_scratch[5 * s + 3]);
-      d.tflag[s] = reinterpret_cast<uint8_t*>(tb + I.off_scratch[5 * s + 4]);
-    }
+    d.rzs = reinterpret_cast<unsigned char*>(tb + I.off_rz);
+    d.set_bytes = (int64_t)I.set_bytes;
+    d.off_F = (int64_t)I.set_off[1];
+    d.off_flist = (int64_t)I.set_off[2];
+    d.off_tpar = (int64_t)I.set_off[3];
+    d.off_tflag = (int64_t)I.set_off[4];
     d.fcount = counters_dev + 1 + total_steps + I.fcount_base;
     d.flist_cap = I.flist_cap;
     d.tile_cap = ccl_tile_cap_host(I.Wp);

@@ -65,7 +65,7 @@ struct Plan {
   int64_t n_thr = 0, n_not = 0, n_and = 0, n_near = 0, n_other = 0;
 };
 
-constexpr int MAX_RZ_BATCH = 4;
+constexpr int MAX_RZ_BATCH = 16;  // selects of one level run together in one step
 // Rank codes: a channel gets a table when at least this many constant
 // thresholds read it; tables hold at most kRankMaxValues values (codes fit
 // 14 bits) and a formula at most kRankMaxTables tables (one bit each in a

@@ -118,17 +118,17 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       const CclGeom geo = ccl_geom(J.H, J.W, J.Wp, tile, J.c_tiles_x);
       const uint32_t* phi1 = J.slots[r.phi1_slot];
       const uint32_t* phi2 = J.slots[r.phi2_slot];
-      int32_t* tpar = J.tpar[k] + (size_t)tile * J.tile_cap;
-      uint8_t* tflag = J.tflag[k] + (size_t)tile * J.tile_cap;
+      int32_t* tpar = rz_tpar(J, k) + (size_t)tile * J.tile_cap;
+      uint8_t* tflag = rz_tflag(J, k) + (size_t)tile * J.tile_cap;
       if (S.kind == SK_RZ_LOCAL) {
         if (!ccl_tile_label(s, phi2, phi1, geo, J.conn, false, J.status)) break;
-        ccl_encode_roots(s, geo, ENC_PUBLISH, false, J.G[k], J.F[k], J.flist[k],
+        ccl_encode_roots(s, geo, ENC_PUBLISH, false, rz_G(J, k), rz_F(J, k), rz_flist(J, k),
                          J.fcount + S.rz_off + j, J.flist_cap, cap, J.status);
-        ccl_publish_border(s, geo, J.G[k]);
+        ccl_publish_border(s, geo, rz_G(J, k));
         ccl_tile_save(s, tpar, tflag);
       } else {
         if (!ccl_tile_load(s, phi2, geo, J.conn, tpar, tflag, J.status)) break;
-        ccl_encode_roots(s, geo, ENC_SELECT, true, J.G[k], J.F[k], nullptr, nullptr, 0, cap,
+        ccl_encode_roots(s, geo, ENC_SELECT, true, rz_G(J, k), rz_F(J, k), nullptr, nullptr, 0, cap,
                          J.status);
         ccl_write_select(s, geo, J.slots[r.z_slot]);
       }
@@ -141,16 +141,16 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       const int nw = blockDim.x >> 5;
       for (int u = chunk * nw + (threadIdx.x >> 5); u < n; u += per_rz * nw)
         ccl_merge_unit(J.slots[r.phi2_slot], J.H, J.W, J.Wp, J.c_tiles_y, u, J.conn,
-                       J.G[r.scratch], cap, J.status);
+                       rz_G(J, r.scratch), cap, J.status);
       break;
     }
     case SK_RZ_FLAGS: {
       const int j = sub / per_rz, chunk = sub - j * per_rz;
       const RzDesc r = J.rz[S.rz_off + j];
       const int n = min(ldcg(J.fcount + S.rz_off + j), J.flist_cap);
-      int32_t* G = J.G[r.scratch];
-      uint8_t* F = J.F[r.scratch];
-      const int32_t* fl = J.flist[r.scratch];
+      int32_t* G = rz_G(J, r.scratch);
+      uint8_t* F = rz_F(J, r.scratch);
+      const int32_t* fl = rz_flist(J, r.scratch);
       for (int i = chunk * blockDim.x + threadIdx.x; i < n; i += per_rz * blockDim.x)
         F[g_find(G, ldcg(fl + i), cap, J.status)] = 1;
       break;

@@ -3,6 +3,12 @@
 #pragma once
 #include <stdint.h>
 
+#if defined(__CUDACC__)
+#define VL_HD_INLINE __host__ __device__ __forceinline__
+#else
+#define VL_HD_INLINE inline
+#endif
+
 namespace vl {
 
 // ----------------------------------------------------------------- geometry
@@ -149,12 +155,13 @@ struct DevJob {
   const RzDesc* rz;
   const PctDesc* pct;
   float* pct_val;               // percentile values by slot
-  int32_t* G[4];                // CCL scratch sets: union-find over gids
-  uint8_t* F[4];                //   component flags by gid
-  int32_t* flist[4];            //   flagged boundary roots
+  // CCL scratch sets, one per select of a batch step, `set_bytes` apart:
+  // union-find over gids (G), component flags by gid (F), flagged border
+  // roots (flist), saved tile union-find state and flags (tiles x tile_cap)
+  unsigned char* rzs;
+  int64_t set_bytes;
+  int64_t off_F, off_flist, off_tpar, off_tflag;
   int32_t* fcount;              // flagged-root count per select (zeroed per launch)
-  int32_t* tpar[4];             //   saved tile union-find state, tiles x tile_cap
-  uint8_t* tflag[4];            //   saved tile flags
   int32_t flist_cap;
   int32_t tile_cap;
   int32_t* status;              // device status word of this job
@@ -164,6 +171,18 @@ struct DevJob {
   int32_t pad_;
   uint32_t* planes;             // rank-code planes, H x Wp words each
 };
+
+VL_HD_INLINE int32_t* rz_G(const DevJob& J, int k) {
+  return reinterpret_cast<int32_t*>(J.rzs + k * J.set_bytes);
+}
+VL_HD_INLINE uint8_t* rz_F(const DevJob& J, int k) { return J.rzs + k * J.set_bytes + J.off_F; }
+VL_HD_INLINE int32_t* rz_flist(const DevJob& J, int k) {
+  return reinterpret_cast<int32_t*>(J.rzs + k * J.set_bytes + J.off_flist);
+}
+VL_HD_INLINE int32_t* rz_tpar(const DevJob& J, int k) {
+  return reinterpret_cast<int32_t*>(J.rzs + k * J.set_bytes + J.off_tpar);
+}
+VL_HD_INLINE uint8_t* rz_tflag(const DevJob& J, int k) { return J.rzs + k * J.set_bytes + J.off_tflag; }
 
 // One work item of the persistent executor: a range of `count` consecutive
 // sub-items (tiles, chunks, rz x tile) of one step of one job.
