@@ -201,7 +201,8 @@ VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes,
  * its instructions on every tile; kinds 2-5 are the four passes of a batch
  * of component selects (tile labelling, border merge, flag propagation,
  * final select); kind 0 computes percentiles; kind 6 computes rank codes
- * (below).  Instruction opcodes: 1 threshold, 2 load slot, 3 not, 4 and,
+ * (below).  Steps are listed in an order that respects their dependencies
+ * (vl_formula_step_deps).  Instruction opcodes: 1 threshold, 2 load slot, 3 not, 4 and,
  * 5 or, 6 N, 7 constant, 8 store slot, 9 and-not, 10 threshold by rank
  * code.  Slots: [0, n_inter) intermediates, then one per distinct root,
  * then one per mask image.
@@ -212,12 +213,13 @@ VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes,
  * code c = 2 * #{k : t_k < v} + [v equals some t_k] (0 for NaN).  Then
  * v > t_k exactly when c >= 2k, and v < t_k exactly when v is not NaN and
  * c < 2k - 1; an opcode-10 instruction holds the table (a), the bound
- * (image, read as uint16), the code bits (channel) and the direction (b).
+ * (image, read as uint16), the code bits (channel), the table's first
+ * plane (slot) and the direction (b).
  * The results are those of the strict float comparisons (Sec. 2 atoms). */
 typedef struct {
   int32_t n_steps, n_insns, n_selects, n_pct;
   int32_t n_inter_slots, n_root_slots, n_mask_slots, n_roots;
-  int32_t n_rank_tables, n_rank_values, n_rank_planes, reserved;
+  int32_t n_rank_tables, n_rank_values, n_rank_planes, n_deps;
 } vl_plan_sizes;
 typedef struct {
   int32_t kind, insn_off, insn_cnt, halo, sel_off, sel_cnt, pct_off, pct_cnt;
@@ -241,6 +243,14 @@ VL_API vl_status vl_formula_plan(const vl_formula* f, vl_plan_sizes* sizes,
                                  vl_plan_step* steps, vl_plan_insn* insns,
                                  vl_plan_select* selects, vl_plan_pct* pct,
                                  int32_t* root_slots, int32_t* mask_slot_images);
+
+/* Step dependencies of a plan: step s may start once every step in
+ * deps[dep_off[s] .. dep_off[s + 1]) has finished (dep_off has n_steps + 1
+ * entries, deps n_deps).  They cover reads after writes, and writes after
+ * the reads and the write of a slot's previous value (slots are reused), so
+ * any order that respects them computes the same masks; the persistent
+ * executor lets independent steps overlap.  Either array may be NULL. */
+VL_API vl_status vl_formula_step_deps(const vl_formula* f, int32_t* dep_off, int32_t* deps);
 
 /* Rank tables of a plan (n_rank_tables entries) and their sorted threshold
  * values (n_rank_values floats; table k owns values [value_off, value_off +

@@ -57,7 +57,7 @@ class VlPlanSizes(C.Structure):
                 ("n_pct", C.c_int32), ("n_inter_slots", C.c_int32), ("n_root_slots", C.c_int32),
                 ("n_mask_slots", C.c_int32), ("n_roots", C.c_int32),
                 ("n_rank_tables", C.c_int32), ("n_rank_values", C.c_int32),
-                ("n_rank_planes", C.c_int32), ("reserved", C.c_int32)]
+                ("n_rank_planes", C.c_int32), ("n_deps", C.c_int32)]
 
 
 class VlPlanStep(C.Structure):
@@ -119,6 +119,7 @@ SIGNATURES = [
     ("vl_mask_create_packed", C.c_int, [_P, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_image_info", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_compile", C.c_int, [_P, C.POINTER(VlNode), _I32, C.POINTER(_I32), _I32, _I32, _PP]),
+    ("vl_formula_step_deps", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_rank_tables", C.c_int, [_P, C.POINTER(VlPlanRank), C.POINTER(C.c_float)]),
     ("vl_formula_info", C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_stats_get", C.c_int, [_P, C.POINTER(VlFormulaStats)]),

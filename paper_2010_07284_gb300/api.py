@@ -284,7 +284,11 @@ class Formula(_Handle):
         rt = (N.VlPlanRank * max(1, sz.n_rank_tables))()
         rv = (C.c_float * max(1, sz.n_rank_values))()
         self._check(lib.vl_formula_rank_tables(self._ptr, rt, rv))
+        doff = (C.c_int32 * (sz.n_steps + 1))()
+        deps = (C.c_int32 * max(1, sz.n_deps))()
+        self._check(lib.vl_formula_step_deps(self._ptr, doff, deps))
         return {
+            "deps": [list(deps[doff[i]:doff[i + 1]]) for i in range(sz.n_steps)],
             "rank_tables": [rec(rt[i]) for i in range(sz.n_rank_tables)],
             "rank_values": np.array(rv[:sz.n_rank_values], dtype=np.float32),
             "sizes": rec(sz),

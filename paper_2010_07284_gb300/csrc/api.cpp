@@ -203,7 +203,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   auto take = [&](size_t bytes, size_t a = 256) { off = align_up(off, a); size_t o = off; off += bytes; return o; };
   const size_t off_jobs = take(sizeof(DevJob) * n_jobs);
   std::vector<size_t> f_steps(formulas.size()), f_insns(formulas.size()), f_rz(formulas.size()),
-      f_pct(formulas.size()), f_rtab(formulas.size()), f_rvals(formulas.size());
+      f_pct(formulas.size()), f_rtab(formulas.size()), f_rvals(formulas.size()),
+      f_doff(formulas.size()), f_deps(formulas.size());
   for (size_t k = 0; k < formulas.size(); ++k) {
     const Plan* P = formulas[k];
     f_steps[k] = take(sizeof(StepDesc) * std::max<size_t>(1, P->steps.size()));
@@ -212,6 +213,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     f_pct[k] = take(sizeof(PctDesc) * std::max<size_t>(1, P->pct.size()));
     f_rtab[k] = take(sizeof(RankTab) * std::max<size_t>(1, P->rtab.size()));
     f_rvals[k] = take(sizeof(float) * std::max<size_t>(1, P->rvals.size()));
+    f_doff[k] = take(sizeof(int32_t) * std::max<size_t>(1, P->dep_off.size()));
+    f_deps[k] = take(sizeof(int32_t) * std::max<size_t>(1, P->deps.size()));
   }
   const TileShape ts = force ? *force : pick_tile_shape(ctx, jobs, n_jobs);
   if (!tile_shape_fits(ctx, ts)) return set_err(ctx, VL_ERR_ARG, "tile shape does not fit shared memory");
@@ -250,10 +253,11 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.off_slotptrs = take(sizeof(uint32_t*) * std::max(1, P.n_inter_slots + P.n_root_slots + P.n_mask_slots));
   }
   // work items, in list-scheduling order: every (job, step) gets the time
-  // its step could start if the job ran alone on the whole GPU (the sum of
-  // estimated latencies of its earlier steps), and pairs are emitted in the
-  // order of those times.  A job's steps keep their order (latencies are
-  // positive), so everything an item waits for comes earlier in the list;
+  // its step could start if the job ran alone on the whole GPU (the latest
+  // estimated finish of its dependencies), and pairs are emitted in the
+  // order of those times.  A step starts after its dependencies finish
+  // (latencies are positive), so everything an item waits for comes earlier
+  // in the list;
   // jobs of very different sizes interleave by their progress instead of
   // step index.  Steps split into items of about a tile each, at most
   // 4 x grid items per step.
@@ -262,20 +266,24 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     std::vector<Pair> pairs;
     for (int j = 0; j < n_jobs; ++j) {
       const Plan& P = *J[j].P;
-      double t = 0;
+      std::vector<double> fin(J[j].need.size(), 0.0);
       for (size_t s = 0; s < J[j].need.size(); ++s) {
+        double t = 0;  // earliest start: after every dependency finished
+        for (int q = P.dep_off[s]; q < P.dep_off[s + 1]; ++q) t = std::max(t, fin[P.deps[q]]);
         pairs.push_back(Pair{t, j, (int)s});
         const int n = J[j].need[s];
         const double waves = std::ceil((double)n / grid);
+        double len;
         switch (P.steps[s].kind) {
-          case SK_GROUP: t += waves * (5.0 + 1.0 * P.steps[s].insn_cnt); break;
-          case SK_RZ_LOCAL: t += waves * 50.0; break;
-          case SK_RZ_MERGE: t += 30.0; break;
-          case SK_RZ_FLAGS: t += 8.0; break;
-          case SK_RZ_FINAL: t += waves * 25.0; break;
-          case SK_RANK: t += 20.0 + waves * 5.0; break;
-          default: t += 100.0; break;
+          case SK_GROUP: len = waves * (5.0 + 1.0 * P.steps[s].insn_cnt); break;
+          case SK_RZ_LOCAL: len = waves * 50.0; break;
+          case SK_RZ_MERGE: len = 30.0; break;
+          case SK_RZ_FLAGS: len = 8.0; break;
+          case SK_RZ_FINAL: len = waves * 25.0; break;
+          case SK_RANK: len = 20.0 + waves * 5.0; break;
+          default: len = 100.0; break;
         }
+        fin[s] = t + len;
       }
     }
     std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& a, const Pair& b) { return a.t < b.t; });
@@ -359,6 +367,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     if (!P->pct.empty()) std::memcpy(&host[f_pct[k]], P->pct.data(), sizeof(PctDesc) * P->pct.size());
     if (!P->rtab.empty()) std::memcpy(&host[f_rtab[k]], P->rtab.data(), sizeof(RankTab) * P->rtab.size());
     if (!P->rvals.empty()) std::memcpy(&host[f_rvals[k]], P->rvals.data(), sizeof(float) * P->rvals.size());
+    if (!P->dep_off.empty()) std::memcpy(&host[f_doff[k]], P->dep_off.data(), sizeof(int32_t) * P->dep_off.size());
+    if (!P->deps.empty()) std::memcpy(&host[f_deps[k]], P->deps.data(), sizeof(int32_t) * P->deps.size());
   }
   DevJob* hj = reinterpret_cast<DevJob*>(&host[off_jobs]);
   int32_t* hneed = reinterpret_cast<int32_t*>(&host[off_need]);
@@ -394,6 +404,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     const int k = I.formula_idx;
     d.insns = reinterpret_cast<const Insn*>(tb + f_insns[k]);
     d.steps = reinterpret_cast<const StepDesc*>(tb + f_steps[k]);
+    d.dep_off = reinterpret_cast<const int32_t*>(tb + f_doff[k]);
+    d.deps = reinterpret_cast<const int32_t*>(tb + f_deps[k]);
     d.rz = reinterpret_cast<const RzDesc*>(tb + f_rz[k]);
     d.pct = reinterpret_cast<const PctDesc*>(tb + f_pct[k]);
     d.pct_val = reinterpret_cast<float*>(tb + I.off_pct);
@@ -956,7 +968,7 @@ VL_API vl_status vl_formula_plan(const vl_formula* f, vl_plan_sizes* sizes, vl_p
     sizes->n_rank_tables = (int32_t)P.rtab.size();
     sizes->n_rank_values = (int32_t)P.rvals.size();
     sizes->n_rank_planes = P.n_planes;
-    sizes->reserved = 0;
+    sizes->n_deps = (int32_t)P.deps.size();
   }
   static_assert(sizeof(vl_plan_step) == sizeof(StepDesc), "step layout");
   static_assert(sizeof(vl_plan_insn) == sizeof(Insn), "insn layout");
@@ -969,6 +981,14 @@ VL_API vl_status vl_formula_plan(const vl_formula* f, vl_plan_sizes* sizes, vl_p
   if (root_slots) for (int r = 0; r < P.n_roots; ++r) root_slots[r] = P.root_slot[r];
   if (mask_slot_images)
     for (int k = 0; k < P.n_mask_slots; ++k) mask_slot_images[k] = P.mask_slot_image[k];
+  return VL_OK;
+}
+
+VL_API vl_status vl_formula_step_deps(const vl_formula* f, int32_t* dep_off, int32_t* deps) {
+  if (!valid(f, TAG_FML)) return VL_ERR_ARG;
+  const Plan& P = f->plan;
+  if (dep_off && !P.dep_off.empty()) std::memcpy(dep_off, P.dep_off.data(), sizeof(int32_t) * P.dep_off.size());
+  if (deps && !P.deps.empty()) std::memcpy(deps, P.deps.data(), sizeof(int32_t) * P.deps.size());
   return VL_OK;
 }
 

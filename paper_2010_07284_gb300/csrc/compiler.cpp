@@ -528,7 +528,7 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
   for (int v : order) {
     int s = -1;
     for (size_t k = 0; k < slot_free_after.size(); ++k)
-      if (slot_free_after[k] < def_step[v]) { s = (int)k; break; }
+      if (slot_free_after[k] + pp.reuse_distance < def_step[v]) { s = (int)k; break; }
     if (s < 0) { s = (int)slot_free_after.size(); slot_free_after.push_back(0); }
     slot_free_after[s] = std::max(last_step[v], def_step[v]);
     slot_of[v] = s;
@@ -623,6 +623,7 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
         in.a = (uint8_t)it->second;
         in.img = (int16_t)(lt ? 2 * kk - 1 : 2 * kk);
         in.ch = (int16_t)t.nbits;
+        in.slot = (int16_t)t.plane0;
         s.rank_mask |= 1 << it->second;
         s.rank_halo = std::max(s.rank_halo, (int)in.h);
       }
@@ -637,6 +638,70 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
     r.phi1_slot = (int16_t)slot_of[r.phi1_slot];
     r.phi2_slot = (int16_t)slot_of[r.phi2_slot];
     r.z_slot = (int16_t)slot_of[r.z_slot];
+  }
+  // ---- 7. step dependencies.  Slots are reused by liveness, so besides
+  // reads after writes a step must also follow the readers and the writer of
+  // the previous value of every slot it writes.  Pseudo slots stand for the
+  // rank planes, the percentile values and each select scratch set.
+  {
+    const int n = (int)P.steps.size();
+    const int n_real = P.n_inter_slots + P.n_root_slots + P.n_mask_slots;
+    const int ps_rank = n_real, ps_pct = n_real + 1, ps_scr = n_real + 2;
+    std::vector<std::vector<int>> R(n), Wr(n);
+    for (int i = 0; i < n; ++i) {
+      const StepDesc& s = P.steps[i];
+      switch (s.kind) {
+        case SK_GROUP:
+          for (int k = s.insn_off; k < s.insn_off + s.insn_cnt; ++k) {
+            const Insn& in = P.insns[k];
+            if (in.op == I_LOAD) R[i].push_back(in.slot);
+            if (in.op == I_STORE) Wr[i].push_back(in.slot);
+            if (in.op == I_RTHR) R[i].push_back(ps_rank);
+            if (in.op == I_THR && in.slot >= 0) R[i].push_back(ps_pct);
+          }
+          break;
+        case SK_PCT: Wr[i].push_back(ps_pct); break;
+        case SK_RANK: Wr[i].push_back(ps_rank); break;
+        default:
+          for (int j = 0; j < s.rz_cnt; ++j) {
+            const RzDesc& r = P.rz[s.rz_off + j];
+            if (s.kind == SK_RZ_LOCAL || s.kind == SK_RZ_FINAL) {
+              R[i].push_back(r.phi1_slot);
+              R[i].push_back(r.phi2_slot);
+            }
+            if (s.kind == SK_RZ_LOCAL) Wr[i].push_back(ps_scr + r.scratch);
+            else R[i].push_back(ps_scr + r.scratch);
+            if (s.kind == SK_RZ_FINAL) Wr[i].push_back(r.z_slot);
+          }
+          break;
+      }
+    }
+    std::map<int, int> last_w;
+    std::map<int, std::vector<int>> readers;
+    P.dep_off.assign(1, 0);
+    P.deps.clear();
+    for (int i = 0; i < n; ++i) {
+      std::vector<int> d;
+      const int kind = P.steps[i].kind;
+      if (kind == SK_RZ_MERGE || kind == SK_RZ_FLAGS || kind == SK_RZ_FINAL) d.push_back(i - 1);
+      for (int sl : R[i]) {
+        auto it = last_w.find(sl);
+        if (it != last_w.end()) d.push_back(it->second);
+      }
+      for (int sl : Wr[i]) {
+        for (int rd : readers[sl])
+          if (rd != i) d.push_back(rd);
+        auto it = last_w.find(sl);
+        if (it != last_w.end()) d.push_back(it->second);
+      }
+      for (int sl : Wr[i]) { readers[sl].clear(); last_w[sl] = i; }
+      for (int sl : R[i]) readers[sl].push_back(i);
+      std::sort(d.begin(), d.end());
+      d.erase(std::unique(d.begin(), d.end()), d.end());
+      for (int x : d)
+        if (x < i) P.deps.push_back(x);
+      P.dep_off.push_back((int32_t)P.deps.size());
+    }
   }
   *out = std::move(P);
   return VL_OK;

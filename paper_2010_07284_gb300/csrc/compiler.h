@@ -30,6 +30,10 @@ struct ENode {
 struct PlanParams {
   int group_buffers;  // shared-memory tile buffers per group
   int hmax;           // maximum halo (N depth) inside a group
+  // a mask slot is reused only by a value defined at least this many steps
+  // after the last read of its previous value: reuse adds write-after-read
+  // dependencies, which a distant reader keeps off the critical path
+  int reuse_distance = 16;
 };
 
 struct Plan {
@@ -61,6 +65,11 @@ struct Plan {
   std::vector<RankTab> rtab;
   std::vector<float> rvals;
   int n_planes = 0;
+  // step dependencies (CSR): step s may start once every step in
+  // deps[dep_off[s] .. dep_off[s+1]) has finished (reads after writes,
+  // writes after reads and writes of the same slot, the phases of a select
+  // batch, rank codes and percentiles before their readers)
+  std::vector<int32_t> dep_off, deps;
   // accounting: primitive op counts by kind (threshold, not, and, N, rho, other)
   int64_t n_thr = 0, n_not = 0, n_and = 0, n_near = 0, n_other = 0;
 };

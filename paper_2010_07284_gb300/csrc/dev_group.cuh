@@ -77,6 +77,9 @@ VL_DEV bool rank_stage_begin(const GroupCtx& c) {
   return true;
 }
 
+// Most code bits of a rank table (values <= 8191: codes < 2^14).
+constexpr int kRankMaxBits = 14;
+
 VL_DEV uint32_t* gbuf(const GroupCtx& c, int b) { return c.buf + (size_t)b * c.bh * c.bw; }
 
 VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
@@ -96,7 +99,6 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
         __syncthreads();
         stage = 2;
       }
-      const RankTab T = c.rtab[I.a];
       const int nb = I.ch;
       const unsigned K = (uint16_t)I.img;
       const bool lt = I.b & 1;
@@ -111,25 +113,39 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
         uint32_t word = 0;
         if (y >= 0 && y < c.H && wg >= 0 && wg < c.Wp) {
           const uint32_t* s0 = sp + (size_t)(i - s_row0) * bw + j;
-          const uint32_t* g0 = c.planes + (size_t)T.plane0 * c.pstride + (size_t)y * c.Wp + wg;
+          const uint32_t* g0 = c.planes + (size_t)I.slot * c.pstride + (size_t)y * c.Wp + wg;
           // bit-sliced c >= K over the code planes, most significant first
-          uint32_t gt = 0, eq = 0xFFFFFFFFu;
-          for (int b = nb - 1; b >= 0; --b) {
-            const uint32_t pw = stage ? s0[(size_t)b * per_plane] : ldcg(g0 + (size_t)b * c.pstride);
-            if ((K >> b) & 1u) {
-              eq &= pw;
-            } else {
-              gt |= eq & pw;
-              eq &= ~pw;
+          // (K's bits are the same for every thread: the branch is uniform)
+          // (two separate loops: a select between a shared and a global load
+          // inside one loop made every word wait for global memory)
+          uint32_t gt = 0, eq = 0xFFFFFFFFu, nan = 0;
+          if (stage) {
+#pragma unroll 4
+            for (int b = kRankMaxBits - 1; b >= 0; --b) {
+              if (b >= nb) continue;
+              const uint32_t pw = s0[b * per_plane];
+              if ((K >> b) & 1u) {
+                eq &= pw;
+              } else {
+                gt |= eq & pw;
+                eq &= ~pw;
+              }
             }
+            if (lt) nan = s0[nb * per_plane];
+          } else {
+            for (int b = nb - 1; b >= 0; --b) {
+              const uint32_t pw = ldcg(g0 + (size_t)b * c.pstride);
+              if ((K >> b) & 1u) {
+                eq &= pw;
+              } else {
+                gt |= eq & pw;
+                eq &= ~pw;
+              }
+            }
+            if (lt) nan = ldcg(g0 + (size_t)nb * c.pstride);
           }
           const uint32_t ge = gt | eq;
-          if (lt) {
-            const uint32_t nan = stage ? s0[(size_t)nb * per_plane] : ldcg(g0 + (size_t)nb * c.pstride);
-            word = ~ge & ~nan;
-          } else {
-            word = ge;
-          }
+          word = lt ? (~ge & ~nan) : ge;
           word &= vmask(wg, c.W);
         }
         d[i * bw + j] = word;

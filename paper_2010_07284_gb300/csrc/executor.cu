@@ -6,8 +6,8 @@
 // items with an atomic counter, so an item's dependencies were popped by
 // CTAs already running: the earliest unfinished item can always progress,
 // and the launch needs no co-residency guarantee.  Before running, an item
-// waits (bounded, with back-off) until every sub-item of its job's previous
-// step is done; a wait that runs out records VL_ERR_TIMEOUT in the job's
+// waits (bounded, with back-off) until every sub-item of each step its
+// step depends on is done; a wait that runs out records VL_ERR_TIMEOUT in the job's
 // status word and the job's remaining items are skipped.  This replaces the
 // paper's host-side event chaining and host-checked CCL termination
 // (Sec. 3.2-3.3) with device-side counters: the host never waits.
@@ -176,18 +176,20 @@ __global__ void __launch_bounds__(EXEC_THREADS, 2) k_exec(ExecLaunch L) {
     if (threadIdx.x == 0) {
       if (L.trace) t_pop = now_ns();
       int skip = 0;
-      if (it.step > 0) {
-        const int32_t* ctr = L.done + ci - 1;
-        const int need = L.need[ci - 1];
+      const int d0 = J.dep_off[it.step], d1 = J.dep_off[it.step + 1];
+      // a negative limit makes every wait expire at once (tests of the
+      // timeout path); otherwise poll with back-off up to the limit
+      if (d1 > d0 && L.spin_limit < 0) {
+        set_status(J.status, ST_TIMEOUT);
+        skip = 1;
+      }
+      for (int q = d0; q < d1 && !skip; ++q) {
+        const int dep = J.step_base + J.deps[q];
+        const int32_t* ctr = L.done + dep;
+        const int need = L.need[dep];
         long long spins = 0;
         unsigned ns = 32;
-        // a negative limit makes every wait expire at once (tests of the
-        // timeout path); otherwise poll with back-off up to the limit
-        if (L.spin_limit < 0) {
-          set_status(J.status, ST_TIMEOUT);
-          skip = 1;
-        }
-        while (!skip && ld_acquire(ctr) < need) {
+        while (ld_acquire(ctr) < need) {
           if (++spins > L.spin_limit) {
             set_status(J.status, ST_TIMEOUT);
             skip = 1;

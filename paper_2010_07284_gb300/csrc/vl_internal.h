@@ -56,7 +56,8 @@ enum InsnOp : uint8_t {
   I_STORE = 8,   // materialised mask slot `slot` = a   (core region only)
   I_ANDNOT = 9,  // dst = a and not b
   I_RTHR = 10,   // dst = threshold by rank code: table a, code bound K = img
-                 //   (as uint16), planes = ch; aux bit0: lt (see RankTab)
+                 //   (as uint16), code bits = ch, first plane = slot; aux
+                 //   bit0: lt (see RankTab)
 };
 
 struct Insn {        // 16 bytes
@@ -152,6 +153,8 @@ struct DevJob {
   uint32_t* const* slots;       // materialised mask slots
   const Insn* insns;
   const StepDesc* steps;        // this job's formula steps
+  const int32_t* dep_off;       // step dependencies (CSR, job-relative steps)
+  const int32_t* deps;
   const RzDesc* rz;
   const PctDesc* pct;
   float* pct_val;               // percentile values by slot

@@ -36,10 +36,36 @@ def _select(phi1, phi2, conn):
     return np.isin(lab, hit) & (lab > 0)
 
 
+def random_topological_order(plan: dict, seed: int):
+    """A random order of the plan's steps that respects its dependencies
+    (what the persistent executor may run, step by step)."""
+    rng = np.random.default_rng(seed)
+    deps = plan["deps"]
+    n = len(deps)
+    users = [[] for _ in range(n)]
+    indeg = [len(set(d)) for d in deps]
+    for s, d in enumerate(deps):
+        for x in set(d):
+            users[x].append(s)
+    ready = [s for s in range(n) if indeg[s] == 0]
+    order = []
+    while ready:
+        k = int(rng.integers(0, len(ready)))
+        s = ready.pop(k)
+        order.append(s)
+        for u in users[s]:
+            indeg[u] -= 1
+            if indeg[u] == 0:
+                ready.append(u)
+    assert len(order) == n, "dependency cycle"
+    return order
+
+
 def simulate(plan: dict, images, masks_by_image: dict, conn: int, seed: int = 0,
-             tile_rows: int = GTH, tile_words: int = GTWW):
+             tile_rows: int = GTH, tile_words: int = GTWW, order=None):
     """images: list of (C, H, W) float32 arrays (None for mask images);
-    masks_by_image: {image index: (H, W) bool}.  Returns one bool mask per root."""
+    masks_by_image: {image index: (H, W) bool}.  Steps run in `order` (default:
+    the listed order).  Returns one bool mask per root."""
     rng = np.random.default_rng(seed)
     some = next(x for x in images if x is not None) if any(x is not None for x in images) else None
     H, W = some.shape[1:] if some is not None else next(iter(masks_by_image.values())).shape
@@ -58,7 +84,8 @@ def simulate(plan: dict, images, masks_by_image: dict, conn: int, seed: int = 0,
     insns = plan["insns"]
     sels = plan["selects"]
     pending_sel = {}
-    for si, st in enumerate(plan["steps"]):
+    for si in (order if order is not None else range(len(plan["steps"]))):
+        st = plan["steps"][si]
         kind = st["kind"]
         if kind == 1:
             halo = st["halo"]

@@ -71,11 +71,12 @@ def test_malformed_formulas_are_rejected(nodes, roots, conn, code):
     assert e.value.code == code
 
 
-def _check_sim(f, images, masks=None, conn=8, seed=0):
+def _check_sim(f, images, masks=None, conn=8, seed=0, shuffle=None):
     masks = masks or {}
     F = vg.compile_formula(_rec(f), f.roots, conn)
     plan = F.plan()
-    got = plan_sim.simulate(plan, images, masks, conn, seed=seed)
+    order = plan_sim.random_topological_order(plan, shuffle) if shuffle is not None else None
+    got = plan_sim.simulate(plan, images, masks, conn, seed=seed, order=order)
     mlist = [masks[k] for k in sorted(masks)] if masks else []
     # the oracle indexes float images and masks separately
     exp = oracle.evaluate(_rec(f), f.roots, [im for im in images if im is not None], mlist,
@@ -210,3 +211,24 @@ def test_rank_thresholds_with_ties_signed_zeros_and_nan(conn):
                               dtype=np.float32), size=(1, 37, 140)).astype(np.float32)
     plan = _check_sim(f, [img], conn=conn)
     assert any(ins["op"] == 10 for ins in plan["insns"])
+
+
+@pytest.mark.parametrize("shuffle", [1, 2, 3])
+def test_step_dependencies_allow_any_respecting_order(shuffle):
+    """Steps run in a random order that respects the plan's dependencies
+    (as the executor may overlap them) still give the oracle's masks: slot
+    reuse, select batches and rank codes are all ordered by the dependencies."""
+    pytest.importorskip("scipy")
+    f = wl.random_dag(2000, seed=shuffle)
+    img = wl.uniform_image(40, 300, seed=shuffle)
+    plan = _check_sim(f, [img], conn=8, shuffle=shuffle)
+    order = plan_sim.random_topological_order(plan, shuffle)
+    assert order != list(range(len(order)))  # the order really differs
+
+
+def test_step_dependencies_with_percentiles_and_masks():
+    pytest.importorskip("scipy")
+    f = wl.config4_formula()
+    img = wl.mri_phantom_batch([(70, 90)], seed=4)[0]
+    for k in range(3):
+        _check_sim(f, [img], conn=8, shuffle=10 + k)
