@@ -320,7 +320,7 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
   // registers.  In each round the lanes of a warp whose roots form the same
   // pair elect one leader to link them; a link that fails because its root
   // was linked elsewhere leaves the follow-up union (old parent, lo) on the
-  // leader.  A flatten after every level keeps the next level's finds short.
+  // leader.
   const int cap = nruns + 64;
   bool ok = true;
   for (int level = 0; (1 << level) < ns; ++level) {
@@ -409,14 +409,8 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
       }
     }
     __syncthreads();
-    if ((2 << level) < ns) {  // flatten before the next level
-      for (int i = tid; i < nruns; i += blockDim.x) {
-        const int root = s_find(s.parent, i, cap);
-        if (root >= 0) s.parent[i] = root;
-        else ok = false;
-      }
-      __syncthreads();
-    }
+    // (no flatten between levels: path halving in s_find keeps the next
+    // level's walks short, and a full pass over all runs costs more)
   }
   // 4. flatten
   for (int i = tid; i < nruns; i += blockDim.x) {
