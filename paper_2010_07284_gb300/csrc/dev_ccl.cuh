@@ -604,14 +604,39 @@ VL_DEV void ccl_publish_border(CclSmem& s, const CclGeom& g, int32_t* G) {
   }
 }
 
-// Write labels of the tile (after ENC_LABEL): coalesced row segments.
-VL_DEV void ccl_write_labels(const CclSmem& s, const CclGeom& g, int32_t* labels) {
+// Write labels of the tile (after ENC_LABEL).  First every strip run takes
+// its root's encoded value (after the flatten non-roots point at roots, and
+// roots are not written, so the pass needs no ordering), then each lane
+// writes 4 consecutive pixels per step: a warp covers 128 pixels of a row
+// with 16-byte stores when rows are 16-byte aligned.
+VL_DEV void ccl_write_labels(CclSmem& s, const CclGeom& g, int32_t* labels) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < s.nruns; i += blockDim.x) {
+    const int p = s.parent[i];
+    if (p >= 0) s.parent[i] = s.parent[p];
+  }
+  __syncthreads();
   const int x_end = min(32 * g.tww, g.W - 32 * g.w0);
+  const bool vec = (g.W & 3) == 0;
   for (int r = warp; r < g.th; r += nw) {
     int32_t* row = labels + (size_t)(g.r0 + r) * g.W + 32 * g.w0;
-    for (int x = lane; x < x_end; x += 32) row[x] = mbit(s, r, x) ? pixel_value(s, r, x) : -1;
+    const int k = r >> 1;
+    for (int x0 = 4 * lane; x0 < x_end; x0 += 128) {
+      const int w = x0 >> 5, b = x0 & 31;
+      const uint32_t bits = s.m[r][w] >> b;
+      const uint32_t st = s.st[k][w];
+      const int base = s.base[k] + s.pre[k][w] - 1;
+      int v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        v[q] = ((bits >> q) & 1u) ? -s.parent[base + __popc(st & le_mask(b + q))] - 2 : -1;
+      if (vec && x0 + 4 <= x_end) {
+        *reinterpret_cast<int4*>(row + x0) = make_int4(v[0], v[1], v[2], v[3]);
+      } else {
+        for (int q = 0; q < 4 && x0 + q < x_end; ++q) row[x0 + q] = v[q];
+      }
+    }
   }
 }
 
