@@ -155,6 +155,63 @@ def oracle_sample(rows: int):
     return r.n_primitive * rows * W / dt / 1e9, dt, r.n_primitive
 
 
+def leg_grow_7680(ctx, stream, flush, runs: int = 5) -> dict:
+    """The case-study spec (two thresholds and grow, Sec. 4.2) on a 7680 x
+    7680 upscaled MRI-shaped slice, the scale of the paper's only published
+    timings: device time with the image resident, and end to end through the
+    public API (pinned host image in, result mask out)."""
+    import torch
+    import workloads as wl
+    from workloads.images import upscaled_slice
+    f = wl.grow_spec_formula()
+    img = upscaled_slice(7680)
+    F = ctx.compile(wl.formula_to_records(f), f.roots, 8)
+    n_prim = F.info()["n_primitive"]
+    P = img.shape[1] * img.shape[2]
+    pin = torch.from_numpy(img).pin_memory()
+    out = np.empty((img.shape[1], ((img.shape[2] + 127) // 128) * 4), dtype=np.uint32)
+    out_t = torch.from_numpy(out).pin_memory()
+    with torch.cuda.stream(stream):
+        im = ctx.image(pin.numpy(), stream)
+        b = ctx.batch([(F, [im])], stream)
+        for _ in range(2):
+            b.run(stream)
+        ev = []
+        for _ in range(runs):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            b.run(stream)
+            z.record(stream)
+            ev.append((a, z))
+        stream.synchronize()
+        if b.result(0).status_word() != 0:
+            raise SystemExit("grow 7680 failed")
+        dev_ms = float(np.mean([a.elapsed_time(z) for a, z in ev]))
+        e2e = []
+        for k in range(runs + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            im2 = ctx.image(pin.numpy(), stream)
+            r = ctx.eval(F, [im2], stream=stream)
+            r.mask_into(0, out_t.numpy(), on_device=False, stream=stream)
+            t1 = time.perf_counter()
+            if r.sync() != 0:
+                raise SystemExit("grow 7680 e2e failed")
+            if k:
+                e2e.append(1e3 * (t1 - t0))
+            r.close()
+            im2.close()
+        b.close()
+        im.close()
+    return {"workload": "grow(I > 0.95, I > 0.86) on a 7680x7680 upscaled MRI-shaped slice (59 Mpx)",
+            "device_ms": dev_ms, "e2e_ms": float(np.mean(e2e)),
+            "value": n_prim * P / (dev_ms / 1e3) / 1e9, "unit": "Gpixel-ops/s",
+            "e2e_bytes": {"h2d": int(img.nbytes), "d2h": int(out.nbytes)},
+            "paper_context_ms": {"TITAN Xp (OpenCL, D2H included)": 600,
+                                 "Intel HD 630 (OpenCL)": 3000, "i7-7700 CPU tool": 1100}}
+
+
 def leg_ccl(ctx, stream, flush, peak: float, S: int = 8192, runs: int = 6) -> dict:
     """Full connected-component labelling (int32 labels, 8-adjacency) of an
     S x S Bernoulli(0.5) mask: 2 untimed runs, then CUDA events per run."""
@@ -517,6 +574,7 @@ def main():
         # ---- MRI-shaped batch and the serving stream
         line["mri_batch"] = leg_mri_batch(ctx, stream, flush)
         line["serving"] = leg_serving(ctx, stream)
+        line["grow_7680"] = leg_grow_7680(ctx, stream, flush)
         # ---- CPU oracle on a bounded sample (rank 0 only)
         if rank == 0:
             v, dt, _ = oracle_sample(CPU_ROWS_BASE)

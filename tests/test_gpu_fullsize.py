@@ -2,8 +2,9 @@
 oracle: connected components and rho on 8192 x 8192 masks (noise at four
 densities around the percolation thresholds, and the adversarial spiral,
 checkerboard and rings), the 2000-node random formula at 2048 x 2048 with
-4-adjacency, and the MRI-shaped batch of 4096 images in one autotuned
-launch (a seeded sample of its images checked one by one)."""
+4-adjacency, the MRI-shaped batch of 4096 images in one autotuned launch (a
+seeded sample of its images checked one by one), and the case-study grow
+spec on a 7680 x 7680 slice."""
 from __future__ import annotations
 
 import numpy as np
@@ -89,7 +90,7 @@ def test_mri_batch_4096_autotuned():
     f = wl.config4_formula()
     rec = wl.formula_to_records(f)
     sides = wl.mri_side_lengths(4096, seed=0)
-    imgs = wl.mri_phantom_batch(sides, seed=0)
+    imgs = wl.mri_phantom_batch_parallel(sides, seed=0)
     ctx = vg.Context()
     F = ctx.compile(rec, f.roots, 8)
     s = torch.cuda.Stream()
@@ -110,3 +111,20 @@ def test_mri_batch_4096_autotuned():
             exp = oracle.evaluate(rec, f.roots, [imgs[k]], conn=8).masks
             assert_same([res.mask(r, s) for r in range(len(f.roots))], exp, f"image {k}")
     ctx.close()
+
+
+def test_grow_spec_7680_both_forms():
+    """The case-study spec of Sec. 4.2 at its timing scale: two thresholds and
+    grow on a 7680 x 7680 upscaled MRI-shaped slice (about 60 Mpx)."""
+    torch_cuda()
+    from workloads.images import upscaled_slice
+    f = wl.grow_spec_formula()
+    rec = wl.formula_to_records(f)
+    img = upscaled_slice(7680)
+    exp = oracle.evaluate(rec, f.roots, [img], conn=8).masks[0]
+    for mode in ("fused", "plain"):
+        ctx = context(mode)
+        F = ctx.compile(rec, f.roots, 8)
+        res = ctx.eval(F, [ctx.image(img)])
+        assert res.sync() == 0, ctx.last_error()
+        assert_same([res.mask(0)], [exp], f"grow 7680 {mode}")

@@ -225,3 +225,14 @@ def mri_phantom_batch_parallel(sides: Sequence[Sequence[int]], seed: int = 0,
     with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
         parts = list(ex.map(_phantom_chunk, chunks))
     return [im for part in parts for im in part]
+
+
+def upscaled_slice(side: int = 7680, base: int = 240, seed: int = 0) -> np.ndarray:
+    """One MRI-shaped slice (channel 0 of an MRI phantom, base x base)
+    upscaled bilinearly to side x side: a stand-in for the paper's upscaled
+    2D slice of its case-study timing (about 60 Mpx at 7680 x 7680).
+    Returns a (1, side, side) float32 array."""
+    from scipy import ndimage as nd
+    ph = mri_phantom(base, base, np.random.default_rng([seed, 7680]))
+    z = nd.zoom(ph[0].astype(np.float64), side / base, order=1, mode="nearest")
+    return z[:side, :side].astype(np.float32)[None]
