@@ -80,12 +80,16 @@ VL_DEV bool rank_stage_begin(const GroupCtx& c) {
 // Most code bits of a rank table (values <= 8191: codes < 2^14).
 constexpr int kRankMaxBits = 14;
 
-VL_DEV uint32_t* gbuf(const GroupCtx& c, int b) { return c.buf + (size_t)b * c.bh * c.bw; }
 
-VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
+// BH, BW > 0: the buffer shape as compile-time constants (index arithmetic
+// and divisions by the row length fold into multiplies); 0: read from c.
+template <int BH, int BW>
+VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-  const int bw = c.bw;
+  const int bw = BW > 0 ? BW : c.bw;
+  const int bhbw = (BH > 0 ? BH : c.bh) * bw;
+  auto gbuf = [&](int b) { return c.buf + (size_t)b * bhbw; };
   // 0: planes read from global memory; 1: being staged; 2: staged
   int stage = rank_stage_begin(c) ? 1 : 0;
   for (int k = 0; k < n_insn; ++k) {
@@ -105,7 +109,7 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
       const int per_plane = (c.th + 2 * c.rank_halo) * bw;
       const uint32_t* sp = c.stage + rank_stage_words(c, I.a);
       const int s_row0 = c.halo - c.rank_halo;  // buffer row of stage row 0
-      uint32_t* d = gbuf(c, I.dst);
+      uint32_t* d = gbuf(I.dst);
       const int nwords = rows * bw;
       for (int idx = tid; idx < nwords; idx += nthr) {
         const int i = i_lo + idx / bw, j = idx - (idx / bw) * bw;
@@ -155,7 +159,7 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
       const float* plane = im.data + (size_t)I.ch * c.H * c.pitch;
       const float t = (I.slot >= 0) ? c.pct_val[I.slot] : I.t;
       const bool lt = (I.b & 1);
-      uint32_t* d = gbuf(c, I.dst);
+      uint32_t* d = gbuf(I.dst);
       const int nwords = rows * bw;
       // one 16-byte load per lane covers 4 pixels: a warp reads 4 words
       // (512 bytes) per load and keeps UNR loads in flight; the 8 lanes of a
@@ -192,7 +196,7 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
         }
       }
     } else if (I.op == I_STORE) {
-      const uint32_t* a = gbuf(c, I.a);
+      const uint32_t* a = gbuf(I.a);
       uint32_t* g = c.slots[I.slot];
       const int nwords = c.th * c.tww;
       for (int idx = tid; idx < nwords; idx += nthr) {
@@ -200,9 +204,9 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
         g[(size_t)(c.r0 + r) * c.Wp + c.w0 + w] = a[(c.halo + r) * bw + 1 + w];
       }
     } else {
-      uint32_t* d = gbuf(c, I.dst);
-      const uint32_t* a = gbuf(c, I.a);
-      const uint32_t* b = gbuf(c, I.b);
+      uint32_t* d = gbuf(I.dst);
+      const uint32_t* a = gbuf(I.a);
+      const uint32_t* b = gbuf(I.b);
       const uint32_t* g = (I.op == I_LOAD) ? c.slots[I.slot] : nullptr;
       const int nwords = rows * bw;
       for (int idx = tid; idx < nwords; idx += nthr) {
@@ -235,6 +239,20 @@ VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
     __syncthreads();
   }
   if (stage == 1) cp_async_wait_all();  // no copy may outlive the tile
+}
+
+// The group interpreter for the tile shapes the autotuner tries (buffer
+// rows = tile rows + 16, words = tile words + 2), generic otherwise.
+VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
+  const int key = c.bh * 1000 + c.bw;
+  switch (key) {
+    case 32 * 1000 + 34: group_tile_t<32, 34>(c, insns, n_insn); break;  // 16 x 32
+    case 48 * 1000 + 18: group_tile_t<48, 18>(c, insns, n_insn); break;  // 32 x 16
+    case 48 * 1000 + 34: group_tile_t<48, 34>(c, insns, n_insn); break;  // 32 x 32
+    case 80 * 1000 + 18: group_tile_t<80, 18>(c, insns, n_insn); break;  // 64 x 16
+    case 80 * 1000 + 10: group_tile_t<80, 10>(c, insns, n_insn); break;  // 64 x 8
+    default: group_tile_t<0, 0>(c, insns, n_insn); break;
+  }
 }
 
 }  // namespace vl
