@@ -212,6 +212,62 @@ def leg_grow_7680(ctx, stream, flush, runs: int = 5) -> dict:
                                  "Intel HD 630 (OpenCL)": 3000, "i7-7700 CPU tool": 1100}}
 
 
+def leg_formula_scaling(ctx, stream, flush, image, sizes=(10, 100, 500, 1000, 2000),
+                        runs: int = 3) -> dict:
+    """Time against formula size (Sec. 4.1): sequential formulas f(g(...(x)))
+    and random DAGs of growing size on the same resident 2048 x 2048 image,
+    the fused persistent form beside the plain per-operator form; at 2000
+    nodes also the deep-N and the reachability chains."""
+    import torch
+    import workloads as wl
+    P = H * W
+
+    def timed(F, mode, n):
+        ms = []
+        with torch.cuda.stream(stream):
+            b = ctx.batch([(F, [image])], stream) if mode == "fused" else None
+            for k in range(n + 1):
+                flush.zero_()
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                if b is not None:
+                    b.run(stream)
+                else:
+                    r = ctx.eval(F, [image], stream=stream, mode="plain")
+                z.record(stream)
+                stream.synchronize()
+                st = b.result(0).status_word() if b is not None else r.sync()
+                if st != 0:
+                    raise SystemExit(f"formula scaling ({mode}) failed: {ctx.last_error()}")
+                if b is None:
+                    r.close()
+                if k:
+                    ms.append(a.elapsed_time(z))
+            if b is not None:
+                b.close()
+        return float(np.mean(ms))
+
+    rows = []
+    cases = [("sequential", n, lambda n: wl.sequential_dag(n, seed=0)) for n in sizes]
+    cases += [("random", n, lambda n: wl.random_dag(n, seed=0, max_depth=min(500, n)))
+              for n in sizes]
+    cases += [(f"sequential-{m}", 2000, lambda n, m=m: wl.sequential_dag(n, seed=0, mix=m))
+              for m in ("near", "reach")]
+    for kind, n, make in cases:
+        f = make(n)
+        F = ctx.compile(wl.formula_to_records(f), f.roots, CONN)
+        info = F.info()
+        fused = timed(F, "fused", runs)
+        plain = timed(F, "plain", max(2, runs - 1))
+        rows.append({"kind": kind, "nodes": n, "n_primitive": info["n_primitive"],
+                     "n_reach": info["n_reach"], "fused_ms": fused, "plain_ms": plain,
+                     "fused_gpixel_ops_s": info["n_primitive"] * P / (fused / 1e3) / 1e9,
+                     "fused_over_plain": plain / fused})
+        F.close()
+    return {"image": [H, W], "connectivity": CONN, "l2": "flushed before every run",
+            "rows": rows}
+
+
 def leg_ccl(ctx, stream, flush, peak: float, S: int = 8192, runs: int = 6) -> dict:
     """Full connected-component labelling (int32 labels, 8-adjacency) of an
     S x S Bernoulli(0.5) mask: 2 untimed runs, then CUDA events per run."""
@@ -413,7 +469,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain/ccl/e2e/cpu legs")
-    ap.add_argument("--leg", default="", choices=["", "ccl"],
+    ap.add_argument("--leg", default="", choices=["", "ccl", "scaling"],
                     help="run only this leg and print its figures (for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -443,6 +499,14 @@ def main():
         stream = torch.cuda.Stream()
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         print(json.dumps({"leg": "ccl", **leg_ccl(ctx, stream, flush, measured_peaks()[0])}), flush=True)
+        return
+    if args.leg == "scaling":
+        stream = torch.cuda.Stream()
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(stream):
+            image = ctx.image(wl.uniform_image(H, W, seed=0), stream)
+        print(json.dumps({"leg": "formula_scaling",
+                          **leg_formula_scaling(ctx, stream, flush, image)}), flush=True)
         return
     f = wl.random_dag(N_NODES, seed=DAG_SEED)
     rec = wl.formula_to_records(f)
@@ -575,6 +639,7 @@ def main():
         line["mri_batch"] = leg_mri_batch(ctx, stream, flush)
         line["serving"] = leg_serving(ctx, stream)
         line["grow_7680"] = leg_grow_7680(ctx, stream, flush)
+        line["formula_scaling"] = leg_formula_scaling(ctx, stream, flush, image)
         # ---- CPU oracle on a bounded sample (rank 0 only)
         if rank == 0:
             v, dt, _ = oracle_sample(CPU_ROWS_BASE)

@@ -6,7 +6,7 @@ library: the C evaluator lives in ``vl_oracle.c`` and the derived-operator
 expansion in ``expand.py``.
 """
 from .oracle import (build, lib_path, expand, threshold, op_not, op_and,
-                     near, reach, ccl, percentile, evaluate, OracleResult)
+                     near, reach, ccl, arith, percentile, evaluate, OracleResult)
 
 __all__ = ["build", "lib_path", "expand", "threshold", "op_not", "op_and",
-           "near", "reach", "ccl", "percentile", "evaluate", "OracleResult"]
+           "near", "reach", "ccl", "arith", "percentile", "evaluate", "OracleResult"]

@@ -23,7 +23,9 @@ _LOCK = threading.Lock()
 _LIB: Optional[C.CDLL] = None
 
 _OPCODE = {"TRUE": 0, "FALSE": 1, "THR_GT": 2, "THR_LT": 3, "PCT_GT": 4,
-           "PCT_LT": 5, "MASK": 6, "NOT": 7, "AND": 8, "NEAR": 9, "REACH": 10}
+           "PCT_LT": 5, "MASK": 6, "NOT": 7, "AND": 8, "NEAR": 9, "REACH": 10,
+           "VALUE": 16, "ADD": 17, "SUB": 18, "MUL": 19, "DIV": 20}
+_ARITH = {"ADD": 0, "SUB": 1, "MUL": 2, "DIV": 3}
 
 
 class _Node(C.Structure):
@@ -44,8 +46,10 @@ def build(force: bool = False) -> str:
         if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
             os.makedirs(_BUILD, exist_ok=True)
             tmp = out + f".tmp{os.getpid()}"
+            # no contraction of a*b+c into one rounding: every arithmetic
+            # result is rounded on its own
             subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-fPIC",
-                                   "-shared", "-o", tmp, _SRC])
+                                   "-ffp-contract=off", "-shared", "-o", tmp, _SRC])
             os.replace(tmp, out)
     return out
 
@@ -63,6 +67,7 @@ def _lib() -> C.CDLL:
         lib.vlo_reach.restype = C.c_int
         lib.vlo_ccl.argtypes = [P, C.c_int, C.c_int, C.c_int, P]
         lib.vlo_ccl.restype = C.c_int64
+        lib.vlo_arith.argtypes = [C.c_int, P, P, C.c_float, C.c_int64, P]
         lib.vlo_percentile.argtypes = [P, C.c_int64, C.c_double]
         lib.vlo_percentile.restype = C.c_float
         lib.vlo_eval.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.c_int,
@@ -129,6 +134,21 @@ def ccl(m, conn: int = 8):
     return lab, int(n)
 
 
+def arith(op: str, a: np.ndarray, b) -> np.ndarray:
+    """a (op) b pixel by pixel in float32, op one of ADD, SUB, MUL, DIV; b is
+    an array of a's shape or a float32 constant."""
+    x = np.ascontiguousarray(a, dtype=np.float32)
+    out = np.empty(x.shape, dtype=np.float32)
+    if np.isscalar(b):
+        _lib().vlo_arith(_ARITH[op], _ptr(x), None, float(np.float32(b)), x.size, _ptr(out))
+    else:
+        y = np.ascontiguousarray(b, dtype=np.float32)
+        if y.shape != x.shape:
+            raise ValueError("arith operands differ in shape")
+        _lib().vlo_arith(_ARITH[op], _ptr(x), _ptr(y), 0.0, x.size, _ptr(out))
+    return out
+
+
 def percentile(channel: np.ndarray, q: float) -> float:
     ch = np.ascontiguousarray(channel, dtype=np.float32)
     return float(_lib().vlo_percentile(_ptr(ch), ch.size, float(q)))
@@ -147,7 +167,8 @@ def evaluate(nodes: Sequence, roots: Sequence[int],
              images: Sequence[np.ndarray] = (), masks: Sequence[np.ndarray] = (),
              conn: int = 8, shape=None) -> OracleResult:
     """Evaluate a formula (records (op, a, b, image, channel, t, q)) on a list
-    of (C, H, W) float32 images and (H, W) masks; all share H, W."""
+    of (C, H, W) float32 or uint16 images and (H, W) masks; all share H, W.
+    A uint16 pixel is its integer value, which float32 holds exactly."""
     prim, proots = expand(nodes, roots)
     imgs = [np.ascontiguousarray(im, dtype=np.float32) for im in images]
     msks = [_mask(m) for m in masks]

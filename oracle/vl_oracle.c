@@ -24,7 +24,13 @@
  *     minimum linear index y*W + x, background -1;
  *   - percentile of a channel: the value at rank floor(q (n-1)) of the
  *     ascending sort of its n = H*W values (the "percentiles" normalisation
- *     of Sec. 4.2; no interpolation).
+ *     of Sec. 4.2; no interpolation); NaN values sort after +infinity;
+ *   - number terms (basic arithmetic beside the SLCS primitives, Sec. 3):
+ *     VALUE reads an image channel as numbers; ADD, SUB, MUL, DIV combine
+ *     two terms (or a term and a float32 constant) pixel by pixel in
+ *     IEEE-754 binary32, round to nearest even, each result stored as a
+ *     float before the next operation uses it.  Thresholds and percentiles
+ *     may compare a number term instead of an image channel.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -160,8 +166,11 @@ VLO_EXPORT int64_t vlo_ccl(const uint8_t* m, int H, int W, int conn,
 
 /* ----------------------------------------------------------- percentile -- */
 
+/* Ascending order with every NaN after +infinity (NaNs equal). */
 static int cmp_float(const void* a, const void* b) {
   float x = *(const float*)a, y = *(const float*)b;
+  int nx = x != x, ny = y != y;
+  if (nx || ny) return nx - ny;
   return (x > y) - (x < y);
 }
 
@@ -183,6 +192,26 @@ VLO_EXPORT float vlo_percentile(const float* img, int64_t n, double q) {
   return r;
 }
 
+/* ------------------------------------------------------------ arithmetic -- */
+
+enum { VLO_ARITH_ADD = 0, VLO_ARITH_SUB = 1, VLO_ARITH_MUL = 2, VLO_ARITH_DIV = 3 };
+
+/* out[i] = a[i] (op) b[i], or a[i] (op) c when b is NULL; every result is
+ * rounded to float by the store. */
+VLO_EXPORT void vlo_arith(int op, const float* a, const float* b, float c, int64_t n,
+                          float* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    float x = a[i], y = b ? b[i] : c, r;
+    switch (op) {
+      case VLO_ARITH_ADD: r = x + y; break;
+      case VLO_ARITH_SUB: r = x - y; break;
+      case VLO_ARITH_MUL: r = x * y; break;
+      default: r = x / y; break;
+    }
+    out[i] = r;
+  }
+}
+
 /* ------------------------------------------------------- DAG evaluation -- */
 
 /* Primitive operators only: derived connectives are expanded before a DAG
@@ -190,7 +219,8 @@ VLO_EXPORT float vlo_percentile(const float* img, int64_t n, double q) {
 enum {
   VLO_TRUE = 0, VLO_FALSE = 1, VLO_THR_GT = 2, VLO_THR_LT = 3,
   VLO_PCT_GT = 4, VLO_PCT_LT = 5, VLO_MASK = 6, VLO_NOT = 7, VLO_AND = 8,
-  VLO_NEAR = 9, VLO_REACH = 10
+  VLO_NEAR = 9, VLO_REACH = 10, VLO_VALUE = 16, VLO_ADD = 17, VLO_SUB = 18,
+  VLO_MUL = 19, VLO_DIV = 20
 };
 
 typedef struct {
@@ -199,38 +229,63 @@ typedef struct {
   double q;
 } vlo_node;
 
+static int is_number_op(int op) {
+  return op == VLO_VALUE || op == VLO_ADD || op == VLO_SUB || op == VLO_MUL || op == VLO_DIV;
+}
+
+/* Number of operands (node indexes) of a node.  Thresholds and percentiles
+ * have one when they compare a number term (a >= 0); an arithmetic node with
+ * b < 0 takes the constant t as its second operand. */
+static int node_arity(const vlo_node* d) {
+  switch (d->op) {
+    case VLO_NOT: case VLO_NEAR: return 1;
+    case VLO_AND: case VLO_REACH: return 2;
+    case VLO_THR_GT: case VLO_THR_LT: case VLO_PCT_GT: case VLO_PCT_LT: return d->a >= 0 ? 1 : 0;
+    case VLO_ADD: case VLO_SUB: case VLO_MUL: case VLO_DIV: return d->b >= 0 ? 2 : 1;
+    default: return 0;
+  }
+}
+
 /* Evaluate a primitive DAG in index order.  images[i] is a float32 planar
  * (C, H, W) array; masks[i] a uint8 (H, W) array (for MASK atoms, indexed by
  * node.image).  out_roots[r] receives the (H, W) uint8 mask of roots[r].
- * Intermediate masks are freed after their last consumer.  Returns 0, -1 on
- * malformed input, -2 when memory runs out. */
+ * Number terms are float (H, W) arrays.  Intermediate values are freed
+ * after their last consumer.  Returns 0, -1 on malformed input, -2 when
+ * memory runs out. */
 VLO_EXPORT int vlo_eval(const vlo_node* nodes, int n_nodes, const int32_t* roots,
                         int n_roots, const float* const* images, int n_images,
                         int C, const uint8_t* const* masks, int n_masks, int H,
                         int W, int conn, uint8_t* const* out_roots) {
   int64_t n = (int64_t)H * W;
   if (n_nodes < 0 || n_roots < 0 || (conn != 4 && conn != 8)) return -1;
-  uint8_t** val = (uint8_t**)calloc((size_t)(n_nodes > 0 ? n_nodes : 1), sizeof(uint8_t*));
+  void** val = (void**)calloc((size_t)(n_nodes > 0 ? n_nodes : 1), sizeof(void*));
   int32_t* uses = (int32_t*)calloc((size_t)(n_nodes > 0 ? n_nodes : 1), sizeof(int32_t));
   if (!val || !uses) { free(val); free(uses); return -2; }
   int rc = 0;
   for (int i = 0; i < n_nodes; ++i) {
     const vlo_node* d = &nodes[i];
-    int arity = (d->op == VLO_NOT || d->op == VLO_NEAR) ? 1
-              : (d->op == VLO_AND || d->op == VLO_REACH) ? 2 : 0;
+    int arity = node_arity(d);
     if (arity >= 1 && (d->a < 0 || d->a >= i)) { rc = -1; goto done; }
     if (arity == 2 && (d->b < 0 || d->b >= i)) { rc = -1; goto done; }
+    /* operand kinds: arithmetic and compared terms are numbers, the rest masks */
+    int want_num = is_number_op(d->op) || d->op == VLO_THR_GT || d->op == VLO_THR_LT ||
+                   d->op == VLO_PCT_GT || d->op == VLO_PCT_LT;
+    if (arity >= 1 && is_number_op(nodes[d->a].op) != want_num) { rc = -1; goto done; }
+    if (arity == 2 && is_number_op(nodes[d->b].op) != want_num) { rc = -1; goto done; }
     if (arity >= 1) uses[d->a]++;
     if (arity == 2) uses[d->b]++;
   }
   for (int r = 0; r < n_roots; ++r) {
-    if (roots[r] < 0 || roots[r] >= n_nodes) { rc = -1; goto done; }
+    if (roots[r] < 0 || roots[r] >= n_nodes || is_number_op(nodes[roots[r]].op)) { rc = -1; goto done; }
   }
   for (int i = 0; i < n_nodes; ++i) {
     const vlo_node* d = &nodes[i];
-    uint8_t* o = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
-    if (!o) { rc = -2; goto done; }
-    val[i] = o;
+    size_t bytes = (size_t)(n > 0 ? n : 1) * (is_number_op(d->op) ? sizeof(float) : 1);
+    void* ov = malloc(bytes);
+    if (!ov) { rc = -2; goto done; }
+    val[i] = ov;
+    uint8_t* o = (uint8_t*)ov;
+    float* fo = (float*)ov;
     switch (d->op) {
       case VLO_TRUE: memset(o, 1, (size_t)n); break;
       case VLO_FALSE: memset(o, 0, (size_t)n); break;
@@ -238,9 +293,14 @@ VLO_EXPORT int vlo_eval(const vlo_node* nodes, int n_nodes, const int32_t* roots
       case VLO_THR_LT:
       case VLO_PCT_GT:
       case VLO_PCT_LT: {
-        if (d->image < 0 || d->image >= n_images || d->channel < 0 ||
-            d->channel >= C) { rc = -1; goto done; }
-        const float* ch = images[d->image] + (int64_t)d->channel * n;
+        const float* ch;
+        if (d->a >= 0) {
+          ch = (const float*)val[d->a];
+        } else {
+          if (d->image < 0 || d->image >= n_images || d->channel < 0 ||
+              d->channel >= C) { rc = -1; goto done; }
+          ch = images[d->image] + (int64_t)d->channel * n;
+        }
         float t = d->t;
         if (d->op == VLO_PCT_GT || d->op == VLO_PCT_LT)
           t = vlo_percentile(ch, n, d->q);
@@ -248,23 +308,34 @@ VLO_EXPORT int vlo_eval(const vlo_node* nodes, int n_nodes, const int32_t* roots
         vlo_threshold(ch, n, t, gt, o);
         break;
       }
+      case VLO_VALUE:
+        if (d->image < 0 || d->image >= n_images || d->channel < 0 ||
+            d->channel >= C) { rc = -1; goto done; }
+        memcpy(fo, images[d->image] + (int64_t)d->channel * n, sizeof(float) * (size_t)n);
+        break;
+      case VLO_ADD: case VLO_SUB: case VLO_MUL: case VLO_DIV:
+        vlo_arith(d->op - VLO_ADD, (const float*)val[d->a],
+                  d->b >= 0 ? (const float*)val[d->b] : NULL, d->t, n, fo);
+        break;
       case VLO_MASK:
         if (d->image < 0 || d->image >= n_masks) { rc = -1; goto done; }
         for (int64_t k = 0; k < n; ++k) o[k] = masks[d->image][k] ? 1 : 0;
         break;
-      case VLO_NOT: vlo_not(val[d->a], n, o); break;
-      case VLO_AND: vlo_and(val[d->a], val[d->b], n, o); break;
-      case VLO_NEAR: vlo_near(val[d->a], H, W, conn, o); break;
+      case VLO_NOT: vlo_not((const uint8_t*)val[d->a], n, o); break;
+      case VLO_AND: vlo_and((const uint8_t*)val[d->a], (const uint8_t*)val[d->b], n, o); break;
+      case VLO_NEAR: vlo_near((const uint8_t*)val[d->a], H, W, conn, o); break;
       case VLO_REACH:
-        if (vlo_reach(val[d->a], val[d->b], H, W, conn, o) != 0) { rc = -2; goto done; }
+        if (vlo_reach((const uint8_t*)val[d->a], (const uint8_t*)val[d->b], H, W, conn, o) != 0) {
+          rc = -2;
+          goto done;
+        }
         break;
       default: rc = -1; goto done;
     }
     for (int r = 0; r < n_roots; ++r)
       if (roots[r] == i) memcpy(out_roots[r], o, (size_t)n);
     /* release operands whose last consumer was this node */
-    int arity = (d->op == VLO_NOT || d->op == VLO_NEAR) ? 1
-              : (d->op == VLO_AND || d->op == VLO_REACH) ? 2 : 0;
+    int arity = node_arity(d);
     if (arity >= 1) uses[d->a]--;
     if (arity == 2) uses[d->b]--;
     if (arity >= 1 && uses[d->a] == 0 && val[d->a]) { free(val[d->a]); val[d->a] = NULL; }

@@ -138,14 +138,30 @@ def random_dag(n_nodes: int = 2000, seed: int = 0, max_depth: int = 500,
     return f
 
 
-def sequential_dag(n_nodes: int = 500, seed: int = 0) -> Formula:
+# Operator mixes of the sequential chains: weights of (NOT, NEAR, AND, REACH).
+CHAIN_MIXES = {
+    "mixed": (0.3, 0.3, 0.25, 0.15),
+    # deep N chains: long runs of dilations cut by complements, which stress
+    # the halo of fused groups (a dilation of a complement is an erosion)
+    "near": (0.3, 0.65, 0.05, 0.0),
+    # reachability after reachability: every rho waits for the one before
+    "reach": (0.3, 0.1, 0.2, 0.4),
+}
+
+
+def sequential_dag(n_nodes: int = 500, seed: int = 0, mix: str = "mixed",
+                   taps: int = 0) -> Formula:
     """A sequential formula f(g(...(x))) (Sec. 4.1): every operator takes the
     previous node as its first operand; binary operators take a fresh
-    threshold as the second."""
+    threshold as the second.  `mix` picks the operator weights (CHAIN_MIXES).
+    The root is the last node; with `taps` > 0 every taps-th node is an output
+    too (chains often end in an all-true or all-false mask, the taps show the
+    states on the way)."""
     rng = np.random.default_rng(seed)
+    p = CHAIN_MIXES[mix]
     nodes = [Node("THR_GT", t=f32(rng.random()))]
     while len(nodes) < n_nodes:
-        kind = ("NOT", "NEAR", "AND", "REACH")[rng.choice(4, p=(0.3, 0.3, 0.25, 0.15))]
+        kind = ("NOT", "NEAR", "AND", "REACH")[rng.choice(4, p=p)]
         prev = len(nodes) - 1
         if kind in ("NOT", "NEAR"):
             nodes.append(Node(kind, a=prev))
@@ -153,7 +169,10 @@ def sequential_dag(n_nodes: int = 500, seed: int = 0) -> Formula:
             op = "THR_GT" if rng.random() < 0.5 else "THR_LT"
             nodes.append(Node(op, t=f32(rng.random())))
             nodes.append(Node(kind, a=prev, b=len(nodes) - 1))
-    f = Formula(nodes, [len(nodes) - 1], name=f"seq{n_nodes}_s{seed}")
+    name = f"seq{n_nodes}_s{seed}" if mix == "mixed" else f"seq-{mix}{n_nodes}_s{seed}"
+    roots = list(range(0, len(nodes) - 1, taps)) if taps > 0 else []
+    f = Formula(nodes, roots + [len(nodes) - 1], name=name,
+                meta={"seed": seed, "mix": mix, "taps": taps})
     f.validate()
     return f
 
