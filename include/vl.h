@@ -127,6 +127,19 @@ VL_API vl_status vl_image_create(vl_context* ctx, int32_t h, int32_t w,
                                  int32_t data_on_device, void* stream,
                                  vl_image** out);
 
+/* Pixel formats of number images. */
+typedef enum { VL_PX_F32 = 0, VL_PX_U16 = 1 } vl_pixel_format;
+
+/* The same for 16-bit unsigned pixels (the tool's native precision, Sec.
+ * 3): `data` holds channels*h*w uint16 values, kept as uint16 on the device
+ * (2 bytes per pixel); a pixel is its integer value, which thresholds,
+ * percentiles and number terms read exactly as a float32.  Errors as
+ * vl_image_create. */
+VL_API vl_status vl_image_create_u16(vl_context* ctx, int32_t h, int32_t w,
+                                     int32_t channels, const uint16_t* data,
+                                     int32_t data_on_device, void* stream,
+                                     vl_image** out);
+
 /* A binary image used directly as an atomic proposition (the paper's atoms
  * "correspond to binary images", Sec. 2).  `data` is h*w bytes (nonzero =
  * true), host or device. */
@@ -145,6 +158,9 @@ VL_API vl_status vl_mask_create_packed(vl_context* ctx, int32_t h, int32_t w,
  * images made by vl_mask_create*. */
 VL_API vl_status vl_image_info(const vl_image* img, int32_t* h, int32_t* w,
                                int32_t* channels, int32_t* is_mask);
+
+/* Pixel format (vl_pixel_format) of a number image; VL_ERR_ARG for masks. */
+VL_API vl_status vl_image_format(const vl_image* img, int32_t* format);
 
 /* ---------------------------------------------------------------- formulas */
 
@@ -165,12 +181,31 @@ typedef enum {
   VL_OP_PCT_GT = 4, VL_OP_PCT_LT = 5, VL_OP_MASK = 6, VL_OP_NOT = 7,
   VL_OP_AND = 8, VL_OP_NEAR = 9, VL_OP_REACH = 10, VL_OP_OR = 11,
   VL_OP_INTERIOR = 12, VL_OP_SURROUNDED = 13, VL_OP_GROW = 14,
-  VL_OP_TOUCH = 15
+  VL_OP_TOUCH = 15,
+  /* number terms (the tool's basic arithmetic, Sec. 3) */
+  VL_OP_VALUE = 16, VL_OP_ADD = 17, VL_OP_SUB = 18, VL_OP_MUL = 19,
+  VL_OP_DIV = 20
 } vl_op;
+
+/* Number terms.  Besides masks, a formula may compute number images pixel by
+ * pixel and compare them:
+ *   VALUE             = channel `channel` of image `image`, as numbers (a
+ *                       uint16 pixel is its integer value);
+ *   ADD/SUB/MUL/DIV   = a (+ - * /) b for two number terms a, b, or
+ *                       a (op) t for the float32 constant t when b = -1;
+ * each an IEEE-754 binary32 operation rounded to nearest even, once per
+ * node (never fused with another node's operation).  A THR_* or PCT_* node
+ * with a >= 0 compares the number term a (instead of image / channel): NaN
+ * satisfies no threshold and sorts after +infinity in a percentile.  Number
+ * terms are operands of arithmetic and comparisons only; connectives and
+ * roots take masks (VL_ERR_FORMULA otherwise).  A plan evaluates all the
+ * number terms its comparisons need in one pass over the pixels (at most
+ * 16 live values and 1024 operations per formula, else VL_ERR_FORMULA). */
 
 /* One node (32 bytes).  Operands a, b index earlier nodes of the same array
  * (a, b < own index; -1 when unused).  For REACH, a = phi1 (the target) and
- * b = phi2 (the intermediate pixels). */
+ * b = phi2 (the intermediate pixels).  Thresholds and percentiles use a only
+ * to compare a number term; arithmetic uses b = -1 for a constant t. */
 typedef struct {
   int32_t op;
   int32_t a;
@@ -201,7 +236,8 @@ VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes,
  * its instructions on every tile; kinds 2-5 are the four passes of a batch
  * of component selects (tile labelling, border merge, flag propagation,
  * final select); kind 0 computes percentiles; kind 6 computes rank codes
- * (below).  Steps are listed in an order that respects their dependencies
+ * (below); kind 7 evaluates number terms (vl_formula_arith).  Steps are
+ * listed in an order that respects their dependencies
  * (vl_formula_step_deps).  Instruction opcodes: 1 threshold, 2 load slot, 3 not, 4 and,
  * 5 or, 6 N, 7 constant, 8 store slot, 9 and-not, 10 threshold by rank
  * code.  Slots: [0, n_inter) intermediates, then one per distinct root,
@@ -262,6 +298,22 @@ typedef struct {
 VL_API vl_status vl_formula_rank_tables(const vl_formula* f, vl_plan_rank* tables,
                                         float* values);
 
+/* Number terms of a plan: one straight-line program run on every pixel
+ * (step kind 7, first in the plan).  Opcodes: 0 load channel `channel` of
+ * image `image` into register dst; 1-4 dst = a (+ - * /) b, b = 255 for
+ * the constant c; 5 store register a into number image `image` (counted
+ * from the first one).  Number images follow the formula's own images in
+ * a job's image list: thresholds, percentiles and rank tables of a plan
+ * name them with index *first_number_image + k.  Any pointer may be NULL;
+ * insns receives *n_insns entries. */
+typedef struct {
+  uint8_t op, dst, a, b;
+  int16_t image, channel;
+  float c;
+} vl_plan_arith;
+VL_API vl_status vl_formula_arith(const vl_formula* f, vl_plan_arith* insns, int32_t* n_insns,
+                                  int32_t* n_number_images, int32_t* first_number_image);
+
 /* Counts of a compiled formula (any pointer may be NULL):
  *   n_primitive -- primitive nodes (threshold, not, and, N, rho, constants,
  *                  masks) after derived-operator expansion and sharing,
@@ -289,7 +341,7 @@ typedef struct {
   int64_t mask_writes;      /* masks written to global memory per evaluation */
   int64_t mask_reads;       /* masks read back from global memory per evaluation */
   int32_t max_halo;         /* largest halo of a fused group */
-  int32_t reserved;
+  int32_t n_number_images;  /* number images the arithmetic step writes */
 } vl_formula_stats;
 
 VL_API vl_status vl_formula_stats_get(const vl_formula* f, vl_formula_stats* st);

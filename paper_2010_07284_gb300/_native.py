@@ -20,7 +20,9 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_FORMULA", 3: "ERR_SHAPE", 4: "ERR
 
 OPCODES = {"TRUE": 0, "FALSE": 1, "THR_GT": 2, "THR_LT": 3, "PCT_GT": 4, "PCT_LT": 5,
            "MASK": 6, "NOT": 7, "AND": 8, "NEAR": 9, "REACH": 10, "OR": 11,
-           "INTERIOR": 12, "SURROUNDED": 13, "GROW": 14, "TOUCH": 15}
+           "INTERIOR": 12, "SURROUNDED": 13, "GROW": 14, "TOUCH": 15,
+           "VALUE": 16, "ADD": 17, "SUB": 18, "MUL": 19, "DIV": 20}
+PX_F32, PX_U16 = 0, 1
 
 EXEC_FUSED, EXEC_PLAIN = 0, 1
 
@@ -49,7 +51,7 @@ class VlFormulaStats(C.Structure):
                 ("n_roots", C.c_int32), ("n_images", C.c_int32), ("n_steps", C.c_int32),
                 ("n_groups", C.c_int32), ("n_selects", C.c_int32),
                 ("n_channels_read", C.c_int32), ("mask_writes", C.c_int64),
-                ("mask_reads", C.c_int64), ("max_halo", C.c_int32), ("reserved", C.c_int32)]
+                ("mask_reads", C.c_int64), ("max_halo", C.c_int32), ("n_number_images", C.c_int32)]
 
 
 class VlPlanSizes(C.Structure):
@@ -88,6 +90,11 @@ class VlPlanRank(C.Structure):
                 ("nbits", C.c_int32), ("value_off", C.c_int32), ("plane0", C.c_int32)]
 
 
+class VlPlanArith(C.Structure):
+    _fields_ = [("op", C.c_uint8), ("dst", C.c_uint8), ("a", C.c_uint8), ("b", C.c_uint8),
+                ("image", C.c_int16), ("channel", C.c_int16), ("c", C.c_float)]
+
+
 class VlServerConfig(C.Structure):
     _fields_ = [("max_inflight_batches", C.c_int32), ("max_batch_jobs", C.c_int32),
                 ("memory_budget", C.c_int64), ("batch_window_us", C.c_int64),
@@ -115,12 +122,16 @@ SIGNATURES = [
     ("vl_last_error", C.c_char_p, [_P]),
     ("vl_free", None, [_P]),
     ("vl_image_create", C.c_int, [_P, _I32, _I32, _I32, _P, _I32, _P, _PP]),
+    ("vl_image_create_u16", C.c_int, [_P, _I32, _I32, _I32, _P, _I32, _P, _PP]),
+    ("vl_image_format", C.c_int, [_P, C.POINTER(_I32)]),
     ("vl_mask_create", C.c_int, [_P, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_mask_create_packed", C.c_int, [_P, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_image_info", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_compile", C.c_int, [_P, C.POINTER(VlNode), _I32, C.POINTER(_I32), _I32, _I32, _PP]),
     ("vl_formula_step_deps", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_rank_tables", C.c_int, [_P, C.POINTER(VlPlanRank), C.POINTER(C.c_float)]),
+    ("vl_formula_arith", C.c_int, [_P, C.POINTER(VlPlanArith), C.POINTER(_I32), C.POINTER(_I32),
+                                   C.POINTER(_I32)]),
     ("vl_formula_info", C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_stats_get", C.c_int, [_P, C.POINTER(VlFormulaStats)]),
     ("vl_formula_plan", C.c_int, [_P, C.POINTER(VlPlanSizes), C.POINTER(VlPlanStep),

@@ -76,22 +76,31 @@ class Context(_Handle):
 
     # ------------------------------------------------------------ images
     def image(self, data, stream=None) -> "Image":
-        """Float image (C, H, W) from a numpy array (host) or a CUDA tensor."""
+        """Number image (C, H, W) from a numpy array (host) or a CUDA tensor:
+        uint16 data stays uint16 on the device, anything else becomes
+        float32."""
         lib = N.load()
         out = C.c_void_p()
         if _is_torch_cuda(data):
-            t = data.contiguous().float()
+            import torch
+            u16 = getattr(torch, "uint16", None)
+            t = data.contiguous()
+            if u16 is None or t.dtype != u16:
+                t = t.float()
             if t.dim() == 2:
                 t = t[None]
             c, h, w = t.shape
-            rc = lib.vl_image_create(self._ptr, h, w, c, t.data_ptr(), 1, _stream_handle(stream), C.byref(out))
+            fn = lib.vl_image_create_u16 if t.dtype != torch.float32 else lib.vl_image_create
+            rc = fn(self._ptr, h, w, c, t.data_ptr(), 1, _stream_handle(stream), C.byref(out))
             keep = t
         else:
-            a = np.ascontiguousarray(data, dtype=np.float32)
+            a = np.asarray(data)
+            a = np.ascontiguousarray(a, dtype=np.uint16 if a.dtype == np.uint16 else np.float32)
             if a.ndim == 2:
                 a = a[None]
             c, h, w = a.shape
-            rc = lib.vl_image_create(self._ptr, h, w, c, a.ctypes.data, 0, _stream_handle(stream), C.byref(out))
+            fn = lib.vl_image_create_u16 if a.dtype == np.uint16 else lib.vl_image_create
+            rc = fn(self._ptr, h, w, c, a.ctypes.data, 0, _stream_handle(stream), C.byref(out))
             keep = a
         self._check(rc)
         return Image(self, out.value, keep)
@@ -241,6 +250,11 @@ class Image(_Handle):
         h, w, c, m = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         N.load().vl_image_info(ptr, C.byref(h), C.byref(w), C.byref(c), C.byref(m))
         self.h, self.w, self.channels, self.is_mask = h.value, w.value, c.value, bool(m.value)
+        self.format = None  # masks
+        if not self.is_mask:
+            f = C.c_int32()
+            N.load().vl_image_format(ptr, C.byref(f))
+            self.format = "u16" if f.value == N.PX_U16 else "f32"
 
     def release_source(self):
         """Drop the reference to the source array once the stream has copied it."""
@@ -287,7 +301,14 @@ class Formula(_Handle):
         doff = (C.c_int32 * (sz.n_steps + 1))()
         deps = (C.c_int32 * max(1, sz.n_deps))()
         self._check(lib.vl_formula_step_deps(self._ptr, doff, deps))
+        na, nn, first = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(lib.vl_formula_arith(self._ptr, None, C.byref(na), C.byref(nn), C.byref(first)))
+        ar = (N.VlPlanArith * max(1, na.value))()
+        self._check(lib.vl_formula_arith(self._ptr, ar, None, None, None))
         return {
+            "arith": [rec(ar[i]) for i in range(na.value)],
+            "n_number_images": nn.value,
+            "first_number_image": first.value,
             "deps": [list(deps[doff[i]:doff[i + 1]]) for i in range(sz.n_steps)],
             "rank_tables": [rec(rt[i]) for i in range(sz.n_rank_tables)],
             "rank_values": np.array(rv[:sz.n_rank_values], dtype=np.float32),
@@ -303,7 +324,7 @@ class Formula(_Handle):
     def info(self) -> dict:
         s = N.VlFormulaStats()
         self._check(N.load().vl_formula_stats_get(self._ptr, C.byref(s)))
-        return {f: getattr(s, f) for f, _ in N.VlFormulaStats._fields_ if f != "reserved"}
+        return {f: getattr(s, f) for f, _ in N.VlFormulaStats._fields_}
 
     @property
     def n_primitive(self) -> int:

@@ -176,7 +176,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     int gty, gtx, cty, ctx_, ctiles;
     std::vector<int> need;
     size_t off_images, off_slotptrs, off_pct, off_slots, off_rz, set_bytes, set_off[5];
-    size_t off_roots, off_status, off_fcount, off_planes;
+    size_t off_roots, off_status, off_fcount, off_planes, off_num;
+    int n_table;  // image table: the formula's images, then its number images
     int step_base, fcount_base;
     int flist_cap;
     int formula_idx;
@@ -204,7 +205,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   const size_t off_jobs = take(sizeof(DevJob) * n_jobs);
   std::vector<size_t> f_steps(formulas.size()), f_insns(formulas.size()), f_rz(formulas.size()),
       f_pct(formulas.size()), f_rtab(formulas.size()), f_rvals(formulas.size()),
-      f_doff(formulas.size()), f_deps(formulas.size());
+      f_doff(formulas.size()), f_deps(formulas.size()), f_arith(formulas.size());
   for (size_t k = 0; k < formulas.size(); ++k) {
     const Plan* P = formulas[k];
     f_steps[k] = take(sizeof(StepDesc) * std::max<size_t>(1, P->steps.size()));
@@ -215,6 +216,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     f_rvals[k] = take(sizeof(float) * std::max<size_t>(1, P->rvals.size()));
     f_doff[k] = take(sizeof(int32_t) * std::max<size_t>(1, P->dep_off.size()));
     f_deps[k] = take(sizeof(int32_t) * std::max<size_t>(1, P->deps.size()));
+    f_arith[k] = take(sizeof(ArithInsn) * std::max<size_t>(1, P->arith.size()));
   }
   const TileShape ts = force ? *force : pick_tile_shape(ctx, jobs, n_jobs);
   if (!tile_shape_fits(ctx, ts)) return set_err(ctx, VL_ERR_ARG, "tile shape does not fit shared memory");
@@ -246,10 +248,13 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
         case SK_RZ_MERGE: n = s.rz_cnt * ccl_merge_chunks(I.H, I.Wp); break;
         case SK_RZ_FLAGS: n = s.rz_cnt * ccl_flag_chunks(I.H, I.Wp); break;
         case SK_RANK: n = (int)P.rtab.size() * ((I.H + RANK_ROWS - 1) / RANK_ROWS); break;
+        case SK_ARITH: n = (I.H + ARITH_ROWS - 1) / ARITH_ROWS; break;
       }
       I.need.push_back(std::max(1, n));
     }
-    I.off_images = take(sizeof(DevImage) * jobs[j].n_images);
+    // the formula's own images, then its number images
+    I.n_table = (int)P.img_kind.size() + P.n_num_images;
+    I.off_images = take(sizeof(DevImage) * std::max(1, I.n_table));
     I.off_slotptrs = take(sizeof(uint32_t*) * std::max(1, P.n_inter_slots + P.n_root_slots + P.n_mask_slots));
   }
   // work items, in list-scheduling order: every (job, step) gets the time
@@ -281,6 +286,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
           case SK_RZ_FLAGS: len = 8.0; break;
           case SK_RZ_FINAL: len = waves * 25.0; break;
           case SK_RANK: len = 20.0 + waves * 5.0; break;
+          case SK_ARITH: len = 10.0 + waves * 2.0 * P.steps[s].insn_cnt; break;
           default: len = 100.0; break;
         }
         fin[s] = t + len;
@@ -319,6 +325,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     const size_t P_px = (size_t)I.H * I.W;
     I.off_pct = take(sizeof(float) * std::max(1, P.n_pct_slots));
     I.off_planes = take(mask_bytes * P.n_planes);
+    I.off_num = take(sizeof(float) * (size_t)I.H * I.pitch * P.n_num_images);
     I.off_slots = take(mask_bytes * P.n_inter_slots);
     const size_t tstate = (size_t)I.ctiles * ccl_tile_cap_host(I.Wp);
     // select scratch sets: G, F, flist, tpar, tflag, each 256-byte aligned
@@ -369,6 +376,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     if (!P->rvals.empty()) std::memcpy(&host[f_rvals[k]], P->rvals.data(), sizeof(float) * P->rvals.size());
     if (!P->dep_off.empty()) std::memcpy(&host[f_doff[k]], P->dep_off.data(), sizeof(int32_t) * P->dep_off.size());
     if (!P->deps.empty()) std::memcpy(&host[f_deps[k]], P->deps.data(), sizeof(int32_t) * P->deps.size());
+    if (!P->arith.empty()) std::memcpy(&host[f_arith[k]], P->arith.data(), sizeof(ArithInsn) * P->arith.size());
   }
   DevJob* hj = reinterpret_cast<DevJob*>(&host[off_jobs]);
   int32_t* hneed = reinterpret_cast<int32_t*>(&host[off_need]);
@@ -385,13 +393,20 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     d.g_tiles_y = I.gty; d.g_tiles_x = I.gtx;
     d.c_tiles_y = I.cty; d.c_tiles_x = I.ctx_;
     d.conn = P.conn;
-    d.n_images = jobs[j].n_images;
+    d.n_images = I.n_table;
     DevImage* him = reinterpret_cast<DevImage*>(&host[I.off_images]);
-    for (int i = 0; i < jobs[j].n_images; ++i) {
+    const int n_own = (int)P.img_kind.size();
+    for (int i = 0; i < n_own; ++i) {
       const vl_image* im = jobs[j].images[i];
-      him[i] = DevImage{im->data, im->mask, im->C, im->is_mask};
+      him[i] = DevImage{im->data, im->mask, im->C, im->is_mask, im->format, 0};
     }
+    for (int k = 0; k < P.n_num_images; ++k)
+      him[n_own + k] = DevImage{tb + I.off_num + sizeof(float) * (size_t)I.H * I.pitch * k, nullptr,
+                                1, 0, PX_F32, 1};
     d.images = reinterpret_cast<const DevImage*>(tb + I.off_images);
+    d.arith = reinterpret_cast<const ArithInsn*>(tb + f_arith[I.formula_idx]);
+    d.n_arith = (int32_t)P.arith.size();
+    d.first_num_image = n_own;
     uint32_t** hs = reinterpret_cast<uint32_t**>(&host[I.off_slotptrs]);
     const size_t mask_bytes = (size_t)I.H * I.Wp * 4;
     for (int s = 0; s < P.n_inter_slots; ++s)
@@ -590,6 +605,48 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
     return reinterpret_cast<uint32_t*>(pb + 256 + mask_bytes * (slot - P.n_inter_slots));
   };
   if ((e = cudaMemsetAsync(status, 0, sizeof(int32_t), st))) return cuda_err(ctx, e, "zeroing status");
+  // number terms: one launch per operation into register planes; the
+  // compared terms are copied into number images, which follow the
+  // formula's own images
+  struct Chan { const void* p; int format; };
+  const size_t plane_elems = (size_t)H * pitch;
+  const int n_own = (int)P.img_kind.size();
+  DevBlockPtr numbuf;
+  std::vector<Chan> reg_view(kArithMaxRegs, Chan{nullptr, PX_F32});
+  if (!P.arith.empty()) {
+    const size_t plane_bytes = plane_elems * sizeof(float);
+    if ((e = dev_alloc(ctx, plane_bytes * (size_t)(P.arith_regs + P.n_num_images), st, &numbuf)))
+      return cuda_err(ctx, e, "allocating number images");
+    char* nb = static_cast<char*>(numbuf->ptr);
+    for (const ArithInsn& A : P.arith) {
+      if (A.op == A_VALUE) {
+        const vl_image* im = imgs[A.img];
+        reg_view[A.dst] = Chan{static_cast<const char*>(im->data) +
+                                   (size_t)A.ch * plane_elems * (im->format == PX_U16 ? 2 : 4),
+                               im->format};
+      } else if (A.op == A_STORE) {
+        e = cudaMemcpyAsync(nb + plane_bytes * (P.arith_regs + A.img), reg_view[A.a].p, plane_bytes,
+                            cudaMemcpyDeviceToDevice, st);
+      } else {
+        float* out = reinterpret_cast<float*>(nb + plane_bytes * A.dst);
+        const Chan a = reg_view[A.a];
+        const Chan b = A.b == kArithConst ? Chan{nullptr, PX_F32} : reg_view[A.b];
+        e = launch_arith(A.op, a.p, a.format, b.p, b.format, A.c, out, H, W, pitch, st);
+        reg_view[A.dst] = Chan{out, PX_F32};
+      }
+      if (e) return cuda_err(ctx, e, "launching a number-term operation");
+    }
+  }
+  auto chan = [&](int img, int ch) -> Chan {
+    if (img >= n_own)
+      return Chan{static_cast<const char*>(numbuf->ptr) +
+                      sizeof(float) * plane_elems * (size_t)(P.arith_regs + img - n_own),
+                  PX_F32};
+    const vl_image* im = imgs[img];
+    return Chan{static_cast<const char*>(im->data) +
+                    (size_t)ch * plane_elems * (im->format == PX_U16 ? 2 : 4),
+                im->format};
+  };
   // percentiles
   DevBlockPtr pct;
   if (P.n_pct_slots) {
@@ -597,8 +654,8 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
     for (const PctDesc& d : P.pct) {
       const long long n = (long long)H * W;
       const long long rank = (long long)(d.q * (double)(n - 1));
-      const float* plane = imgs[d.img]->data + (size_t)d.ch * H * pitch;
-      if ((e = launch_select(plane, pitch, H, W, rank, static_cast<float*>(pct->ptr) + d.slot, st)))
+      const Chan c = chan(d.img, d.ch);
+      if ((e = launch_select(c.p, c.format, pitch, H, W, rank, static_cast<float*>(pct->ptr) + d.slot, st)))
         return cuda_err(ctx, e, "launching a percentile select");
     }
   }
@@ -650,10 +707,17 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
     switch (x.op) {
       case E_TRUE: e = launch_const(g, true, o, st); break;
       case E_FALSE: e = launch_const(g, false, o, st); break;
-      case E_THR: e = launch_threshold(imgs[x.img]->data + (size_t)x.ch * H * pitch, pitch, g, x.t,
-                                       nullptr, x.lt, o, st); break;
-      case E_PCT: e = launch_threshold(imgs[x.img]->data + (size_t)x.ch * H * pitch, pitch, g, 0.f,
-                                       static_cast<float*>(pct->ptr) + x.pct_slot, x.lt, o, st); break;
+      case E_THR: {
+        const Chan c = chan(x.img, x.ch);
+        e = launch_threshold(c.p, c.format, pitch, g, x.t, nullptr, x.lt, o, st);
+        break;
+      }
+      case E_PCT: {
+        const Chan c = chan(x.img, x.ch);
+        e = launch_threshold(c.p, c.format, pitch, g, 0.f, static_cast<float*>(pct->ptr) + x.pct_slot,
+                             x.lt, o, st);
+        break;
+      }
       case E_NOT: e = launch_not(val[x.a], g, o, st); break;
       case E_AND: e = launch_and(val[x.a], val[x.b], g, o, st); break;
       case E_OR: e = launch_or(val[x.a], val[x.b], g, o, st); break;
@@ -829,9 +893,9 @@ static vl_status image_common(vl_context* ctx, int32_t h, int32_t w, int32_t c) 
   return VL_OK;
 }
 
-VL_API vl_status vl_image_create(vl_context* ctx, int32_t h, int32_t w, int32_t channels,
-                                 const float* data, int32_t data_on_device, void* stream,
-                                 vl_image** out) {
+static vl_status image_create(vl_context* ctx, int32_t h, int32_t w, int32_t channels,
+                              const void* data, int format, int32_t data_on_device, void* stream,
+                              vl_image** out) {
   vl_status s = image_common(ctx, h, w, channels);
   if (s != VL_OK) return s;
   if (!data || !out) return set_err(ctx, VL_ERR_ARG, "null data or output");
@@ -839,15 +903,17 @@ VL_API vl_status vl_image_create(vl_context* ctx, int32_t h, int32_t w, int32_t 
   auto im = std::make_unique<vl_image>();
   im->ctx = ctx;
   im->H = h; im->W = w; im->C = channels;
+  im->format = format;
   im->Wp = words_per_row(w);
   im->pitch = 32 * im->Wp;
-  const size_t bytes = (size_t)channels * h * im->pitch * sizeof(float);
+  const size_t esz = format == PX_U16 ? 2 : 4;
+  const size_t bytes = (size_t)channels * h * im->pitch * esz;
   cudaError_t e = dev_alloc(ctx, bytes, S(stream), &im->block);
   if (e) return cuda_err(ctx, e, "allocating an image");
-  im->data = static_cast<float*>(im->block->ptr);
+  im->data = im->block->ptr;
   if (im->pitch != w && (e = cudaMemsetAsync(im->data, 0, bytes, S(stream))))
     return cuda_err(ctx, e, "clearing image padding");
-  e = cudaMemcpy2DAsync(im->data, (size_t)im->pitch * 4, data, (size_t)w * 4, (size_t)w * 4,
+  e = cudaMemcpy2DAsync(im->data, (size_t)im->pitch * esz, data, (size_t)w * esz, (size_t)w * esz,
                         (size_t)channels * h,
                         data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         S(stream));
@@ -855,6 +921,18 @@ VL_API vl_status vl_image_create(vl_context* ctx, int32_t h, int32_t w, int32_t 
   if ((e = record_ready(im.get(), S(stream)))) return cuda_err(ctx, e, "recording an event");
   *out = im.release();
   return VL_OK;
+}
+
+VL_API vl_status vl_image_create(vl_context* ctx, int32_t h, int32_t w, int32_t channels,
+                                 const float* data, int32_t data_on_device, void* stream,
+                                 vl_image** out) {
+  return image_create(ctx, h, w, channels, data, PX_F32, data_on_device, stream, out);
+}
+
+VL_API vl_status vl_image_create_u16(vl_context* ctx, int32_t h, int32_t w, int32_t channels,
+                                     const uint16_t* data, int32_t data_on_device, void* stream,
+                                     vl_image** out) {
+  return image_create(ctx, h, w, channels, data, PX_U16, data_on_device, stream, out);
 }
 
 VL_API vl_status vl_mask_create(vl_context* ctx, int32_t h, int32_t w, const uint8_t* data,
@@ -919,6 +997,12 @@ VL_API vl_status vl_image_info(const vl_image* img, int32_t* h, int32_t* w, int3
   if (w) *w = img->W;
   if (channels) *channels = img->C;
   if (is_mask) *is_mask = img->is_mask;
+  return VL_OK;
+}
+
+VL_API vl_status vl_image_format(const vl_image* img, int32_t* format) {
+  if (!valid(img, TAG_IMG) || img->is_mask) return VL_ERR_ARG;
+  if (format) *format = img->format;
   return VL_OK;
 }
 
@@ -1002,6 +1086,18 @@ VL_API vl_status vl_formula_rank_tables(const vl_formula* f, vl_plan_rank* table
   return VL_OK;
 }
 
+VL_API vl_status vl_formula_arith(const vl_formula* f, vl_plan_arith* insns, int32_t* n_insns,
+                                  int32_t* n_number_images, int32_t* first_number_image) {
+  if (!valid(f, TAG_FML)) return VL_ERR_ARG;
+  static_assert(sizeof(vl_plan_arith) == sizeof(ArithInsn), "arithmetic program layout");
+  const Plan& P = f->plan;
+  if (insns && !P.arith.empty()) std::memcpy(insns, P.arith.data(), sizeof(ArithInsn) * P.arith.size());
+  if (n_insns) *n_insns = (int32_t)P.arith.size();
+  if (n_number_images) *n_number_images = P.n_num_images;
+  if (first_number_image) *first_number_image = (int32_t)P.img_kind.size();
+  return VL_OK;
+}
+
 VL_API vl_status vl_formula_info(const vl_formula* f, int64_t* n_primitive, int64_t* n_reach,
                                  int32_t* n_roots, int32_t* n_images) {
   if (!valid(f, TAG_FML)) return VL_ERR_ARG;
@@ -1037,6 +1133,7 @@ VL_API vl_status vl_formula_stats_get(const vl_formula* f, vl_formula_stats* st)
   }
   st->mask_writes += (int64_t)P.rz.size();  // each select writes Z
   st->max_halo = P.max_group_halo;
+  st->n_number_images = P.n_num_images;
   return VL_OK;
 }
 

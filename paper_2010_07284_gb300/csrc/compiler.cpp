@@ -45,17 +45,39 @@ struct PrimBuilder {
 
   int add(const vl_node& n) {
     Key k{n.op, -1, -1, 0, 0, 0, 0, 0};
+    vl_node c = n;
     switch (n.op) {
       case VL_OP_TRUE: case VL_OP_FALSE: break;
       case VL_OP_MASK: k.img = n.image; break;
-      case VL_OP_THR_GT: case VL_OP_THR_LT: k.img = n.image; k.ch = n.channel; k.tb = fbits(n.t); break;
-      case VL_OP_PCT_GT: case VL_OP_PCT_LT: k.img = n.image; k.ch = n.channel; k.qb = dbits(n.q); break;
-      default: k.a = n.a; k.b = n.b; break;
+      case VL_OP_THR_GT: case VL_OP_THR_LT: case VL_OP_PCT_GT: case VL_OP_PCT_LT:
+        if (n.a >= 0) {  // compares a number term
+          k.a = n.a; k.img = -1;
+          c.image = c.channel = 0;
+        } else {
+          k.img = n.image; k.ch = n.channel;
+          c.a = -1;
+        }
+        c.b = -1;
+        if (n.op == VL_OP_THR_GT || n.op == VL_OP_THR_LT) { k.tb = fbits(n.t); c.q = 0; }
+        else { k.qb = dbits(n.q); c.t = 0; }
+        break;
+      case VL_OP_VALUE:
+        k.img = n.image; k.ch = n.channel;
+        c.a = c.b = -1; c.t = 0; c.q = 0;
+        break;
+      case VL_OP_ADD: case VL_OP_SUB: case VL_OP_MUL: case VL_OP_DIV:
+        k.a = n.a; k.b = n.b;
+        if (n.b < 0) k.tb = fbits(n.t);
+        else c.t = 0;
+        c.image = c.channel = 0; c.q = 0;
+        break;
+      default:
+        k.a = n.a; k.b = n.b;
+        c.image = 0; c.channel = 0; c.t = 0; c.q = 0;
+        break;
     }
     auto it = index.find(k);
     if (it != index.end()) return it->second;
-    vl_node c = n;
-    if (n.op >= VL_OP_NOT) { c.image = 0; c.channel = 0; c.t = 0; c.q = 0; }
     nodes.push_back(c);
     index.emplace(k, (int)nodes.size() - 1);
     return (int)nodes.size() - 1;
@@ -145,6 +167,12 @@ struct ExecBuilder {
 };
 
 bool is_atom(int op) { return op == E_TRUE || op == E_FALSE || op == E_THR || op == E_PCT || op == E_MASK; }
+bool is_number_op(int op) {
+  return op == VL_OP_VALUE || op == VL_OP_ADD || op == VL_OP_SUB || op == VL_OP_MUL || op == VL_OP_DIV;
+}
+// Provisional image index of the k-th number image (renumbered to follow the
+// formula's own images once the live nodes are known).
+constexpr int kNumImageBase = 16384;
 int arity(int op) {
   switch (op) {
     case E_NOT: case E_NEAR: case E_COPY: return 1;
@@ -167,10 +195,53 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
   // ---- 1. expansion with sharing
   PrimBuilder pb;
   std::vector<int> prim_of(n_nodes);
+  std::vector<char> num(n_nodes, 0);  // node i is a number term
   for (int i = 0; i < n_nodes; ++i) {
     const vl_node& n = in[i];
     auto bad_operand = [&](int x) { return x < 0 || x >= i; };
     const char* why = nullptr;
+    const bool thr = n.op == VL_OP_THR_GT || n.op == VL_OP_THR_LT || n.op == VL_OP_PCT_GT ||
+                     n.op == VL_OP_PCT_LT;
+    if (thr && n.a >= 0) {  // comparison of a number term
+      if (n.a >= i || !num[n.a]) why = "a compared operand must be an earlier number term";
+      else if ((n.op == VL_OP_PCT_GT || n.op == VL_OP_PCT_LT) && !(n.q >= 0.0 && n.q <= 1.0))
+        why = "percentile level outside [0, 1]";
+      else if ((n.op == VL_OP_THR_GT || n.op == VL_OP_THR_LT) && std::isnan(n.t))
+        why = "threshold is NaN";
+      if (!why) {
+        vl_node c = n;
+        c.a = prim_of[n.a];
+        prim_of[i] = pb.add(c);
+      }
+      if (why) { *err = "node " + std::to_string(i) + ": " + why; return VL_ERR_FORMULA; }
+      continue;
+    }
+    if (is_number_op(n.op)) {
+      num[i] = 1;
+      if (n.op == VL_OP_VALUE) {
+        if (n.image < 0 || n.image > 4095) why = "image index out of range";
+        else if (n.channel < 0 || n.channel > 4095) why = "channel out of range";
+        if (!why) prim_of[i] = pb.add(n);
+      } else if (bad_operand(n.a) || !num[n.a] || (n.b >= 0 && (n.b >= i || !num[n.b]))) {
+        why = "arithmetic operands must be earlier number terms";
+      } else if (n.b < 0 && std::isnan(n.t)) {
+        why = "arithmetic constant is NaN";
+      } else {
+        vl_node c = n;
+        c.a = prim_of[n.a];
+        c.b = n.b >= 0 ? prim_of[n.b] : -1;
+        prim_of[i] = pb.add(c);
+      }
+      if (why) { *err = "node " + std::to_string(i) + ": " + why; return VL_ERR_FORMULA; }
+      continue;
+    }
+    if (n.op >= VL_OP_NOT && n.op <= VL_OP_TOUCH) {
+      const bool unary = n.op == VL_OP_NOT || n.op == VL_OP_NEAR || n.op == VL_OP_INTERIOR;
+      if ((n.a >= 0 && n.a < i && num[n.a]) || (!unary && n.b >= 0 && n.b < i && num[n.b])) {
+        *err = "node " + std::to_string(i) + ": connectives take masks, not number terms";
+        return VL_ERR_FORMULA;
+      }
+    }
     switch (n.op) {
       case VL_OP_TRUE: case VL_OP_FALSE: prim_of[i] = pb.add(n); break;
       case VL_OP_THR_GT: case VL_OP_THR_LT: case VL_OP_PCT_GT: case VL_OP_PCT_LT:
@@ -206,10 +277,13 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
     }
     if (why) { *err = "node " + std::to_string(i) + ": " + why; return VL_ERR_FORMULA; }
   }
-  for (int r = 0; r < n_roots; ++r)
+  for (int r = 0; r < n_roots; ++r) {
     if (roots[r] < 0 || roots[r] >= n_nodes) { *err = "root index out of range"; return VL_ERR_FORMULA; }
+    if (num[roots[r]]) { *err = "root " + std::to_string(r) + " is a number term, not a mask"; return VL_ERR_FORMULA; }
+  }
   P.n_primitive = (int64_t)pb.nodes.size();
   for (const vl_node& n : pb.nodes) {
+    if (is_number_op(n.op)) { P.n_num++; continue; }
     switch (n.op) {
       case VL_OP_REACH: P.n_reach++; break;
       case VL_OP_THR_GT: case VL_OP_THR_LT: case VL_OP_PCT_GT: case VL_OP_PCT_LT: P.n_thr++; break;
@@ -221,18 +295,34 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
   }
   // ---- 2. lowering + simplification
   ExecBuilder eb;
-  std::vector<int> e_of(pb.nodes.size());
+  std::vector<int> e_of(pb.nodes.size(), -1);
+  // a compared number term reads a number image: VALUE terms are the image
+  // channel itself; every other term gets a number image of its own
+  std::vector<int> num_image(pb.nodes.size(), -1);
+  std::vector<int> num_root_prim;  // prim node of each provisional number image
+  auto compared = [&](const vl_node& n, int* img, int* ch) {
+    if (n.a < 0) { *img = n.image; *ch = n.channel; return; }
+    const vl_node& v = pb.nodes[n.a];
+    if (v.op == VL_OP_VALUE) { *img = v.image; *ch = v.channel; return; }
+    if (num_image[n.a] < 0) {
+      num_image[n.a] = kNumImageBase + (int)num_root_prim.size();
+      num_root_prim.push_back(n.a);
+    }
+    *img = num_image[n.a];
+    *ch = 0;
+  };
   for (size_t i = 0; i < pb.nodes.size(); ++i) {
     const vl_node& n = pb.nodes[i];
+    if (is_number_op(n.op)) continue;  // programs are built below
     switch (n.op) {
       case VL_OP_TRUE: e_of[i] = eb.TRUE_(); break;
       case VL_OP_FALSE: e_of[i] = eb.FALSE_(); break;
       case VL_OP_THR_GT: case VL_OP_THR_LT: {
-        ENode e = eb.blank(E_THR); e.img = n.image; e.ch = n.channel; e.t = n.t;
+        ENode e = eb.blank(E_THR); compared(n, &e.img, &e.ch); e.t = n.t;
         e.lt = n.op == VL_OP_THR_LT; e_of[i] = eb.add(e); break;
       }
       case VL_OP_PCT_GT: case VL_OP_PCT_LT: {
-        ENode e = eb.blank(E_PCT); e.img = n.image; e.ch = n.channel; e.q = n.q;
+        ENode e = eb.blank(E_PCT); compared(n, &e.img, &e.ch); e.q = n.q;
         e.lt = n.op == VL_OP_PCT_LT; e_of[i] = eb.add(e); break;
       }
       case VL_OP_MASK: { ENode e = eb.blank(E_MASK); e.img = n.image; e_of[i] = eb.add(e); break; }
@@ -281,19 +371,108 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
   if (N > 32000) { *err = "formula too large after expansion (> 32000 nodes)"; return VL_ERR_FORMULA; }
   std::vector<ENode>& X = P.exec;
 
-  // image requirements and percentile slots
-  std::map<std::tuple<int, int, uint64_t>, int> pct_slot;
-  for (ENode& e : X) {
-    if (e.op == E_THR || e.op == E_PCT || e.op == E_MASK) {
-      if ((int)P.img_kind.size() <= e.img) { P.img_kind.resize(e.img + 1, 0); P.img_channels.resize(e.img + 1, 0); }
-      int kind = e.op == E_MASK ? 2 : 1;
-      if (P.img_kind[e.img] != 0 && P.img_kind[e.img] != kind) {
-        *err = "image " + std::to_string(e.img) + " used both as a mask and as a float image";
+  // image requirements
+  auto need_image = [&](int img, int kind, int ch) -> bool {
+    if ((int)P.img_kind.size() <= img) { P.img_kind.resize(img + 1, 0); P.img_channels.resize(img + 1, 0); }
+    if (P.img_kind[img] != 0 && P.img_kind[img] != kind) {
+      *err = "image " + std::to_string(img) + " used both as a mask and as a number image";
+      return false;
+    }
+    P.img_kind[img] = kind;
+    if (kind == 1) P.img_channels[img] = std::max(P.img_channels[img], ch + 1);
+    return true;
+  };
+  for (const ENode& e : X)
+    if ((e.op == E_THR || e.op == E_PCT || e.op == E_MASK) && e.img < kNumImageBase)
+      if (!need_image(e.img, e.op == E_MASK ? 2 : 1, e.ch)) return VL_ERR_FORMULA;
+  // ---- number terms: the live compared terms, numbered after the
+  // formula's images; the terms they need, in order, as one program with
+  // registers reused after their last read
+  {
+    std::vector<int> live_num;  // provisional index -> final (or -1)
+    live_num.assign(num_root_prim.size(), -1);
+    std::vector<int> roots_in_order;
+    for (const ENode& e : X)
+      if ((e.op == E_THR || e.op == E_PCT) && e.img >= kNumImageBase && live_num[e.img - kNumImageBase] < 0) {
+        live_num[e.img - kNumImageBase] = (int)roots_in_order.size();
+        roots_in_order.push_back(num_root_prim[e.img - kNumImageBase]);
+      }
+    const int NP = (int)pb.nodes.size();
+    std::vector<char> need(NP, 0);
+    for (int r : roots_in_order) need[r] = 1;
+    for (int i = NP - 1; i >= 0; --i)
+      if (need[i] && pb.nodes[i].op != VL_OP_VALUE) {
+        need[pb.nodes[i].a] = 1;
+        if (pb.nodes[i].b >= 0) need[pb.nodes[i].b] = 1;
+      }
+    std::vector<int> uses(NP, 0), store_k(NP, -1);
+    for (size_t k = 0; k < roots_in_order.size(); ++k) {
+      store_k[roots_in_order[k]] = (int)k;
+      uses[roots_in_order[k]]++;
+    }
+    for (int i = 0; i < NP; ++i)
+      if (need[i] && pb.nodes[i].op != VL_OP_VALUE) {
+        uses[pb.nodes[i].a]++;
+        if (pb.nodes[i].b >= 0) uses[pb.nodes[i].b]++;
+      }
+    std::vector<int> reg(NP, -1);
+    std::vector<char> busy(kArithMaxRegs, 0);
+    auto release = [&](int v) {
+      if (--uses[v] == 0) busy[reg[v]] = 0;
+    };
+    for (int i = 0; i < NP; ++i) {
+      if (!need[i]) continue;
+      const vl_node& n = pb.nodes[i];
+      ArithInsn A{};
+      A.b = kArithConst;
+      if (n.op == VL_OP_VALUE) {
+        A.op = A_VALUE;
+        A.img = (int16_t)n.image;
+        A.ch = (int16_t)n.channel;
+        if (!need_image(n.image, 1, n.channel)) return VL_ERR_FORMULA;
+      } else {
+        A.op = n.op == VL_OP_ADD ? A_ADD : n.op == VL_OP_SUB ? A_SUB : n.op == VL_OP_MUL ? A_MUL : A_DIV;
+        A.a = (uint8_t)reg[n.a];
+        if (n.b >= 0) A.b = (uint8_t)reg[n.b];
+        else A.c = n.t;
+        release(n.a);  // operands are read before the result is written
+        if (n.b >= 0) release(n.b);
+      }
+      int r = 0;
+      while (r < kArithMaxRegs && busy[r]) ++r;
+      if (r == kArithMaxRegs) {
+        *err = "number terms need more than " + std::to_string(kArithMaxRegs) + " live values";
         return VL_ERR_FORMULA;
       }
-      P.img_kind[e.img] = kind;
-      if (kind == 1) P.img_channels[e.img] = std::max(P.img_channels[e.img], e.ch + 1);
+      busy[r] = 1;
+      reg[i] = r;
+      A.dst = (uint8_t)r;
+      P.arith_regs = std::max(P.arith_regs, r + 1);
+      P.arith.push_back(A);
+      if (store_k[i] >= 0) {
+        ArithInsn S{};
+        S.op = A_STORE;
+        S.a = (uint8_t)r;
+        S.b = kArithConst;
+        S.img = (int16_t)store_k[i];
+        P.arith.push_back(S);
+        release(i);
+      }
     }
+    if ((int)P.arith.size() > kArithMaxInsns) {
+      *err = "number terms need more than " + std::to_string(kArithMaxInsns) + " operations";
+      return VL_ERR_FORMULA;
+    }
+    P.n_num_images = (int)roots_in_order.size();
+    const int first = (int)P.img_kind.size();
+    if (first + P.n_num_images > 32000) { *err = "too many images"; return VL_ERR_FORMULA; }
+    for (ENode& e : X)
+      if ((e.op == E_THR || e.op == E_PCT) && e.img >= kNumImageBase)
+        e.img = first + live_num[e.img - kNumImageBase];
+  }
+  // percentile slots
+  std::map<std::tuple<int, int, uint64_t>, int> pct_slot;
+  for (ENode& e : X) {
     if (e.op == E_PCT) {
       auto key = std::make_tuple(e.img, e.ch, dbits(e.q));
       auto it = pct_slot.find(key);
@@ -634,6 +813,13 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
       P.steps.insert(P.steps.begin(), r);
     }
   }
+  // ---- 6. number terms run first: everything that compares them waits
+  if (!P.arith.empty()) {
+    StepDesc a{};
+    a.kind = SK_ARITH;
+    a.insn_cnt = (int)P.arith.size();
+    P.steps.insert(P.steps.begin(), a);
+  }
   for (RzDesc& r : P.rz) {
     r.phi1_slot = (int16_t)slot_of[r.phi1_slot];
     r.phi2_slot = (int16_t)slot_of[r.phi2_slot];
@@ -646,7 +832,8 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
   {
     const int n = (int)P.steps.size();
     const int n_real = P.n_inter_slots + P.n_root_slots + P.n_mask_slots;
-    const int ps_rank = n_real, ps_pct = n_real + 1, ps_scr = n_real + 2;
+    const int ps_rank = n_real, ps_pct = n_real + 1, ps_num = n_real + 2, ps_scr = n_real + 3;
+    const int first_num = (int)P.img_kind.size();
     std::vector<std::vector<int>> R(n), Wr(n);
     for (int i = 0; i < n; ++i) {
       const StepDesc& s = P.steps[i];
@@ -658,10 +845,20 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
             if (in.op == I_STORE) Wr[i].push_back(in.slot);
             if (in.op == I_RTHR) R[i].push_back(ps_rank);
             if (in.op == I_THR && in.slot >= 0) R[i].push_back(ps_pct);
+            if (in.op == I_THR && in.img >= first_num) R[i].push_back(ps_num);
           }
           break;
-        case SK_PCT: Wr[i].push_back(ps_pct); break;
-        case SK_RANK: Wr[i].push_back(ps_rank); break;
+        case SK_PCT:
+          Wr[i].push_back(ps_pct);
+          for (const PctDesc& d : P.pct)
+            if (d.img >= first_num) R[i].push_back(ps_num);
+          break;
+        case SK_RANK:
+          Wr[i].push_back(ps_rank);
+          for (const RankTab& t : P.rtab)
+            if (t.img >= first_num) R[i].push_back(ps_num);
+          break;
+        case SK_ARITH: Wr[i].push_back(ps_num); break;
         default:
           for (int j = 0; j < s.rz_cnt; ++j) {
             const RzDesc& r = P.rz[s.rz_off + j];

@@ -70,8 +70,15 @@ struct Plan {
   // writes after reads and writes of the same slot, the phases of a select
   // batch, rank codes and percentiles before their readers)
   std::vector<int32_t> dep_off, deps;
-  // accounting: primitive op counts by kind (threshold, not, and, N, rho, other)
-  int64_t n_thr = 0, n_not = 0, n_and = 0, n_near = 0, n_other = 0;
+  // number terms: one straight-line program over the pixels (SK_ARITH)
+  // writes the number images that comparisons read; in a job's image table
+  // they follow the formula's own images (index img_kind.size() + k)
+  std::vector<ArithInsn> arith;
+  int n_num_images = 0;
+  int arith_regs = 0;
+  // accounting: primitive op counts by kind (threshold, not, and, N, rho,
+  // number terms, other)
+  int64_t n_thr = 0, n_not = 0, n_and = 0, n_near = 0, n_num = 0, n_other = 0;
 };
 
 constexpr int MAX_RZ_BATCH = 16;  // selects of one level run together in one step

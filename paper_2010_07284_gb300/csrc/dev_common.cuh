@@ -45,14 +45,44 @@ VL_DEV uint32_t near_word(uint32_t ul, uint32_t uc, uint32_t ur, uint32_t ml,
   return uc | dc | hdil(ml, mc, mr);
 }
 
-// Order-preserving map float -> uint32 (for selects on float keys).
+// Order-preserving map float -> uint32 (for selects on float keys); every
+// NaN maps to the largest key, after +infinity.
 VL_DEV uint32_t f2key(float f) {
+  if (f != f) return 0xFFFFFFFFu;
   uint32_t u = __float_as_uint(f);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 VL_DEV float key2f(uint32_t k) {
   uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
   return __uint_as_float(u);
+}
+
+// ---- number images: float or uint16 planes of H x pitch elements
+// (a uint16 pixel is its integer value, exact in float)
+
+// Channel ch of image im; plane_elems = H * pitch.
+VL_DEV const void* chan_ptr(const DevImage& im, int ch, size_t plane_elems) {
+  const size_t esz = im.format == PX_U16 ? 2 : 4;
+  return static_cast<const char*>(im.data) + (size_t)ch * plane_elems * esz;
+}
+
+// Element i of a channel plane.  `nc`: the read-only path may be used (the
+// image is not written during the launch).
+VL_DEV float ld_px(const void* p, int format, bool nc, size_t i) {
+  if (format == PX_U16) return (float)__ldg(static_cast<const unsigned short*>(p) + i);
+  const float* f = static_cast<const float*>(p) + i;
+  return nc ? __ldg(f) : __ldcg(f);
+}
+
+// Elements i .. i+3 (i a multiple of 4: 16- or 8-byte aligned).
+VL_DEV float4 ld_px4(const void* p, int format, bool nc, size_t i) {
+  if (format == PX_U16) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(p) + i));
+    return make_float4((float)(u.x & 0xFFFFu), (float)(u.x >> 16), (float)(u.y & 0xFFFFu),
+                       (float)(u.y >> 16));
+  }
+  const float4* f = reinterpret_cast<const float4*>(static_cast<const float*>(p) + i);
+  return nc ? __ldg(f) : __ldcg(f);
 }
 
 }  // namespace vl

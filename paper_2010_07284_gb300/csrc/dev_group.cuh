@@ -156,7 +156,9 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
       }
     } else if (I.op == I_THR) {
       const DevImage im = c.images[I.img];
-      const float* plane = im.data + (size_t)I.ch * c.H * c.pitch;
+      const void* plane = chan_ptr(im, I.ch, (size_t)c.H * c.pitch);
+      const int fmt = im.format;
+      const bool nc = !im.written;
       const float t = (I.slot >= 0) ? c.pct_val[I.slot] : I.t;
       const bool lt = (I.b & 1);
       uint32_t* d = gbuf(I.dst);
@@ -166,6 +168,27 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
       // word merge their 4-bit pieces with three shuffles
       constexpr int UNR = 2;
       const int sub = lane & 7;
+      if (fmt == PX_U16) {
+        // uint16 planes: one 8-byte load of 4 pixels per lane
+        const unsigned short* p16 = static_cast<const unsigned short*>(plane);
+        for (int idx0 = warp * 4; idx0 < nwords; idx0 += nw * 4) {
+          const int idx = idx0 + (lane >> 3);
+          const int i = i_lo + idx / bw, j = idx - (idx / bw) * bw, wg = c.w0 - 1 + j;
+          const int y = c.r0 - c.halo + i;
+          const bool in = idx < nwords && y >= 0 && y < c.H && wg >= 0 && wg < c.Wp;
+          uint2 q = make_uint2(0u, 0u);
+          if (in) q = __ldg(reinterpret_cast<const uint2*>(p16 + (size_t)y * c.pitch + 32 * wg + 4 * sub));
+          const float v0 = (float)(q.x & 0xFFFFu), v1 = (float)(q.x >> 16);
+          const float v2 = (float)(q.y & 0xFFFFu), v3 = (float)(q.y >> 16);
+          const uint32_t nib = lt ? ((v0 < t) | ((v1 < t) << 1) | ((v2 < t) << 2) | ((v3 < t) << 3))
+                                  : ((v0 > t) | ((v1 > t) << 1) | ((v2 > t) << 2) | ((v3 > t) << 3));
+          uint32_t word = nib << (4 * sub);
+          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+          if (sub == 0 && idx < nwords) d[i * bw + j] = in ? (word & vmask(wg, c.W)) : 0u;
+        }
+      } else
       for (int base = warp * 4 * UNR; base < nwords; base += nw * 4 * UNR) {
         float4 v[UNR];
         uint32_t inm = 0;
@@ -175,8 +198,9 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
           const int i = i_lo + idx / bw, wg = c.w0 - 1 + (idx - (idx / bw) * bw);
           const int y = c.r0 - c.halo + i;
           const bool in = idx < nwords && y >= 0 && y < c.H && wg >= 0 && wg < c.Wp;
-          v[u] = in ? __ldg(reinterpret_cast<const float4*>(plane + (size_t)y * c.pitch + 32 * wg) + sub)
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4* p4 = reinterpret_cast<const float4*>(
+              static_cast<const float*>(plane) + (size_t)y * c.pitch + 32 * wg) + sub;
+          v[u] = in ? (nc ? __ldg(p4) : __ldcg(p4)) : make_float4(0.f, 0.f, 0.f, 0.f);
           inm |= (in ? 1u : 0u) << u;
         }
 #pragma unroll

@@ -1,5 +1,6 @@
 // Exact order statistic of one image channel by radix select on
-// order-preserving float32 keys (three passes of 11, 11 and 10 bits).  The
+// order-preserving float32 keys (three passes of 8, 12 and 12 bits; NaN
+// sorts after +infinity).  The
 // percentile of level q is the value of rank floor(q*(n-1)) in ascending
 // order, no interpolation (the "percentiles" normalisation of Sec. 4.2).
 #pragma once
@@ -15,14 +16,15 @@ struct SelectSmem {
   uint32_t below;
 };
 
-// One CTA selects rank k of the H x W channel `plane` (row pitch `pitch`).
+// One CTA selects rank k of the H x W channel `plane` (row pitch `pitch`
+// elements, float or uint16 by `format`; `nc`: read-only path allowed).
 // Rows go to warps and columns to lanes (coalesced); lanes of a warp that
 // fall into the same bin add once (match_any), since pixels of smooth images
 // crowd into a few bins of the top digits; the digit holding rank k is found
 // with a block-wide scan of per-thread bin sums.  Returns the value in every
 // thread (after a block barrier).
-static __device__ __noinline__ float select_rank(SelectSmem& s, const float* plane, int H, int W, int pitch,
-                         long long k) {
+static __device__ __noinline__ float select_rank(SelectSmem& s, const void* plane, int format,
+                                                 bool nc, int H, int W, int pitch, long long k) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   uint32_t prefix = 0, pmask = 0;
@@ -40,13 +42,13 @@ static __device__ __noinline__ float select_rank(SelectSmem& s, const float* pla
     __syncthreads();
     constexpr int UNR = 8;  // loads in flight per lane
     for (int y = warp; y < H; y += nw) {
-      const float* row = plane + (size_t)y * pitch;
+      const size_t row = (size_t)y * pitch;
       for (int x0 = 0; x0 < W; x0 += 32 * UNR) {
         float v[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
           const int x = x0 + 32 * u + lane;
-          v[u] = x < W ? __ldg(row + x) : 0.f;
+          v[u] = x < W ? ld_px(plane, format, nc, row + x) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {

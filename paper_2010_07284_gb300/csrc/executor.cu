@@ -36,8 +36,8 @@ VL_DEV int ld_acquire(const int32_t* p) {
 // Rank codes of rows [y0, y1) of one channel against the sorted table tv
 // (see RankTab): one warp per 32-pixel word, one lane per pixel; code bit b
 // of the word's pixels is a ballot, written to plane b (lane b writes it).
-VL_DEV void rank_rows(const float* tv, const RankTab& T, const float* plane, int H, int W,
-                      int Wp, int pitch, int y0, int y1, uint32_t* out) {
+VL_DEV void rank_rows(const float* tv, const RankTab& T, const void* plane, int format, bool nc,
+                      int H, int W, int Wp, int pitch, int y0, int y1, uint32_t* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const size_t pstride = (size_t)H * Wp;
   const int nwords = (y1 - y0) * Wp;
@@ -45,7 +45,12 @@ VL_DEV void rank_rows(const float* tv, const RankTab& T, const float* plane, int
     const int y = y0 + idx / Wp, w = idx - (idx / Wp) * Wp;
     const int x = 32 * w + lane;
     const bool in = x < W;
-    const float v = in ? plane[(size_t)y * pitch + x] : 0.f;
+    float v = 0.f;
+    if (in) {
+      const size_t i = (size_t)y * pitch + x;
+      if (format == PX_U16) v = (float)static_cast<const unsigned short*>(plane)[i];
+      else v = nc ? __ldg(static_cast<const float*>(plane) + i) : __ldcg(static_cast<const float*>(plane) + i);
+    }
     int lo = 0, hi = T.m;  // thresholds below v (none for NaN)
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -64,6 +69,47 @@ VL_DEV void rank_rows(const float* tv, const RankTab& T, const float* plane, int
   }
 }
 
+// Number terms of rows [sub * ARITH_ROWS, +ARITH_ROWS): the program runs per
+// pixel on a register file in shared memory (register q of thread t at
+// R[q * blockDim + t]; no local memory).
+VL_DEV void arith_rows(const DevJob& J, int sub, unsigned char* smem) {
+  const int nt = blockDim.x, n = J.n_arith;
+  float* R = reinterpret_cast<float*>(smem);
+  ArithInsn* prog = reinterpret_cast<ArithInsn*>(R + (size_t)kArithMaxRegs * nt);
+  for (int i = threadIdx.x; i < n; i += nt) prog[i] = J.arith[i];
+  __syncthreads();
+  float* r = R + threadIdx.x;
+  const size_t plane = (size_t)J.H * J.pitch;
+  const int y0 = sub * ARITH_ROWS, rows = min(J.H - y0, ARITH_ROWS);
+  for (int idx = threadIdx.x; idx < rows * J.W; idx += nt) {
+    const int y = y0 + idx / J.W, x = idx - (idx / J.W) * J.W;
+    const size_t off = (size_t)y * J.pitch + x;
+    for (int k = 0; k < n; ++k) {
+      const ArithInsn A = prog[k];
+      if (A.op == A_VALUE) {
+        const DevImage im = J.images[A.img];
+        r[A.dst * nt] = ld_px(chan_ptr(im, A.ch, plane), im.format, !im.written, off);
+      } else if (A.op == A_STORE) {
+        float* out = static_cast<float*>(const_cast<void*>(J.images[J.first_num_image + A.img].data));
+        out[off] = r[A.a * nt];
+      } else {
+        const float u = r[A.a * nt];
+        const float w = A.b == kArithConst ? A.c : r[A.b * nt];
+        // one IEEE rounding per operation: the _rn intrinsics are never
+        // contracted into fused multiply-adds
+        float z;
+        switch (A.op) {
+          case A_ADD: z = __fadd_rn(u, w); break;
+          case A_SUB: z = __fsub_rn(u, w); break;
+          case A_MUL: z = __fmul_rn(u, w); break;
+          default: z = __fdiv_rn(u, w); break;
+        }
+        r[A.dst * nt] = z;
+      }
+    }
+  }
+}
+
 VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
                         unsigned char* smem, const ExecLaunch& L) {
   const int cap = min(J.H * J.W + 64, 1 << 22);
@@ -74,8 +120,8 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       const DevImage im = J.images[d.img];
       const long long n = (long long)J.H * J.W;
       const long long rank = (long long)(d.q * (double)(n - 1));
-      const float v = select_rank(s, im.data + (size_t)d.ch * J.H * J.pitch, J.H, J.W,
-                                  J.pitch, rank);
+      const float v = select_rank(s, chan_ptr(im, d.ch, (size_t)J.H * J.pitch), im.format,
+                                  !im.written, J.H, J.W, J.pitch, rank);
       if (threadIdx.x == 0) J.pct_val[d.slot] = v;
       break;
     }
@@ -104,11 +150,15 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       float* tv = reinterpret_cast<float*>(smem);
       for (int i = threadIdx.x; i < T.m; i += blockDim.x) tv[i] = J.rvals[T.val_off + i];
       __syncthreads();
-      rank_rows(tv, T, J.images[T.img].data + (size_t)T.ch * J.H * J.pitch, J.H, J.W, J.Wp,
-                J.pitch, rb * RANK_ROWS, min(J.H, (rb + 1) * RANK_ROWS),
+      const DevImage im = J.images[T.img];
+      rank_rows(tv, T, chan_ptr(im, T.ch, (size_t)J.H * J.pitch), im.format, !im.written, J.H,
+                J.W, J.Wp, J.pitch, rb * RANK_ROWS, min(J.H, (rb + 1) * RANK_ROWS),
                 J.planes + (size_t)T.plane0 * J.H * J.Wp);
       break;
     }
+    case SK_ARITH:
+      arith_rows(J, sub, smem);
+      break;
     case SK_RZ_LOCAL:
     case SK_RZ_FINAL: {
       CclSmem& s = *reinterpret_cast<CclSmem*>(smem);
@@ -206,7 +256,7 @@ __global__ void __launch_bounds__(EXEC_THREADS, 2) k_exec(ExecLaunch L) {
     __syncthreads();
     if (!s_skip) {
       int per_rz = 1;
-      if (S.kind >= SK_RZ_LOCAL) per_rz = L.need[ci] / S.rz_cnt;
+      if (S.kind >= SK_RZ_LOCAL && S.kind <= SK_RZ_FINAL) per_rz = L.need[ci] / S.rz_cnt;
       for (int k = 0; k < it.count; ++k) {
         run_subitem(J, S, it.first + k, per_rz, smem_raw, L);
         __syncthreads();
@@ -234,6 +284,8 @@ size_t exec_smem_bytes(int group_buffers, int group_bh, int group_bw) {
   size_t g = (size_t)group_buffers * group_bh * group_bw * 4;
   size_t m = sizeof(CclSmem);
   if (sizeof(SelectSmem) > m) m = sizeof(SelectSmem);
+  const size_t arith = (size_t)kArithMaxRegs * EXEC_THREADS * 4 + sizeof(ArithInsn) * kArithMaxInsns;
+  if (arith > m) m = arith;
   if (g > m) m = g;
   return (m + 15) & ~(size_t)15;
 }

@@ -24,7 +24,7 @@ int grid_for(long long items, int per_block, int cap = 152 * 32) {
 
 // A lane loads 4 pixels (16 bytes); the 8 lanes of a 32-pixel word merge
 // their 4-bit pieces with three shuffles; each warp keeps two loads in flight.
-__global__ void k_threshold(const float* __restrict__ plane, int pitch, MaskGeom g,
+__global__ void k_threshold(const void* __restrict__ plane, int format, int pitch, MaskGeom g,
                             float t, const float* t_dev, int lt, uint32_t* __restrict__ out) {
   if (t_dev) t = *t_dev;
   const int lane = threadIdx.x & 31, sub = lane & 7;
@@ -38,7 +38,7 @@ __global__ void k_threshold(const float* __restrict__ plane, int pitch, MaskGeom
       const long long i = base + 4 * u + (lane >> 3);
       if (i < nwords) {
         const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
-        v[u] = __ldg(reinterpret_cast<const float4*>(plane + (size_t)y * pitch + 32 * w) + sub);
+        v[u] = ld_px4(plane, format, true, (size_t)y * pitch + 32 * w + 4 * sub);
       } else {
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -98,11 +98,35 @@ __global__ void k_near(const uint32_t* __restrict__ a, MaskGeom g, int conn,
 
 // --------------------------------------------------------------- select --
 
-__global__ void __launch_bounds__(EXEC_THREADS) k_select(const float* plane, int pitch, int H,
-                                                         int W, long long rank, float* out) {
+__global__ void __launch_bounds__(EXEC_THREADS) k_select(const void* plane, int format, int pitch,
+                                                         int H, int W, long long rank, float* out) {
   __shared__ SelectSmem s;
-  float v = select_rank(s, plane, H, W, pitch, rank);
+  float v = select_rank(s, plane, format, true, H, W, pitch, rank);
   if (threadIdx.x == 0) *out = v;
+}
+
+// ----------------------------------------------------------- arithmetic --
+
+// out = a (op) b pixel by pixel over H x W (row pitch `pitch` elements); b
+// is a plane or, when null, the constant c.  One IEEE rounding per pixel.
+__global__ void k_arith(int op, const void* __restrict__ a, int a_format, const void* b,
+                        int b_format, float c, float* out, int H, int W, int pitch) {
+  const long long n = (long long)H * W;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const size_t off = (size_t)y * pitch + x;
+    const float u = ld_px(a, a_format, false, off);
+    const float w = b ? ld_px(b, b_format, false, off) : c;
+    float z;
+    switch (op) {
+      case A_ADD: z = __fadd_rn(u, w); break;
+      case A_SUB: z = __fsub_rn(u, w); break;
+      case A_MUL: z = __fmul_rn(u, w); break;
+      default: z = __fdiv_rn(u, w); break;
+    }
+    out[off] = z;
+  }
 }
 
 // ------------------------------------------------------------------ ccl --
@@ -203,11 +227,11 @@ __global__ void k_clear_padding(uint32_t* m, MaskGeom g) {
 
 // ============================================================ wrappers ==
 
-cudaError_t launch_threshold(const float* plane, int pitch, MaskGeom g, float t,
+cudaError_t launch_threshold(const void* plane, int format, int pitch, MaskGeom g, float t,
                              const float* t_dev, bool lt, uint32_t* out, cudaStream_t st) {
   long long nwords = (long long)g.H * g.Wp;
-  k_threshold<<<grid_for(nwords * 4, kThreads * 4), kThreads, 0, st>>>(plane, pitch, g, t,
-                                                                      t_dev, lt, out);
+  k_threshold<<<grid_for(nwords * 4, kThreads * 4), kThreads, 0, st>>>(plane, format, pitch, g,
+                                                                      t, t_dev, lt, out);
   return cudaGetLastError();
 }
 
@@ -248,9 +272,16 @@ cudaError_t launch_near(const uint32_t* a, MaskGeom g, int conn, uint32_t* out,
   k_near<<<grid_for((long long)g.H * g.Wp, kThreads * 2), kThreads, 0, st>>>(a, g, conn, out);
   return cudaGetLastError();
 }
-cudaError_t launch_select(const float* plane, int pitch, int H, int W, long long rank,
+cudaError_t launch_select(const void* plane, int format, int pitch, int H, int W, long long rank,
                           float* out, cudaStream_t st) {
-  k_select<<<1, EXEC_THREADS, 0, st>>>(plane, pitch, H, W, rank, out);
+  k_select<<<1, EXEC_THREADS, 0, st>>>(plane, format, pitch, H, W, rank, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arith(int op, const void* a, int a_format, const void* b, int b_format, float c,
+                         float* out, int H, int W, int pitch, cudaStream_t st) {
+  k_arith<<<grid_for((long long)H * W, kThreads), kThreads, 0, st>>>(op, a, a_format, b, b_format,
+                                                                    c, out, H, W, pitch);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,8 @@ struct MaskGeom {
 };
 
 // ---- plain per-operator kernels (one launch per primitive) ----
-cudaError_t launch_threshold(const float* plane, int pitch, MaskGeom g, float t,
+// `plane`: one channel of H x pitch elements, float or uint16 by `format`.
+cudaError_t launch_threshold(const void* plane, int format, int pitch, MaskGeom g, float t,
                              const float* t_dev, bool lt, uint32_t* out, cudaStream_t st);
 cudaError_t launch_not(const uint32_t* a, MaskGeom g, uint32_t* out, cudaStream_t st);
 cudaError_t launch_and(const uint32_t* a, const uint32_t* b, MaskGeom g, uint32_t* out,
@@ -25,8 +26,12 @@ cudaError_t launch_andnot(const uint32_t* a, const uint32_t* b, MaskGeom g, uint
 cudaError_t launch_const(MaskGeom g, bool value, uint32_t* out, cudaStream_t st);
 cudaError_t launch_near(const uint32_t* a, MaskGeom g, int conn, uint32_t* out,
                         cudaStream_t st);
-cudaError_t launch_select(const float* plane, int pitch, int H, int W, long long rank,
+cudaError_t launch_select(const void* plane, int format, int pitch, int H, int W, long long rank,
                           float* out, cudaStream_t st);
+// out = a (op) b per pixel (op an ArithOp, A_ADD .. A_DIV); b null: the
+// constant c.
+cudaError_t launch_arith(int op, const void* a, int a_format, const void* b, int b_format, float c,
+                         float* out, int H, int W, int pitch, cudaStream_t st);
 
 // ---- connected components (tile-local, merge, flags, final) ----
 struct CclScratch {

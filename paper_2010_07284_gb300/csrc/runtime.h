@@ -76,7 +76,8 @@ struct vl_image {
   vl_context* ctx = nullptr;
   int H = 0, W = 0, C = 0, Wp = 0, pitch = 0;
   int is_mask = 0;
-  float* data = nullptr;
+  int format = vl::PX_F32;  // number images: PX_F32 or PX_U16 elements
+  void* data = nullptr;     // number images: C planes of H x pitch elements
   uint32_t* mask = nullptr;
   vl::DevBlockPtr block;
   std::shared_ptr<vl::EventHolder> ready;  // recorded after the upload

@@ -82,7 +82,27 @@ enum StepKind : int32_t {
   SK_RZ_FLAGS = 4,   // rho batch, flags to global roots: item = (rz, chunk)
   SK_RZ_FINAL = 5,   // rho batch, relabel + write Z: item = (rz, tile)
   SK_RANK = 6,       // rank codes of threshold tables: item = (table, row block)
+  SK_ARITH = 7,      // number terms: item = row block, writes the number images
 };
+
+// Rows of one arithmetic work item.
+constexpr int ARITH_ROWS = 8;
+
+// Number terms of a formula as one straight-line program run per pixel on a
+// register file of floats: A_VALUE loads image[img].channel[ch], the
+// operations read registers a and b (b = kArithConst: the constant c) and
+// write dst, A_STORE writes register a to number image `img` (counted from
+// the first number image).  Every operation rounds to float once.
+enum ArithOp : uint8_t { A_VALUE = 0, A_ADD = 1, A_SUB = 2, A_MUL = 3, A_DIV = 4, A_STORE = 5 };
+constexpr uint8_t kArithConst = 0xFF;
+constexpr int kArithMaxRegs = 16;
+constexpr int kArithMaxInsns = 1024;
+struct ArithInsn {   // 12 bytes
+  uint8_t op, dst, a, b;
+  int16_t img, ch;
+  float c;
+};
+static_assert(sizeof(ArithInsn) == 12, "ArithInsn layout");
 
 // Rows of one rank-code work item.
 constexpr int RANK_ROWS = 8;
@@ -133,11 +153,20 @@ struct PctDesc {
 };
 
 // ----------------------------------------------------- executor job table
+// Pixel formats of number images.
+constexpr int32_t PX_F32 = 0;
+constexpr int32_t PX_U16 = 1;
+
 struct DevImage {
-  const float* data;       // float images: channels planes of H x pitch
+  const void* data;        // number images: channels planes of H x pitch
+                           //   elements (float, or uint16 by `format`)
   const uint32_t* mask;    // mask images: H x Wp words
   int32_t channels;
   int32_t is_mask;
+  int32_t format;          // PX_F32 or PX_U16
+  int32_t written;         // 1: written earlier in the same launch (number
+                           //   images of SK_ARITH): read through L2, not the
+                           //   read-only path
 };
 
 struct DevJob {
@@ -173,6 +202,9 @@ struct DevJob {
   int32_t n_rtab;
   int32_t pad_;
   uint32_t* planes;             // rank-code planes, H x Wp words each
+  const ArithInsn* arith;       // number-term program (SK_ARITH)
+  int32_t n_arith;
+  int32_t first_num_image;      // image index of number image 0
 };
 
 VL_HD_INLINE int32_t* rz_G(const DevJob& J, int k) {

@@ -77,16 +77,43 @@ def simulate(plan: dict, images, masks_by_image: dict, conn: int, seed: int = 0,
     base_mask = sz["n_inter_slots"] + sz["n_root_slots"]
     for k, img in enumerate(plan["mask_slot_images"]):
         slots[base_mask + k] = masks_by_image[img].astype(bool)
+    # number images (step kind 7) follow the formula's own images
+    first_num = plan.get("first_number_image", len(images))
+    nums = {}
+
+    def img_of(k):
+        if k >= first_num:
+            if k - first_num not in nums:
+                raise AssertionError("a number image is read before the step that writes it")
+            return nums[k - first_num]
+        return np.asarray(images[k], dtype=np.float32)
+
     pct = {}
-    for d in plan["pct"]:
-        v = np.sort(images[d["image"]][d["channel"]].ravel())
-        pct[d["slot"]] = v[int(np.floor(d["q"] * (v.size - 1)))]
     insns = plan["insns"]
     sels = plan["selects"]
     pending_sel = {}
     for si in (order if order is not None else range(len(plan["steps"]))):
         st = plan["steps"][si]
         kind = st["kind"]
+        if kind == 7:  # number terms: the program on every pixel, in float32
+            regs = {}
+            for A in plan["arith"]:
+                if A["op"] == 0:
+                    regs[A["dst"]] = img_of(A["image"])[A["channel"]].astype(np.float32)
+                elif A["op"] == 5:
+                    nums[A["image"]] = regs[A["a"]][None].copy()
+                else:
+                    u = regs[A["a"]]
+                    w = np.float32(A["c"]) if A["b"] == 255 else regs[A["b"]]
+                    with np.errstate(all="ignore"):
+                        regs[A["dst"]] = {1: np.add, 2: np.subtract, 3: np.multiply,
+                                          4: np.divide}[A["op"]](u, w).astype(np.float32)
+            continue
+        if kind == 0:  # percentiles (numpy sorts NaN last)
+            for d in plan["pct"]:
+                v = np.sort(img_of(d["image"])[d["channel"]].ravel())
+                pct[d["slot"]] = v[int(np.floor(d["q"] * (v.size - 1)))]
+            continue
         if kind == 1:
             halo = st["halo"]
             prog = insns[st["insn_off"]:st["insn_off"] + st["insn_cnt"]]
@@ -122,14 +149,16 @@ def simulate(plan: dict, images, masks_by_image: dict, conn: int, seed: int = 0,
                             outs[s] = True
                             continue
                         if op == 1:
-                            ch = images[ins["image"]][ins["channel"]]
+                            ch = img_of(ins["image"])[ins["channel"]]
+                            if ins["slot"] >= 0 and ins["slot"] not in pct:
+                                raise AssertionError(f"step {si}: percentile read before it is computed")
                             t = pct[ins["slot"]] if ins["slot"] >= 0 else np.float32(ins["t"])
                             v = ch[rr][:, cc]
                             val = (v < t) if ins["b"] & 1 else (v > t)
                         elif op == 10:  # threshold by rank code
                             tab = plan["rank_tables"][ins["a"]]
                             vals = plan["rank_values"][tab["value_off"]:tab["value_off"] + tab["m"]]
-                            v = images[tab["image"]][tab["channel"]][rr][:, cc]
+                            v = img_of(tab["image"])[tab["channel"]][rr][:, cc]
                             nan = np.isnan(v)
                             below = np.searchsorted(vals, np.where(nan, 0, v), side="left")
                             hit = vals[np.minimum(below, tab["m"] - 1)] == v

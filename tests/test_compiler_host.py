@@ -232,3 +232,120 @@ def test_step_dependencies_with_percentiles_and_masks():
     img = wl.mri_phantom_batch([(70, 90)], seed=4)[0]
     for k in range(3):
         _check_sim(f, [img], conn=8, shuffle=10 + k)
+
+
+# ---------------------------------------------------------- number terms --
+
+def _two_channel(h, w, seed):
+    return np.stack([wl.gaussian_field_image(h, w, seed=seed)[0], wl.uniform_image(h, w, seed=seed)[0]])
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("conn", [4, 8])
+def test_number_terms_plan_matches_oracle(seed, conn):
+    """Random formulas with + - * / over two channels, compared by
+    percentiles and sign tests: the planned program (one pass over the
+    pixels, registers reused) and any dependency-respecting step order give
+    the oracle's masks."""
+    pytest.importorskip("scipy")
+    f = wl.arith_dag(70, seed=seed)
+    img = _two_channel(45, 170, seed)
+    plan = _check_sim(f, [img], conn=conn)
+    assert plan["steps"][0]["kind"] == 7 and plan["arith"]
+    for k in range(2):
+        _check_sim(f, [img], conn=conn, shuffle=20 + k)
+
+
+def test_number_terms_on_uint16_images():
+    pytest.importorskip("scipy")
+    f = wl.arith_dag(50, seed=9)
+    img = wl.uniform_image_u16(33, 140, channels=2, seed=9)
+    img[:, ::7, ::5] = 0  # quotients 0/0 and x/0: NaN and infinities
+    _check_sim(f, [img], conn=8)
+
+
+def test_comparing_a_channel_value_is_a_plain_threshold():
+    """THR(VALUE(i, c)) is the threshold of the channel itself: shared with
+    it, and no arithmetic step."""
+    rec = [("VALUE", -1, -1, 0, 1, 0, 0), ("THR_GT", 0, -1, 0, 0, 0.5, 0),
+           ("THR_GT", -1, -1, 0, 1, 0.5, 0), ("AND", 1, 2, 0, 0, 0, 0),
+           ("PCT_LT", 0, -1, 0, 0, 0, 0.25), ("AND", 3, 4, 0, 0, 0, 0)]
+    F = vg.compile_formula(rec, [5])
+    p = F.plan()
+    assert not p["arith"] and all(s["kind"] != 7 for s in p["steps"])
+    assert p["pct"][0]["image"] == 0 and p["pct"][0]["channel"] == 1
+    thr = [i for i in p["insns"] if i["op"] == 1 and i["slot"] < 0]
+    assert len(thr) == 1 and (thr[0]["image"], thr[0]["channel"]) == (0, 1)
+    assert F.info()["n_number_images"] == 0
+
+
+def test_number_images_follow_the_formula_images_and_dead_terms_vanish():
+    rec = [("VALUE", -1, -1, 0, 0, 0, 0), ("VALUE", -1, -1, 2, 0, 0, 0),     # images 0 and 2
+           ("MUL", 0, 1, 0, 0, 0, 0), ("THR_GT", 2, -1, 0, 0, 0.25, 0),
+           ("ADD", 0, -1, 0, 0, 3.0, 0), ("THR_LT", 4, -1, 0, 0, 1.0, 0),      # dead
+           ("MASK", -1, -1, 1, 0, 0, 0), ("AND", 3, 6, 0, 0, 0, 0)]
+    F = vg.compile_formula(rec, [7])
+    p = F.plan()
+    assert p["first_number_image"] == 3 and p["n_number_images"] == 1
+    assert [a["op"] for a in p["arith"]] == [0, 0, 3, 5]      # value, value, mul, store
+    assert all(a["op"] != 1 for a in p["arith"])               # the dead + is gone
+    thr = [i for i in p["insns"] if i["op"] == 1]
+    assert [i["image"] for i in thr] == [3]
+    # the group comparing the number image waits for the arithmetic step
+    arith_step = [k for k, s in enumerate(p["steps"]) if s["kind"] == 7][0]
+    for k, s in enumerate(p["steps"]):
+        if s["kind"] == 1:
+            assert arith_step in p["deps"][k]
+
+
+def test_rank_table_on_a_number_image():
+    """Many constant thresholds of one number term share a rank table that
+    reads the number image."""
+    pytest.importorskip("scipy")
+    nodes = [wl.Node("VALUE", channel=0), wl.Node("VALUE", channel=1), wl.Node("SUB", a=0, b=1)]
+    ts = [-0.5, -0.25, 0.0, 0.125, 0.25, 0.5]
+    for k, t in enumerate(ts):
+        nodes.append(wl.Node("THR_GT" if k % 2 else "THR_LT", a=2, t=t))
+    nodes.append(wl.Node("AND", a=3, b=4))
+    nodes.append(wl.Node("NEAR", a=9))
+    f = wl.Formula(nodes, list(range(3, len(nodes))))
+    img = _two_channel(40, 260, 4)
+    plan = _check_sim(f, [img], conn=8)
+    assert plan["rank_tables"] and plan["rank_tables"][0]["image"] == plan["first_number_image"]
+
+
+@pytest.mark.parametrize("rec,roots", [
+    ([("VALUE", -1, -1, 0, 0, 0, 0)], [0]),                                      # number root
+    ([("VALUE", -1, -1, 0, 0, 0, 0), ("NEAR", 0, -1, 0, 0, 0, 0)], [1]),         # N of a number
+    ([("THR_GT", -1, -1, 0, 0, 0.5, 0), ("MUL", 0, -1, 0, 0, 2, 0),
+      ("THR_GT", 1, -1, 0, 0, 0, 0)], [2]),                                     # * of a mask
+    ([("THR_GT", -1, -1, 0, 0, 0.5, 0), ("THR_LT", 0, -1, 0, 0, 0, 0)], [1]),   # threshold of a mask
+    ([("VALUE", -1, -1, 0, 0, 0, 0), ("ADD", 0, -1, 0, 0, float("nan"), 0),
+      ("THR_GT", 1, -1, 0, 0, 0, 0)], [2]),                                     # NaN constant
+    ([("VALUE", -1, -1, 0, 0, 0, 0), ("ADD", 0, 5, 0, 0, 0, 0),
+      ("THR_GT", 1, -1, 0, 0, 0, 0)], [2]),                                     # operand after node
+])
+def test_number_terms_and_masks_do_not_mix(rec, roots):
+    with pytest.raises(N.VlError) as e:
+        vg.compile_formula(rec, roots)
+    assert e.value.code == N.ERR_FORMULA
+
+
+def test_number_terms_register_limit():
+    """17 channel values live at once (each summed only at the end) exceed
+    the 16 registers of the arithmetic step: a clean compile error; 16 fit."""
+    def chain(k):
+        # k channel values, summed from the last one back to the first: all
+        # k are live when the first add runs
+        rec = [("VALUE", -1, -1, 0, c, 0, 0) for c in range(k)]
+        acc = k - 1
+        for c in range(k - 2, -1, -1):
+            rec.append(("ADD", acc, c, 0, 0, 0, 0))
+            acc = len(rec) - 1
+        rec.append(("THR_GT", acc, -1, 0, 0, 0.0, 0))
+        return rec
+    p = vg.compile_formula(chain(16), [len(chain(16)) - 1]).plan()
+    assert max(a["dst"] for a in p["arith"]) == 15
+    with pytest.raises(N.VlError) as e:
+        vg.compile_formula(chain(17), [len(chain(17)) - 1])
+    assert e.value.code == N.ERR_FORMULA

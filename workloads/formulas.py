@@ -25,7 +25,10 @@ import numpy as np
 PRIMITIVE_OPS = ("TRUE", "FALSE", "THR_GT", "THR_LT", "PCT_GT", "PCT_LT",
                  "MASK", "NOT", "AND", "NEAR", "REACH")
 DERIVED_OPS = ("OR", "INTERIOR", "SURROUNDED", "GROW", "TOUCH")
-OPS = PRIMITIVE_OPS + DERIVED_OPS
+# number terms: VALUE reads a channel; ADD/SUB/MUL/DIV take two terms, or a
+# term and the constant t when b = -1; THR_*/PCT_* with a >= 0 compare term a
+NUMBER_OPS = ("VALUE", "ADD", "SUB", "MUL", "DIV")
+OPS = PRIMITIVE_OPS + DERIVED_OPS + NUMBER_OPS
 UNARY = ("NOT", "NEAR", "INTERIOR")
 BINARY = ("AND", "REACH", "OR", "SURROUNDED", "GROW", "TOUCH")
 ATOMS = ("TRUE", "FALSE", "THR_GT", "THR_LT", "PCT_GT", "PCT_LT", "MASK")
@@ -61,6 +64,8 @@ class Formula:
             if nd.op in UNARY and not (0 <= nd.a < i):
                 raise ValueError(f"node {i}: bad operand {nd.a}")
             if nd.op in BINARY and not (0 <= nd.a < i and 0 <= nd.b < i):
+                raise ValueError(f"node {i}: bad operands {nd.a},{nd.b}")
+            if nd.op in NUMBER_OPS[1:] and not (0 <= nd.a < i and nd.b < i):
                 raise ValueError(f"node {i}: bad operands {nd.a},{nd.b}")
         for r in self.roots:
             if not 0 <= r < n:
@@ -240,6 +245,74 @@ def config4_formula() -> Formula:
     ninner = add("NOT", a=inner)
     edge = add("AND", a=gtv, b=ninner)
     f = Formula(n, [seg, act, gtv, edge], name="config4")
+    f.validate()
+    return f
+
+
+def arith_dag(n_nodes: int = 60, seed: int = 0, n_channels: int = 2,
+              n_images: int = 1, p_const: float = 0.3) -> Formula:
+    """A random formula with number terms (the tool's basic arithmetic,
+    Sec. 3): channel values combined by + - * / (with each other or with
+    constants), compared by percentile thresholds (the values of products
+    and quotients have no fixed range) and by sign tests against 0, and the
+    masks combined by not / and / N / rho.  Roots: the unconsumed masks."""
+    rng = np.random.default_rng(seed)
+    nodes: List[Node] = []
+    nums: List[int] = []
+    masks: List[int] = []
+    for im in range(n_images):
+        for c in range(n_channels):
+            nodes.append(Node("VALUE", image=im, channel=c))
+            nums.append(len(nodes) - 1)
+    consumed = set()
+    while len(nodes) < n_nodes:
+        r = rng.random()
+        if r < 0.35 or len(masks) < 2:
+            # arithmetic on recent terms (deep expressions), or a new channel
+            a = nums[-1 - int(rng.integers(0, min(4, len(nums))))]
+            op = ("ADD", "SUB", "MUL", "DIV")[int(rng.integers(0, 4))]
+            if rng.random() < p_const:
+                c = f32(rng.uniform(-2.0, 2.0))
+                if op == "DIV" and c == 0.0:
+                    c = 1.0
+                nodes.append(Node(op, a=a, t=c))
+            else:
+                b = nums[int(rng.integers(0, len(nums)))]
+                nodes.append(Node(op, a=a, b=b))
+            nums.append(len(nodes) - 1)
+            consumed.add(a)
+            # compare it
+            x = len(nodes) - 1
+            if rng.random() < 0.7:
+                op = "PCT_GT" if rng.random() < 0.5 else "PCT_LT"
+                nodes.append(Node(op, a=x, q=float(rng.choice([0.1, 0.25, 0.5, 0.75, 0.9]))))
+            else:
+                op = "THR_GT" if rng.random() < 0.5 else "THR_LT"
+                nodes.append(Node(op, a=x, t=0.0))
+            masks.append(len(nodes) - 1)
+        else:
+            kind = ("NOT", "AND", "NEAR", "REACH")[int(rng.choice(4, p=(0.2, 0.35, 0.25, 0.2)))]
+            a = masks[-1 - int(rng.integers(0, min(4, len(masks))))]
+            if kind in ("NOT", "NEAR"):
+                nodes.append(Node(kind, a=a))
+            else:
+                b = masks[int(rng.integers(0, len(masks)))]
+                nodes.append(Node(kind, a=a, b=b))
+                consumed.add(b)
+            consumed.add(a)
+            masks.append(len(nodes) - 1)
+    roots = [m for m in masks if m not in consumed] or [masks[-1]]
+    f = Formula(nodes, roots, name=f"arith{n_nodes}_s{seed}", meta={"seed": seed})
+    f.validate()
+    return f
+
+
+def grow_spec_u16_formula() -> Formula:
+    """The segmentation spec of Fig. "specification" as the paper runs it: on
+    16-bit pixels, intensity > 62258 (0.95 of 65535) and > 56360 (0.86),
+    gtv = grow(hI, vI)."""
+    n = [Node("THR_GT", t=62258.0), Node("THR_GT", t=56360.0), Node("GROW", a=0, b=1)]
+    f = Formula(n, [2], name="grow_spec_u16")
     f.validate()
     return f
 

@@ -236,3 +236,15 @@ def upscaled_slice(side: int = 7680, base: int = 240, seed: int = 0) -> np.ndarr
     ph = mri_phantom(base, base, np.random.default_rng([seed, 7680]))
     z = nd.zoom(ph[0].astype(np.float64), side / base, order=1, mode="nearest")
     return z[:side, :side].astype(np.float32)[None]
+
+
+def to_u16(img: np.ndarray) -> np.ndarray:
+    """A [0, 1] image as 16-bit pixels: round(v * 65535), clipped (the paper
+    scales its normalised slices by 2^16 - 1, Sec. 4.2)."""
+    return np.clip(np.rint(np.asarray(img, dtype=np.float64) * 65535.0), 0, 65535).astype(np.uint16)
+
+
+def uniform_image_u16(h: int, w: int, channels: int = 1, seed: int = 0) -> np.ndarray:
+    """(C, H, W) uint16 pixels, uniform over 0..65535."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 65536, size=(channels, h, w), dtype=np.uint16)
