@@ -204,8 +204,33 @@ def leg_grow_7680(ctx, stream, flush, runs: int = 5) -> dict:
             im2.close()
         b.close()
         im.close()
+        # the same spec as the paper runs it: 16-bit pixels, thresholds 62258
+        # and 56360 (2 bytes per pixel read instead of 4)
+        fu = wl.grow_spec_u16_formula()
+        Fu = ctx.compile(wl.formula_to_records(fu), fu.roots, 8)
+        img16 = wl.to_u16(img)
+        im16 = ctx.image(img16, stream)
+        bu = ctx.batch([(Fu, [im16])], stream)
+        for _ in range(2):
+            bu.run(stream)
+        ev16 = []
+        for _ in range(runs):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bu.run(stream)
+            z.record(stream)
+            ev16.append((a, z))
+        stream.synchronize()
+        if bu.result(0).status_word() != 0:
+            raise SystemExit("grow 7680 uint16 failed")
+        u16_ms = float(np.mean([a.elapsed_time(z) for a, z in ev16]))
+        bu.close()
+        im16.close()
     return {"workload": "grow(I > 0.95, I > 0.86) on a 7680x7680 upscaled MRI-shaped slice (59 Mpx)",
             "device_ms": dev_ms, "e2e_ms": float(np.mean(e2e)),
+            "uint16": {"device_ms": u16_ms, "thresholds": [62258, 56360],
+                       "value": n_prim * P / (u16_ms / 1e3) / 1e9},
             "value": n_prim * P / (dev_ms / 1e3) / 1e9, "unit": "Gpixel-ops/s",
             "e2e_bytes": {"h2d": int(img.nbytes), "d2h": int(out.nbytes)},
             "paper_context_ms": {"TITAN Xp (OpenCL, D2H included)": 600,
@@ -295,6 +320,31 @@ def leg_ccl(ctx, stream, flush, peak: float, S: int = 8192, runs: int = 6) -> di
             "achieved_GBps": 4.125 * S * S / (cms / 1e3) / 1e9,
             "frac": 4.125 * S * S / (cms / 1e3) / 1e9 / peak,
             "traffic": profiled_traffic("ccl", "dram_bytes_per_labelling") if S == 8192 else None}
+
+
+def leg_pointer_jumping(ctx, stream, union_find_ms: float, S: int = 8192, runs: int = 3) -> dict:
+    """The paper's pointer-jumping labelling (Alg. 1, reconnect every 16
+    main iterations, host-checked termination each round) on the CCL leg's
+    mask, timed on the host clock around the synchronous call: the in-library
+    comparison for the union-find labelling (context, not a target)."""
+    import torch
+    m = torch.rand((S, S), device="cuda", generator=torch.Generator("cuda").manual_seed(3)) < 0.5
+    with torch.cuda.stream(stream):
+        mimg = ctx.mask(m.to(torch.uint8), stream)
+        labels = torch.empty(S * S, dtype=torch.int32, device="cuda")
+        stream.synchronize()
+        ms, iters = [], 0
+        for k in range(runs + 1):
+            t0 = time.perf_counter()
+            iters = ctx.ccl_pointer_jumping(mimg, labels, 8, period=16, stream=stream)
+            if k:
+                ms.append(1e3 * (time.perf_counter() - t0))
+    mimg.close()
+    pj = float(np.mean(ms))
+    return {"algorithm": "pointer jumping (Alg. 1), reconnect period 16", "ms": pj,
+            "main_iterations": iters, "value": S * S / (pj / 1e3) / 1e9, "unit": "Gpix/s",
+            "mask": f"{S}x{S} Bernoulli(0.5), 8-adjacency",
+            "union_find_speedup": pj / union_find_ms}
 
 
 def leg_mri_batch(ctx, stream, flush, n_images: int = 4096, reps: int = 5) -> dict:
@@ -611,6 +661,7 @@ def main():
         line["batched_over_plain"] = line["value"] / world / line["plain"]["value"]
         # ---- full CCL on an 8192 x 8192 Bernoulli(0.5) mask
         line["ccl"] = leg_ccl(ctx, stream, flush, peak)
+        line["ccl"]["pointer_jumping"] = leg_pointer_jumping(ctx, stream, line["ccl"]["ms"])
         # ---- end to end through the public API with host buffers
         import torch as _t
         pin_in = _t.from_numpy(host_img).pin_memory()

@@ -491,6 +491,26 @@ VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask,
                         int32_t connectivity, int32_t* labels_dev,
                         void* stream);
 
+/* The paper's own labelling (Sec. 3.3, Alg. 1), for comparison: labels are
+ * pixel indices; every set pixel starts with its own; a main iteration
+ * gives pixel p the largest label around the pixel its label names
+ * (pointer jumping); every `period` main iterations (0: 16, the period the
+ * paper's text gives) a reconnect step raises, by atomic maximum, the label
+ * of the pixel that p's label names to the largest label around p; then a
+ * termination check (no set pixel has a set neighbour with another label)
+ * is read back by the host.  On return labels_dev (device, h*w int32) holds,
+ * for every set pixel, the index of one pixel of its component (the same
+ * for the whole component), -1 for background: the same partition as
+ * vl_ccl, under other label values.  Synchronous: waits for `stream` once
+ * per round.  *iterations (may be NULL) receives the number of main
+ * iterations.  VL_ERR_TIMEOUT if max_rounds rounds (0: 65536) did not
+ * converge; VL_ERR_ARG for a non-mask image, a null buffer or connectivity
+ * other than 4 or 8. */
+VL_API vl_status vl_ccl_pointer_jumping(vl_context* ctx, const vl_image* mask,
+                                        int32_t connectivity, int32_t period,
+                                        int32_t max_rounds, int32_t* labels_dev,
+                                        void* stream, int32_t* iterations);
+
 /* Synchronise `stream` and return the status word of the last vl_ccl call
  * on this context (VL_OK, VL_ERR_TIMEOUT, VL_ERR_INTERNAL). */
 VL_API vl_status vl_ccl_status(vl_context* ctx, void* stream);

@@ -160,6 +160,7 @@ SIGNATURES = [
     ("vl_result_device_ptr", C.c_int, [_P, _I32, _PP]),
     ("vl_ccl", C.c_int, [_P, _P, _I32, _P, _P]),
     ("vl_ccl_status", C.c_int, [_P, _P]),
+    ("vl_ccl_pointer_jumping", C.c_int, [_P, _P, _I32, _I32, _I32, _P, _P, C.POINTER(_I32)]),
     ("vl_ccl_noalloc", C.c_int, [_P, _I32, _I32, _I32, _P, _I32, _P]),
     ("vl_server_create", C.c_int, [_P, C.POINTER(VlServerConfig), _PP]),
     ("vl_server_submit", C.c_int, [_P, _P, _PP, _I32, C.POINTER(_I64)]),

@@ -234,6 +234,18 @@ class Context(_Handle):
         rc = N.load().vl_ccl(self._ptr, mask._ptr, conn, labels.data_ptr(), _stream_handle(stream))
         self._check(rc)
 
+    def ccl_pointer_jumping(self, mask: "Image", labels, conn: int = 8, period: int = 16,
+                            max_rounds: int = 0, stream=None) -> int:
+        """The paper's pointer-jumping labelling (comparison only) into a
+        caller-owned int32 CUDA tensor of H*W elements; synchronous.  Labels
+        are one pixel index per component (not the minimum).  Returns the
+        number of main iterations."""
+        it = C.c_int32()
+        rc = N.load().vl_ccl_pointer_jumping(self._ptr, mask._ptr, conn, period, max_rounds,
+                                             labels.data_ptr(), _stream_handle(stream), C.byref(it))
+        self._check(rc)
+        return it.value
+
     def ccl_status(self, stream=None) -> int:
         return N.load().vl_ccl_status(self._ptr, _stream_handle(stream))
 

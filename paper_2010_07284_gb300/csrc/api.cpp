@@ -1348,6 +1348,35 @@ VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask, int32_t connectiv
   return VL_OK;
 }
 
+VL_API vl_status vl_ccl_pointer_jumping(vl_context* ctx, const vl_image* mask, int32_t connectivity,
+                                        int32_t period, int32_t max_rounds, int32_t* labels_dev,
+                                        void* stream, int32_t* iterations) {
+  if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
+  if (!valid(mask, TAG_IMG) || !mask->is_mask) return set_err(ctx, VL_ERR_ARG, "pointer jumping needs a mask image");
+  if (!labels_dev) return set_err(ctx, VL_ERR_ARG, "null labels buffer");
+  if (connectivity != 4 && connectivity != 8) return set_err(ctx, VL_ERR_ARG, "connectivity must be 4 or 8");
+  if (period < 0 || max_rounds < 0) return set_err(ctx, VL_ERR_ARG, "negative period or round limit");
+  DeviceGuard dg(ctx->device);
+  const size_t n = (size_t)mask->H * mask->W;
+  DevBlockPtr tmp;  // second label buffer + termination flag
+  cudaError_t e = dev_alloc(ctx, align_up(n * 4, 256) + 256, S(stream), &tmp);
+  if (e) return cuda_err(ctx, e, "allocating pointer-jumping scratch");
+  int32_t* scratch = static_cast<int32_t*>(tmp->ptr);
+  int32_t* flag = reinterpret_cast<int32_t*>(static_cast<char*>(tmp->ptr) + align_up(n * 4, 256));
+  vl_image* mi = const_cast<vl_image*>(mask);
+  if ((e = wait_images(&mi, 1, S(stream)))) return cuda_err(ctx, e, "waiting for the mask");
+  int32_t flag_host = 0;
+  int iters = 0;
+  bool converged = false;
+  e = ccl_pointer_jumping(mask->mask, MaskGeom{mask->H, mask->W, mask->Wp}, connectivity,
+                          period ? period : 16, max_rounds ? max_rounds : 65536, labels_dev, scratch,
+                          flag, &flag_host, S(stream), &iters, &converged);
+  if (e) return cuda_err(ctx, e, "running pointer jumping");
+  if (iterations) *iterations = iters;
+  if (!converged) return set_err(ctx, VL_ERR_TIMEOUT, "pointer jumping did not converge within the round limit");
+  return VL_OK;
+}
+
 VL_API vl_status vl_ccl_status(vl_context* ctx, void* stream) {
   if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
   DeviceGuard dg(ctx->device);

@@ -169,24 +169,36 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
       constexpr int UNR = 2;
       const int sub = lane & 7;
       if (fmt == PX_U16) {
-        // uint16 planes: one 8-byte load of 4 pixels per lane
+        // uint16 planes: 8-byte loads of 4 pixels per lane, UNR16 in flight
+        constexpr int UNR16 = 2;
         const unsigned short* p16 = static_cast<const unsigned short*>(plane);
-        for (int idx0 = warp * 4; idx0 < nwords; idx0 += nw * 4) {
-          const int idx = idx0 + (lane >> 3);
-          const int i = i_lo + idx / bw, j = idx - (idx / bw) * bw, wg = c.w0 - 1 + j;
-          const int y = c.r0 - c.halo + i;
-          const bool in = idx < nwords && y >= 0 && y < c.H && wg >= 0 && wg < c.Wp;
-          uint2 q = make_uint2(0u, 0u);
-          if (in) q = __ldg(reinterpret_cast<const uint2*>(p16 + (size_t)y * c.pitch + 32 * wg + 4 * sub));
-          const float v0 = (float)(q.x & 0xFFFFu), v1 = (float)(q.x >> 16);
-          const float v2 = (float)(q.y & 0xFFFFu), v3 = (float)(q.y >> 16);
-          const uint32_t nib = lt ? ((v0 < t) | ((v1 < t) << 1) | ((v2 < t) << 2) | ((v3 < t) << 3))
-                                  : ((v0 > t) | ((v1 > t) << 1) | ((v2 > t) << 2) | ((v3 > t) << 3));
-          uint32_t word = nib << (4 * sub);
-          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
-          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
-          word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
-          if (sub == 0 && idx < nwords) d[i * bw + j] = in ? (word & vmask(wg, c.W)) : 0u;
+        for (int base = warp * 4 * UNR16; base < nwords; base += nw * 4 * UNR16) {
+          uint2 q[UNR16];
+#pragma unroll
+          for (int u = 0; u < UNR16; ++u) {
+            const int idx = base + 4 * u + (lane >> 3);
+            const int i = i_lo + idx / bw, wg = c.w0 - 1 + (idx - (idx / bw) * bw);
+            const int y = c.r0 - c.halo + i;
+            const bool in = idx < nwords && y >= 0 && y < c.H && wg >= 0 && wg < c.Wp;
+            q[u] = in ? __ldg(reinterpret_cast<const uint2*>(p16 + (size_t)y * c.pitch + 32 * wg + 4 * sub))
+                      : make_uint2(0u, 0u);
+          }
+#pragma unroll
+          for (int u = 0; u < UNR16; ++u) {
+            const int idx = base + 4 * u + (lane >> 3);
+            const int i = i_lo + idx / bw, j = idx - (idx / bw) * bw, wg = c.w0 - 1 + j;
+            const int y = c.r0 - c.halo + i;
+            const bool in = idx < nwords && y >= 0 && y < c.H && wg >= 0 && wg < c.Wp;
+            const float v0 = (float)(q[u].x & 0xFFFFu), v1 = (float)(q[u].x >> 16);
+            const float v2 = (float)(q[u].y & 0xFFFFu), v3 = (float)(q[u].y >> 16);
+            const uint32_t nib = lt ? ((v0 < t) | ((v1 < t) << 1) | ((v2 < t) << 2) | ((v3 < t) << 3))
+                                    : ((v0 > t) | ((v1 > t) << 1) | ((v2 > t) << 2) | ((v3 > t) << 3));
+            uint32_t word = nib << (4 * sub);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+            if (sub == 0 && idx < nwords) d[i * bw + j] = in ? (word & vmask(wg, c.W)) : 0u;
+          }
         }
       } else
       for (int base = warp * 4 * UNR; base < nwords; base += nw * 4 * UNR) {

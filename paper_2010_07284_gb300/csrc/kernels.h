@@ -65,6 +65,15 @@ cudaError_t launch_pack_u8(const uint8_t* src, MaskGeom g, uint32_t* out, cudaSt
 cudaError_t launch_unpack_u8(const uint32_t* src, MaskGeom g, uint8_t* out, cudaStream_t st);
 cudaError_t launch_clear_padding(uint32_t* m, MaskGeom g, cudaStream_t st);
 
+// ---- the paper's pointer-jumping labelling (comparison only) ----
+// Runs rounds of `period` main iterations + reconnect + termination check
+// until converged or `max_rounds`; synchronises `st` once per round.
+// labels / scratch: H*W int32 each; flag_dev: one int32; flag_host: host.
+cudaError_t ccl_pointer_jumping(const uint32_t* mask, MaskGeom g, int conn, int period,
+                                int max_rounds, int32_t* labels, int32_t* scratch,
+                                int32_t* flag_dev, int32_t* flag_host, cudaStream_t st,
+                                int* iterations, bool* converged);
+
 // ---- persistent executor ----
 struct ExecLaunch {
   const DevJob* jobs;

@@ -15,6 +15,7 @@ import pytest
 
 import brute
 import golden_io
+from exact_f32 import round_f32
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "oracle", "vl_oracle.c")
@@ -31,6 +32,12 @@ MUTANTS = {
     "percentile_off_by_one": ("int64_t k = (int64_t)(q * (double)(n - 1));",
                               "int64_t k = (int64_t)(q * (double)(n - 1) + 0.5);"),
     "ccl_labels_by_last_pixel": ("labels[u] = (int32_t)s;", "labels[u] = (int32_t)u;"),
+    "sub_operands_swapped": ("case VLO_ARITH_SUB: r = x - y;", "case VLO_ARITH_SUB: r = y - x;"),
+    "div_is_mul": ("default: r = x / y;", "default: r = x * y;"),
+    "constant_operand_dropped": ("float x = a[i], y = b ? b[i] : c, r;", "float x = a[i], y = b ? b[i] : 0.0f, r;"),
+    "add_rounds_to_half": ("case VLO_ARITH_ADD: r = x + y;",
+                           "case VLO_ARITH_ADD: r = (float)(_Float16)(x + y);"),
+    "nan_sorts_first": ("if (nx || ny) return nx - ny;", "if (nx || ny) return ny - nx;"),
 }
 
 
@@ -51,6 +58,7 @@ def _build(tmp, name, old, new):
     lib.vlo_ccl.restype = C.c_int64
     lib.vlo_percentile.argtypes = [P, C.c_int64, C.c_double]
     lib.vlo_percentile.restype = C.c_float
+    lib.vlo_arith.argtypes = [C.c_int, P, P, C.c_float, C.c_int64, P]
     return lib
 
 
@@ -107,6 +115,29 @@ def _pins_pass(lib) -> bool:
     o = np.empty(3, np.uint8)
     lib.vlo_threshold(ch.ctypes.data, 3, C.c_float(0.5), 1, o.ctypes.data)
     if list(o) != [0, 0, 1]:
+        return False
+    # number terms: exact rational results rounded to binary32, for both an
+    # array and a constant second operand
+    from fractions import Fraction
+    xs = (rng.standard_normal(200) * 1e3).astype(np.float32)
+    ys = (rng.standard_normal(200) * 1e-2).astype(np.float32)
+    ops = {0: lambda a, b: a + b, 1: lambda a, b: a - b, 2: lambda a, b: a * b,
+           3: lambda a, b: a / b}
+    for op, fn in ops.items():
+        for second in (ys, np.float32(0.3)):
+            out = np.empty_like(xs)
+            if np.isscalar(second):
+                lib.vlo_arith(op, xs.ctypes.data, None, C.c_float(second), xs.size, out.ctypes.data)
+                bs = [float(second)] * xs.size
+            else:
+                lib.vlo_arith(op, xs.ctypes.data, second.ctypes.data, 0.0, xs.size, out.ctypes.data)
+                bs = second.tolist()
+            want = [round_f32(fn(Fraction(a), Fraction(b))) for a, b in zip(xs.tolist(), bs)]
+            if out.tolist() != want:
+                return False
+    # NaN sorts after every number in a percentile: -1, 0.5, 2, NaN, NaN
+    v = np.array([np.nan, 2.0, -1.0, np.nan, 0.5], np.float32)
+    if lib.vlo_percentile(v.ctypes.data, v.size, 0.5) != 2.0:
         return False
     return True
 
