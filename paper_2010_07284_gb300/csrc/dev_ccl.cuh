@@ -158,6 +158,18 @@ VL_DEV void g_union(int32_t* G, int a, int b, int cap, int32_t* status) {
 // inside one run of A' | B' (cut the same way for 4-adjacency) is connected,
 // so each row run starting inside it is united with the run's anchor.
 
+// The lowest bit of x in every segment of a 32-bit word, segments starting
+// at bit 0 and at every set bit of s: clear the bits of x that have another
+// bit of x below them in the same segment.  "Has an x bit below in its
+// segment" is the carry into that position of P + x, P = ~s | x: a carry
+// starts at every x bit, runs on through positions not in s, and dies at
+// a bit of s that is not in x.
+VL_DEV uint32_t first_in_segments(uint32_t x, uint32_t s) {
+  const uint32_t p = ~s | x;
+  const uint32_t carry_in = (p + x) ^ p ^ x;
+  return x & ~(carry_in & ~s);
+}
+
 // Strip-run starts of a two-row strip (a, b) given the previous word's
 // (a, b) (0 at the tile's left edge).
 VL_DEV uint32_t strip_starts(uint32_t a, uint32_t b, uint32_t al, uint32_t bl, int conn) {
@@ -346,27 +358,14 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
       bb = s.base[b] + s.pre[b][w] - 1;
       bc = s.base[b + 1] + s.pre[b + 1][w] - 1;
       carry = s.qc[b][w];
-      // one event per (boundary run, strip run): drop a row-run start when
-      // neither a boundary-run start nor a strip-run start separates it
-      // from the previous one
+      // one event per (boundary run, strip run): keep a row-run start only
+      // when a boundary-run or strip-run start separates it from the
+      // previous one, i.e. the first row-run start of every segment that
+      // begins at such a start (or at the word's left edge)
       const uint32_t ra_ = A & ~((A << 1) | (Al >> 31));
       const uint32_t rb_ = B & ~((B << 1) | (Bl >> 31));
-      uint32_t t = ra_;
-      int q = -1;
-      while (t) {
-        const int p = __ffs(t) - 1;
-        t &= t - 1;
-        if (q < 0 || ((qs | stb) & le_mask(p) & ~le_mask(q))) evA |= 1u << p;
-        q = p;
-      }
-      t = rb_;
-      q = -1;
-      while (t) {
-        const int p = __ffs(t) - 1;
-        t &= t - 1;
-        if (q < 0 || ((qs | stc) & le_mask(p) & ~le_mask(q))) evB |= 1u << p;
-        q = p;
-      }
+      evA = first_in_segments(ra_, qs | stb);
+      evB = first_in_segments(rb_, qs | stc);
     }
     const int nA = __popc(evA), nE = nA + __popc(evB);
     int j = sub;       // next event of this thread
