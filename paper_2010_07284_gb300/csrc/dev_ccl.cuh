@@ -329,10 +329,10 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
   // belongs to level = trailing ones of b), so each level unites disjoint
   // groups of strips.  Every thread takes a share of the row-run starts
   // ("events") of one boundary word; the word's strip data sits in
-  // registers.  In each round the lanes of a warp whose roots form the same
-  // pair elect one leader to link them; a link that fails because its root
-  // was linked elsewhere leaves the follow-up union (old parent, lo) on the
-  // leader.
+  // registers.  In each round every thread with an event links its pair of
+  // roots (atomicMin of the larger root's parent); a link that finds the
+  // larger root already linked elsewhere leaves the follow-up union (old
+  // parent, lo) to the same thread.
   const int cap = nruns + 64;
   bool ok = true;
   for (int level = 0; (1 << level) < ns; ++level) {
@@ -368,18 +368,34 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
       evB = first_in_segments(rb_, qs | stc);
     }
     const int nA = __popc(evA), nE = nA + __popc(evB);
-    int j = sub;       // next event of this thread
+    // this thread's events: a contiguous share [j, e1) of the pair's list
+    // (the A events, then the B events), walked by clearing lowest bits
+    const int per = (nE + T - 1) / T;
+    int j = min(nE, sub * per);
+    const int e1 = min(nE, j + per);
+    uint32_t curA = 0, curB = 0;
+    if (j < e1) {
+      if (j < nA) {
+        curA = j ? evA & ~((1u << __fns(evA, 0, j + 1)) - 1u) : evA;
+        curB = evB;
+      } else {
+        curB = j > nA ? evB & ~((1u << __fns(evB, 0, j - nA + 1)) - 1u) : evB;
+      }
+    }
     int pu = -1, pv = -1;
     for (int round = 0; round < 4 * CCL_MAXRUNS; ++round) {
-      const bool has = act && (pu >= 0 || j < nE);
+      const bool has = act && (pu >= 0 || j < e1);
       if (!__any_sync(FULL, has)) break;
       int ra = 0, rb = 0;
       const bool from_event = has && pu < 0;
       if (has) {
         int u = pu, v = pv;
         if (from_event) {
-          const bool isA = j < nA;
-          const int p = (int)__fns(isA ? evA : evB, 0, (isA ? j : j - nA) + 1);
+          const bool isA = curA != 0;
+          const uint32_t cur = isA ? curA : curB;
+          const int p = __ffs(cur) - 1;
+          if (isA) curA &= curA - 1u;
+          else curB &= curB - 1u;
           u = isA ? bb + __popc(stb & le_mask(p)) : bc + __popc(stc & le_mask(p));
           const uint32_t qq = qs & le_mask(p);
           if (qq) {
@@ -393,18 +409,16 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
         rb = s_find(s.parent, v, cap);
         if (ra < 0 || rb < 0) { ok = false; ra = rb = 0; }
       }
+      // link the larger root under the smaller; when hi was no longer a
+      // root its old parent (unless already lo) still has to meet lo
       const bool need = has && ra != rb;
       const int hi = max(ra, rb), lo = min(ra, rb);
-      const unsigned long long key =
-          need ? (((unsigned long long)(unsigned)hi << 32) | (unsigned)lo) : ~0ull;
-      const unsigned peers = __match_any_sync(FULL, key);
-      const int leader = __ffs(peers) - 1;
       int old = hi;
-      if (need && lane == leader) old = atomicMin(&s.parent[hi], lo);
+      if (need) old = atomicMin(&s.parent[hi], lo);
       if (has) {
-        if (from_event) j += T;
+        if (from_event) ++j;
         else pu = pv = -1;
-        if (need && lane == leader && old != hi) { pu = old; pv = lo; }
+        if (need && old != hi && old != lo) { pu = old; pv = lo; }
       }
     }
     __syncthreads();
