@@ -451,7 +451,8 @@ VL_API vl_status vl_result_sync(vl_result* res);
 /* Wait, then the raw device status word: 0, VL_ERR_TIMEOUT, or VL_ERR_INTERNAL
  * in the low byte with the failed check in bits 8.. (1 global find bound,
  * 2 global union bound, 3 flagged-root list overflow, 4 saved tile state out
- * of range, 5 tile strip-run capacity, 6 shared union-find bound). */
+ * of range, 5 tile strip-run capacity, 6 shared union-find bound, 7 global
+ * union-find entry outside the image). */
 VL_API vl_status vl_result_status_word(vl_result* res, int32_t* word);
 
 /* Shape of a result (any pointer may be NULL); words_per_row = Wp. */

@@ -65,8 +65,12 @@ VL_DEV int warp_incl_scan(int v, int lane) {
 
 // ---------------------------------------------------------- shared u-f --
 
+// cap = strip runs + 64: an index outside the runs, or a walk longer than
+// cap, returns -1 (the caller reports RS_SUNION) instead of reading past
+// the array.
 VL_DEV int s_find(int32_t* par, int x, int cap) {
   volatile int32_t* p = par;
+  if ((unsigned)x >= (unsigned)(cap - 64)) return -1;
   for (int it = 0; it < cap; ++it) {
     int q = p[x];
     if (q == x) return x;
@@ -102,12 +106,24 @@ VL_DEV bool s_union(int32_t* par, int a, int b, int cap) {
 // lie on x's single chain of ancestors, the root above them (ids decrease
 // along the chain).  The final relabelling pass must not compress: there,
 // entries of finished tiles already hold their final labels.
-VL_DEV int g_find(int32_t* G, int x, int cap, int32_t* status, bool compress = true) {
+// npx: pixels of the image (G's length).  An entry outside [0, npx) can
+// only come from corrupted state; it is reported (reason RS_GRANGE) and the
+// walk stops at the last valid node instead of reading out of bounds.
+VL_DEV int g_find(int32_t* G, int x, int npx, int32_t* status, bool compress = true) {
+  const int cap = min(npx + 64, 1 << 22);
+  if ((unsigned)x >= (unsigned)npx) {
+    set_status(status, ST_INTERNAL | RS_GRANGE);
+    return 0;
+  }
   int root = x;
   int it = 0;
   for (; it < cap; ++it) {
     const int p = ldcg(&G[root]);
     if (p == root) break;
+    if ((unsigned)p >= (unsigned)npx) {
+      set_status(status, ST_INTERNAL | RS_GRANGE);
+      return root;
+    }
     root = p;
   }
   if (it == cap) {
@@ -132,10 +148,11 @@ VL_DEV int g_find(int32_t* G, int x, int cap, int32_t* status, bool compress = t
 // following that fresh link could then carry a node of the other set into
 // this one and strand the rest of that set.)  A failed swap retries from
 // fresh roots.
-VL_DEV void g_union(int32_t* G, int a, int b, int cap, int32_t* status) {
+VL_DEV void g_union(int32_t* G, int a, int b, int npx, int32_t* status) {
+  const int cap = min(npx + 64, 1 << 22);
   for (int it = 0; it < cap; ++it) {
-    a = g_find(G, a, cap, status);
-    b = g_find(G, b, cap, status);
+    a = g_find(G, a, npx, status);
+    b = g_find(G, b, npx, status);
     if (a == b) return;
     if (a < b) { int t = a; a = b; b = t; }
     if (atomicCAS(&G[a], a, b) == a) return;
@@ -425,11 +442,25 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
     // (no flatten between levels: path halving in s_find keeps the next
     // level's walks short, and a full pass over all runs costs more)
   }
-  // 4. flatten
-  for (int i = tid; i < nruns; i += blockDim.x) {
-    int root = s_find(s.parent, i, cap);
-    if (root < 0) { ok = false; root = i; }
-    s.parent[i] = root;
+  // 4. flatten: every thread points its own runs at their roots with finds
+  // that only read.  (A path-halving find writes grandparents into the
+  // entries it passes; landing after another thread's final write to one of
+  // them, such a write would leave that run one hop short of its root.)
+  // Other threads' writes only move entries closer to the roots, so a
+  // read-only walk still ends at the root.
+  {
+    volatile int32_t* vp = s.parent;
+    for (int i = tid; i < nruns; i += blockDim.x) {
+      int x = i, it = 0;
+      for (; it < cap; ++it) {
+        const int q = vp[x];
+        if (q == x) break;
+        if ((unsigned)q >= (unsigned)nruns) { it = cap; break; }
+        x = q;
+      }
+      if (it == cap) { ok = false; x = i; }
+      vp[i] = x;
+    }
   }
   if (!ok) set_status(status, ST_INTERNAL | RS_SUNION);
   __syncthreads();
@@ -562,7 +593,7 @@ constexpr int ENC_SELECT = 2;   // flag bit2 = component selected (rho)
 // barrier at the end.
 VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, bool min_pixel, int32_t* G,
                              uint8_t* F, int32_t* flist, int32_t* fcount, int flist_cap,
-                             int cap, int32_t* status) {
+                             int npx, int32_t* status) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int ns = (g.th + 1) >> 1;
@@ -591,10 +622,10 @@ VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, bool min_pi
           }
         }
       } else if (mode == ENC_LABEL) {
-        if (fl & 2) v = g_find(G, v, cap, status, false);
+        if (fl & 2) v = g_find(G, v, npx, status, false);
       } else {
         uint8_t sel = fl & 1;
-        if (fl & 2) sel = ldcg(&F[g_find(G, v, cap, status, false)]);
+        if (fl & 2) sel = ldcg(&F[g_find(G, v, npx, status, false)]);
         if (sel) s.flag[S] = fl | 4;
       }
       s.parent[S] = -(v + 2);
@@ -706,7 +737,7 @@ VL_DEV int window_hit(uint32_t l, uint32_t c, uint32_t r, int b, int conn) {
 // representative in G, so a plain read gives a key without a find); equal
 // key pairs in the warp are united once, by the lowest lane holding them.
 // Must be called by the whole warp.
-VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int cap, int32_t* status) {
+VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int npx, int32_t* status) {
   int ka = 0, kb = 0;
   if (valid) {
     ka = ldcg(&G[a]);
@@ -716,7 +747,7 @@ VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int cap, int32_t* s
   const unsigned long long key =
       valid ? (((unsigned long long)(unsigned)max(ka, kb) << 32) | (unsigned)min(ka, kb)) : ~0ull;
   const unsigned peers = __match_any_sync(FULL, key);
-  if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) g_union(G, ka, kb, cap, status);
+  if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) g_union(G, ka, kb, npx, status);
 }
 
 // Unite the components that touch across the tile border of merge unit
@@ -727,7 +758,7 @@ VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int cap, int32_t* s
 // it, or, for 8-adjacency when that one is clear, with its diagonal
 // neighbours.  Must be called by the whole warp.
 VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y, int unit,
-                           int conn, int32_t* G, int cap, int32_t* status) {
+                           int conn, int32_t* G, int npx, int32_t* status) {
   const int lane = threadIdx.x & 31;
   const int nh = (tiles_y - 1) * Wp;
   if (unit < nh) {
@@ -745,9 +776,9 @@ VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y,
     const uint32_t su = mu & ~((mu << 1) | (mul >> 31));
     const int x = 32 * w + lane;
     int dx = (sd >> lane) & 1u ? window_hit(mul, mu, mur, lane, conn) : 2;
-    warp_unite(G, dx != 2, yd * W + x, yu * W + x + dx, cap, status);
+    warp_unite(G, dx != 2, yd * W + x, yu * W + x + dx, npx, status);
     dx = (su >> lane) & 1u ? window_hit(mdl, md, mdr, lane, conn) : 2;
-    warp_unite(G, dx != 2, yu * W + x, yd * W + x + dx, cap, status);
+    warp_unite(G, dx != 2, yu * W + x, yd * W + x + dx, npx, status);
   } else {
     const int nv = (H + 31) >> 5;
     const int j = unit - nh;
@@ -769,8 +800,8 @@ VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y,
     // (lane-dependent choices go into the arguments: every lane calls)
     const int a = y * W + x0 - 1;
     const bool straight = R || conn == 4;
-    warp_unite(G, L && (straight ? R : Ru), a, (straight ? y : y - 1) * W + x0, cap, status);
-    warp_unite(G, L && !straight && Rd, a, (y + 1) * W + x0, cap, status);
+    warp_unite(G, L && (straight ? R : Ru), a, (straight ? y : y - 1) * W + x0, npx, status);
+    warp_unite(G, L && !straight && Rd, a, (y + 1) * W + x0, npx, status);
   }
 }
 

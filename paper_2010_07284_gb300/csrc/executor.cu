@@ -112,7 +112,7 @@ VL_DEV void arith_rows(const DevJob& J, int sub, unsigned char* smem) {
 
 VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
                         unsigned char* smem, const ExecLaunch& L) {
-  const int cap = min(J.H * J.W + 64, 1 << 22);
+  const int npx = J.H * J.W;
   switch (S.kind) {
     case SK_PCT: {
       SelectSmem& s = *reinterpret_cast<SelectSmem*>(smem);
@@ -173,12 +173,12 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       if (S.kind == SK_RZ_LOCAL) {
         if (!ccl_tile_label(s, phi2, phi1, geo, J.conn, false, J.status)) break;
         ccl_encode_roots(s, geo, ENC_PUBLISH, false, rz_G(J, k), rz_F(J, k), rz_flist(J, k),
-                         J.fcount + S.rz_off + j, J.flist_cap, cap, J.status);
+                         J.fcount + S.rz_off + j, J.flist_cap, npx, J.status);
         ccl_publish_border(s, geo, rz_G(J, k));
         ccl_tile_save(s, tpar, tflag);
       } else {
         if (!ccl_tile_load(s, phi2, geo, J.conn, tpar, tflag, J.status)) break;
-        ccl_encode_roots(s, geo, ENC_SELECT, true, rz_G(J, k), rz_F(J, k), nullptr, nullptr, 0, cap,
+        ccl_encode_roots(s, geo, ENC_SELECT, true, rz_G(J, k), rz_F(J, k), nullptr, nullptr, 0, npx,
                          J.status);
         ccl_write_select(s, geo, J.slots[r.z_slot]);
       }
@@ -191,7 +191,7 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       const int nw = blockDim.x >> 5;
       for (int u = chunk * nw + (threadIdx.x >> 5); u < n; u += per_rz * nw)
         ccl_merge_unit(J.slots[r.phi2_slot], J.H, J.W, J.Wp, J.c_tiles_y, u, J.conn,
-                       rz_G(J, r.scratch), cap, J.status);
+                       rz_G(J, r.scratch), npx, J.status);
       break;
     }
     case SK_RZ_FLAGS: {
@@ -202,7 +202,7 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       uint8_t* F = rz_F(J, r.scratch);
       const int32_t* fl = rz_flist(J, r.scratch);
       for (int i = chunk * blockDim.x + threadIdx.x; i < n; i += per_rz * blockDim.x)
-        F[g_find(G, ldcg(fl + i), cap, J.status)] = 1;
+        F[g_find(G, ldcg(fl + i), npx, J.status)] = 1;
       break;
     }
     default:

@@ -137,11 +137,11 @@ k_ccl_local(const uint32_t* mask, const uint32_t* phi1, MaskGeom g, int tiles_x,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
   const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
-  const int cap = min(g.H * g.W + 64, 1 << 22);
+  const int npx = g.H * g.W;
   const bool labels = sc.F == nullptr;  // full labelling: canonical minimum pixel
   if (!ccl_tile_label(s, mask, phi1, geo, conn, labels, status)) return;
   ccl_encode_roots(s, geo, ENC_PUBLISH, labels, sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap,
-                   cap, status);
+                   npx, status);
   ccl_publish_border(s, geo, sc.G);
   ccl_tile_save(s, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
                 sc.tflag + (size_t)blockIdx.x * sc.tile_cap);
@@ -150,17 +150,17 @@ k_ccl_local(const uint32_t* mask, const uint32_t* phi1, MaskGeom g, int tiles_x,
 __global__ void k_ccl_merge(const uint32_t* mask, MaskGeom g, int tiles_y, int tiles_x,
                             int conn, int32_t* G, int32_t* status) {
   const int n = merge_units(g.H, g.Wp, tiles_y, tiles_x);
-  const int cap = min(g.H * g.W + 64, 1 << 22);
+  const int npx = g.H * g.W;
   const int wpb = blockDim.x >> 5;
   for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n; u += gridDim.x * wpb)
-    ccl_merge_unit(mask, g.H, g.W, g.Wp, tiles_y, u, conn, G, cap, status);
+    ccl_merge_unit(mask, g.H, g.W, g.Wp, tiles_y, u, conn, G, npx, status);
 }
 
 __global__ void k_ccl_flags(int32_t* G, uint8_t* F, const int32_t* flist,
-                            const int32_t* fcount, int flist_cap, int cap, int32_t* status) {
+                            const int32_t* fcount, int flist_cap, int npx, int32_t* status) {
   const int n = min(*fcount, flist_cap);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    F[g_find(G, flist[i], cap, status)] = 1;
+    F[g_find(G, flist[i], npx, status)] = 1;
 }
 
 __global__ void __launch_bounds__(EXEC_THREADS, 2)
@@ -169,11 +169,11 @@ k_ccl_final_labels(const uint32_t* mask, MaskGeom g, int tiles_x, int conn, CclS
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
   const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
-  const int cap = min(g.H * g.W + 64, 1 << 22);
+  const int npx = g.H * g.W;
   if (!ccl_tile_load(s, mask, geo, conn, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
                      sc.tflag + (size_t)blockIdx.x * sc.tile_cap, status))
     return;
-  ccl_encode_roots(s, geo, ENC_LABEL, true, sc.G, nullptr, nullptr, nullptr, 0, cap, status);
+  ccl_encode_roots(s, geo, ENC_LABEL, true, sc.G, nullptr, nullptr, nullptr, 0, npx, status);
   ccl_write_labels(s, geo, sc.G);
 }
 
@@ -183,11 +183,11 @@ k_rz_final(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int tiles_x, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
   const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
-  const int cap = min(g.H * g.W + 64, 1 << 22);
+  const int npx = g.H * g.W;
   if (!ccl_tile_load(s, phi2, geo, conn, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
                      sc.tflag + (size_t)blockIdx.x * sc.tile_cap, status))
     return;
-  ccl_encode_roots(s, geo, ENC_SELECT, true, sc.G, sc.F, nullptr, nullptr, 0, cap, status);
+  ccl_encode_roots(s, geo, ENC_SELECT, true, sc.G, sc.F, nullptr, nullptr, 0, npx, status);
   ccl_write_select(s, geo, Z);
 }
 
@@ -342,7 +342,7 @@ cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, in
   if (e) return e;
   const int ty = ccl_tiles_y(g.H), tx = ccl_tiles_x(g.Wp);
   const size_t sm = sizeof(CclSmem);
-  const int cap = min(g.H * g.W + 64, 1 << 22);
+  const int npx = g.H * g.W;
   if ((e = cudaMemsetAsync(sc.fcount, 0, sizeof(int32_t), st))) return e;
   k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(phi2, phi1, g, tx, conn, sc, status);
   if ((e = cudaGetLastError())) return e;
@@ -353,7 +353,7 @@ cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, in
     if ((e = cudaGetLastError())) return e;
   }
   k_ccl_flags<<<grid_for(sc.flist_cap, kThreads), kThreads, 0, st>>>(
-      sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap, cap, status);
+      sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap, npx, status);
   if ((e = cudaGetLastError())) return e;
   k_rz_final<<<ty * tx, EXEC_THREADS, sm, st>>>(phi1, phi2, g, tx, conn, sc, Z, status);
   return cudaGetLastError();

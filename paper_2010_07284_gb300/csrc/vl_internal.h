@@ -38,6 +38,7 @@ constexpr int RS_FLIST = 3 << 8;     // flagged-root list overflow
 constexpr int RS_TLOAD = 4 << 8;     // saved tile state out of range
 constexpr int RS_TRUNS = 5 << 8;     // more strip runs than a tile holds
 constexpr int RS_SUNION = 6 << 8;    // shared union-find ran past its bound
+constexpr int RS_GRANGE = 7 << 8;    // global union-find entry outside the image
 
 // --------------------------------------------------------- group bytecode
 // One instruction of a fused tile group.  Buffers are shared-memory tiles
