@@ -128,3 +128,22 @@ def test_grow_spec_7680_both_forms():
         res = ctx.eval(F, [ctx.image(img)])
         assert res.sync() == 0, ctx.last_error()
         assert_same([res.mask(0)], [exp], f"grow 7680 {mode}")
+
+
+def test_ccl_8192_repeated_labellings_agree():
+    """Twelve labellings of one 8192 x 8192 mask at 4-adjacency near its
+    percolation threshold: every status is clean and every labelling equals
+    the oracle's (a race in the tile flatten once left, in about one run in
+    twenty, a run one hop short of its root and a bad index in the global
+    union-find)."""
+    torch = torch_cuda()
+    m = wl.bernoulli_mask(S, S, 0.60, seed=4)
+    exp = torch.from_numpy(oracle.ccl(m, 4)[0].ravel()).cuda()
+    ctx = context()
+    mimg = ctx.mask(m)
+    lab = torch.empty(S * S, dtype=torch.int32, device="cuda")
+    for rep in range(12):
+        lab.fill_(-7)
+        ctx.ccl(mimg, lab, 4)
+        assert ctx.ccl_status() == 0, f"rep {rep}: {ctx.last_error()}"
+        assert torch.equal(lab, exp), f"rep {rep}: labels differ"
