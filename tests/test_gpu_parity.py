@@ -231,3 +231,21 @@ def test_config2_full_size_repeated_replays():
         assert plain.sync() == 0
         for r in range(0, len(f.roots), 50):
             assert np.array_equal(plain.mask(r, s), exp[r])
+
+
+@pytest.mark.parametrize("shape", [(65535, 40), (40, 65535)])
+def test_longest_sides(shape):
+    """Sides at the 65535 limit: labelling tiles, group tiles and the last
+    padded word of a row all at their edges; a formula with N, rho, grow and
+    a uint16 threshold, and a full labelling."""
+    torch = torch_cuda()
+    img = wl.uniform_image_u16(*shape, seed=3)
+    nodes = [_f("THR_GT", t=60000.0), _f("THR_LT", t=20000.0), _f("NEAR", 0), _f("REACH", 0, 1),
+             _f("GROW", 1, 0), _f("AND", 3, 4), _f("NOT", 5)]
+    check_formula(nodes, [2, 3, 4, 6], [img], conn=8)
+    m = wl.bernoulli_mask(*shape, 0.55, seed=4)
+    ctx = context()
+    lab = torch.empty(m.size, dtype=torch.int32, device="cuda")
+    ctx.ccl(ctx.mask(m), lab, 4)
+    assert ctx.ccl_status() == 0
+    np.testing.assert_array_equal(lab.cpu().numpy().reshape(shape), oracle.ccl(m, 4)[0])

@@ -95,3 +95,33 @@ def test_cancel_reject_and_tight_budget():
     assert stats["cancelled"] == len(cancelled)
     assert stats["completed"] == len(qs) - len(cancelled)
     srv.close()
+
+
+def test_serving_mixes_number_terms_and_uint16_images():
+    """Queries with number terms on float and uint16 images served in one
+    mix equal the oracle's masks."""
+    torch_cuda()
+    import oracle
+    import paper_2010_07284_gb300 as vg
+    ctx = context()
+    imgs = []
+    for k in range(4):
+        im = np.stack([wl.gaussian_field_image(150 + 40 * k, 300 + 70 * k, seed=k)[0],
+                       wl.uniform_image(150 + 40 * k, 300 + 70 * k, seed=k)[0]])
+        imgs.append(wl.to_u16(np.clip(im, 0.0, 1.0)) if k % 2 else im)
+    handles = [ctx.image(im) for im in imgs]
+    srv = vg.Server(ctx, max_inflight_batches=2, max_batch_jobs=4, batch_window_us=100)
+    jobs = []
+    for k in range(12):
+        f = wl.arith_dag(50, seed=40 + k)
+        rec = wl.formula_to_records(f)
+        F = ctx.compile(rec, f.roots, 8)
+        j = k % len(imgs)
+        jobs.append((rec, f.roots, j, srv.submit(F, [handles[j]])))
+    for rec, roots, j, t in jobs:
+        st, res = srv.wait(t, timeout_us=60_000_000)
+        assert st == 0, f"ticket {t}: status {st}"
+        exp = oracle.evaluate(rec, roots, [imgs[j]], conn=8).masks
+        for r, e in enumerate(exp):
+            assert np.array_equal(res.mask(r), e), f"ticket {t} root {r}"
+    srv.close()
