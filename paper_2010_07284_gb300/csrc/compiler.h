@@ -33,7 +33,7 @@ struct PlanParams {
   // a mask slot is reused only by a value defined at least this many steps
   // after the last read of its previous value: reuse adds write-after-read
   // dependencies, which a distant reader keeps off the critical path
-  int reuse_distance = 16;
+  int reuse_distance = 32;
 };
 
 struct Plan {
@@ -81,7 +81,7 @@ struct Plan {
   int64_t n_thr = 0, n_not = 0, n_and = 0, n_near = 0, n_num = 0, n_other = 0;
 };
 
-constexpr int MAX_RZ_BATCH = 16;  // selects of one level run together in one step
+constexpr int MAX_RZ_BATCH = 32;  // selects of one level run together in one step
 // Rank codes: a channel gets a table when at least this many constant
 // thresholds read it; tables hold at most kRankMaxValues values (codes fit
 // 14 bits) and a formula at most kRankMaxTables tables (one bit each in a
