@@ -349,3 +349,44 @@ def test_number_terms_register_limit():
     with pytest.raises(N.VlError) as e:
         vg.compile_formula(chain(17), [len(chain(17)) - 1])
     assert e.value.code == N.ERR_FORMULA
+
+
+# ------------------------------------------------ entry points without GPU --
+
+def test_entry_points_reject_null_handles():
+    """Every entry point added for uint16 images, number terms and the
+    pointer-jumping comparison returns VL_ERR_ARG for a null handle before
+    touching the device."""
+    lib = N.load()
+    out = C.c_void_p()
+    i = C.c_int32()
+    data = (C.c_uint16 * 4)()
+    assert lib.vl_image_create_u16(None, 2, 2, 1, data, 0, None, C.byref(out)) == N.ERR_ARG
+    assert lib.vl_image_format(None, C.byref(i)) == N.ERR_ARG
+    assert lib.vl_formula_arith(None, None, C.byref(i), None, None) == N.ERR_ARG
+    assert lib.vl_ccl_pointer_jumping(None, None, 8, 16, 0, None, None, C.byref(i)) == N.ERR_ARG
+
+
+def test_number_term_plan_of_a_compiled_formula_without_context():
+    """vl_formula_arith on a host-compiled formula: program, number-image
+    count and the index of the first number image."""
+    f = wl.arith_dag(40, seed=2)
+    F = vg.compile_formula(_rec(f), f.roots)
+    p = F.plan()
+    assert p["arith"][-1]["op"] == 5                      # ends with a store
+    assert p["first_number_image"] == 1                    # one float image read
+    stores = [a for a in p["arith"] if a["op"] == 5]
+    assert sorted(a["image"] for a in stores) == list(range(p["n_number_images"]))
+    assert max(a["dst"] for a in p["arith"]) < 16
+
+
+@pytest.mark.parametrize("mix", ["mixed", "near", "reach"])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_sequential_chains_plan_matches_oracle(mix, conn):
+    """The chains of Sec. 4.1 (tapped every 20 nodes): deep N runs split at
+    the halo budget, rho after rho, in listed and random dependency orders."""
+    pytest.importorskip("scipy")
+    f = wl.sequential_dag(300, seed=7, mix=mix, taps=20)
+    img = wl.gaussian_field_image(40, 300, sigma=8.0, seed=7)
+    _check_sim(f, [img], conn=conn)
+    _check_sim(f, [img], conn=conn, shuffle=3)
