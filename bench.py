@@ -155,6 +155,37 @@ def oracle_sample(rows: int):
     return r.n_primitive * rows * W / dt / 1e9, dt, r.n_primitive
 
 
+def _oracle_warm(_):
+    import oracle
+    oracle.build()
+    return os.getpid()
+
+
+def _oracle_task(task):
+    rec, roots, img = task
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.evaluate(rec, roots, [img], conn=8)
+    return time.perf_counter() - t0, float(r.n_primitive) * img.shape[-2] * img.shape[-1]
+
+
+def oracle_all_cores(tasks) -> dict:
+    """The CPU oracle, as it stands, over (records, roots, image) tasks on
+    every host core: a spawn pool (workers start without the parent's CUDA
+    context), warmed up before the clock starts.  Wall time of all tasks,
+    summed task seconds, pixel-ops, cores."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_warm, range(cores)))
+        t0 = time.perf_counter()
+        res = list(ex.map(_oracle_task, tasks))
+        wall = time.perf_counter() - t0
+    return {"wall_s": wall, "task_s": float(sum(r[0] for r in res)),
+            "pixel_ops": float(sum(r[1] for r in res)), "cores": cores, "tasks": len(tasks)}
+
+
 def leg_grow_7680(ctx, stream, flush, runs: int = 5) -> dict:
     """The case-study spec (two thresholds and grow, Sec. 4.2) on a 7680 x
     7680 upscaled MRI-shaped slice, the scale of the paper's only published
@@ -397,6 +428,8 @@ def leg_mri_batch(ctx, stream, flush, n_images: int = 4096, reps: int = 5) -> di
         h.close()
     val = n_prim * px / (float(np.mean(ms)) / 1e3) / 1e9
     plain = n_prim * spx / plain_s / 1e9
+    # the oracle on every host core over every 16th image
+    cpu = oracle_all_cores([(rec, f.roots, imgs[k]) for k in range(0, n_images, 16)])
     return {"workload": f"{n_images} MRI-shaped images 160-512 px (median 240), 4 channels, "
                         "40-primitive formula with percentile thresholds, 8-adjacency",
             "value": val, "unit": "Gpixel-ops/s", "images_per_s": n_images / (float(np.mean(ms)) / 1e3),
@@ -404,7 +437,12 @@ def leg_mri_batch(ctx, stream, flush, n_images: int = 4096, reps: int = 5) -> di
             "tiles": {k: tune["best"][k] for k in ("tile_rows", "tile_words", "ctas_per_sm")},
             "plain_one_at_a_time": {"value": plain, "unit": "Gpixel-ops/s",
                                     "images": len(sample), "wall_s": plain_s},
-            "batched_over_plain": val / plain}
+            "batched_over_plain": val / plain,
+            "cpu_oracle_all_cores": {"kind": "oracle", "cores": cpu["cores"],
+                                     "sample": f"every 16th image ({cpu['tasks']} images)",
+                                     "images_per_s": cpu["tasks"] / cpu["wall_s"],
+                                     "value": cpu["pixel_ops"] / cpu["wall_s"] / 1e9,
+                                     "unit": "Gpixel-ops/s"}}
 
 
 def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formulas: int = 48,
@@ -472,6 +510,18 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
     plain_s = time.perf_counter() - t0
     for im in pool:
         im.close()
+    # the oracle on every host core over a seeded 1 % sample of the queries,
+    # restricted to images of at most 1024^2 (a 4096^2 query with a
+    # 2000-node formula takes the oracle minutes; the whole stream would take
+    # core-hours)
+    order = np.random.default_rng(9).permutation(n_queries)
+    pick = [int(k) for k in order if int(sides[qi[k]]) <= 1024][: max(1, n_queries // 100)]
+    tasks = []
+    for k in pick:
+        fd = wl.random_dag(int(sizes[qf[k]]), seed=1000 + int(qf[k]), max_depth=min(500, int(sizes[qf[k]])))
+        sd = int(sides[qi[k]])
+        tasks.append((wl.formula_to_records(fd), fd.roots, wl.uniform_image(sd, sd, seed=100 + int(qi[k]))))
+    cpu = oracle_all_cores(tasks)
     return {"workload": f"{n_queries} queries over {n_images} resident images (sides log-uniform "
                         f"128-4096), {n_formulas} formulas of 10-2000 nodes, 8-adjacency",
             "saturated": {"queries_per_s": rate, "value": work / wall_sat / 1e9,
@@ -481,7 +531,13 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
                         "value": work / wall_p / 1e9, "unit": "Gpixel-ops/s",
                         "p50_ms": st_p["p50_ms"], "p99_ms": st_p["p99_ms"], "batches": st_p["batches"]},
             "plain_one_at_a_time": {"queries": len(sample), "queries_per_s": len(sample) / plain_s,
-                                    "value": swork / plain_s / 1e9, "unit": "Gpixel-ops/s"}}
+                                    "value": swork / plain_s / 1e9, "unit": "Gpixel-ops/s"},
+            "cpu_oracle_all_cores": {"kind": "oracle", "cores": cpu["cores"],
+                                     "sample": f"{cpu['tasks']} queries (seeded 1 % draw, sides <= 1024)",
+                                     "cpu_s_per_query": cpu["task_s"] / max(1, cpu["tasks"]),
+                                     "queries_per_s": cpu["tasks"] / cpu["wall_s"],
+                                     "value": cpu["pixel_ops"] / cpu["wall_s"] / 1e9,
+                                     "unit": "Gpixel-ops/s"}}
 
 
 def run_reference(args, rank: int, world: int) -> None:
