@@ -68,6 +68,11 @@ def _lib() -> C.CDLL:
         lib.vlo_ccl.argtypes = [P, C.c_int, C.c_int, C.c_int, P]
         lib.vlo_ccl.restype = C.c_int64
         lib.vlo_arith.argtypes = [C.c_int, P, P, C.c_float, C.c_int64, P]
+        lib.vlo_near3.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P]
+        lib.vlo_reach3.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P]
+        lib.vlo_reach3.restype = C.c_int
+        lib.vlo_ccl3.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P]
+        lib.vlo_ccl3.restype = C.c_int64
         lib.vlo_percentile.argtypes = [P, C.c_int64, C.c_double]
         lib.vlo_percentile.restype = C.c_float
         lib.vlo_eval.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.c_int,
@@ -203,3 +208,78 @@ def evaluate(nodes: Sequence, roots: Sequence[int],
     if rc != 0:
         raise MemoryError("oracle: out of memory")
     return OracleResult(outs, len(prim), prim, proots)
+
+
+# ------------------------------------------------------------- 3D volumes ---
+# Volumes are (D, H, W) arrays (masks) or (C, D, H, W) arrays (number
+# images); adjacency 26 (3x3x3 cube) or 6 (faces).  The derived connectives,
+# thresholds, percentiles and number terms are those of the 2D evaluator,
+# applied voxel by voxel; only N and rho see the third axis.
+
+def near3(a, conn: int = 26) -> np.ndarray:
+    a = _mask(a)
+    out = np.empty_like(a)
+    _lib().vlo_near3(_ptr(a), a.shape[0], a.shape[1], a.shape[2], conn, _ptr(out))
+    return out
+
+
+def reach3(phi1, phi2, conn: int = 26) -> np.ndarray:
+    a, b = _mask(phi1), _mask(phi2)
+    out = np.empty_like(a)
+    if _lib().vlo_reach3(_ptr(a), _ptr(b), a.shape[0], a.shape[1], a.shape[2], conn,
+                         _ptr(out)) != 0:
+        raise MemoryError("oracle reach3: out of memory")
+    return out
+
+
+def ccl3(m, conn: int = 26):
+    """(labels int32 (D, H, W), number of components); label = minimum
+    linear index z*H*W + y*W + x of the component, background -1."""
+    m = _mask(m)
+    lab = np.empty(m.shape, dtype=np.int32)
+    n = _lib().vlo_ccl3(_ptr(m), m.shape[0], m.shape[1], m.shape[2], conn, _ptr(lab))
+    if n < 0:
+        raise MemoryError("oracle ccl3: out of memory")
+    return lab, int(n)
+
+
+def evaluate3(nodes: Sequence, roots: Sequence[int], volumes: Sequence[np.ndarray] = (),
+              masks: Sequence[np.ndarray] = (), conn: int = 26) -> OracleResult:
+    """Evaluate a formula on (C, D, H, W) number volumes (float32 or uint16)
+    and (D, H, W) mask volumes, node by node in the expanded DAG's order."""
+    if conn not in (6, 26):
+        raise ValueError("volume adjacency is 6 or 26")
+    prim, proots = expand(nodes, roots)
+    vols = [np.ascontiguousarray(v, dtype=np.float32) for v in volumes]
+    msks = [_mask(m) for m in masks]
+    shape = vols[0].shape[1:] if vols else msks[0].shape
+    val: List[Optional[np.ndarray]] = [None] * len(prim)
+    for i, (op, a, b, img, ch, t, q) in enumerate(prim):
+        if op == "TRUE":
+            v = np.ones(shape, np.uint8)
+        elif op == "FALSE":
+            v = np.zeros(shape, np.uint8)
+        elif op == "MASK":
+            v = msks[img]
+        elif op == "VALUE":
+            v = np.ascontiguousarray(vols[img][ch])
+        elif op in ("ADD", "SUB", "MUL", "DIV"):
+            v = arith(op, val[a], np.float32(t) if b < 0 else val[b])
+        elif op in ("THR_GT", "THR_LT", "PCT_GT", "PCT_LT"):
+            x = val[a] if a >= 0 else vols[img][ch]
+            thr = percentile(x, q) if op.startswith("PCT") else t
+            v = threshold(x, thr, gt=op.endswith("GT"))
+        elif op == "NOT":
+            v = op_not(val[a])
+        elif op == "AND":
+            v = op_and(val[a], val[b])
+        elif op == "NEAR":
+            v = near3(val[a], conn)
+        elif op == "REACH":
+            v = reach3(val[a], val[b], conn)
+        else:
+            raise ValueError(f"unknown primitive {op}")
+        val[i] = v
+    return OracleResult([np.ascontiguousarray(val[r], dtype=np.uint8) for r in proots],
+                        len(prim), prim, proots)
+

@@ -348,3 +348,107 @@ done:
   free(uses);
   return rc;
 }
+
+/* ------------------------------------------------------------ 3D volumes -- */
+
+/* Volumes of D slices of H x W voxels, voxel (z, y, x) at z*H*W + y*W + x.
+ * Adjacency 26 (the 3x3x3 cube, the 3D Moore neighbourhood) or 6 (the six
+ * face neighbours); the voxel itself counts for N (reflexive), nothing
+ * exists outside the volume.  These functions are separate from the 2D
+ * ones above, which they leave untouched. */
+static int is_offset3(int dz, int dy, int dx, int conn) {
+  if (dz < -1 || dz > 1 || dy < -1 || dy > 1 || dx < -1 || dx > 1) return 0;
+  if (conn == 6) return (dz != 0) + (dy != 0) + (dx != 0) <= 1;
+  return 1;
+}
+
+VLO_EXPORT void vlo_near3(const uint8_t* a, int D, int H, int W, int conn,
+                          uint8_t* out) {
+  for (int z = 0; z < D; ++z)
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) {
+        uint8_t v = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (!is_offset3(dz, dy, dx, conn)) continue;
+              int zz = z + dz, yy = y + dy, xx = x + dx;
+              if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+              if (a[((int64_t)zz * H + yy) * W + xx]) v = 1;
+            }
+        out[((int64_t)z * H + y) * W + x] = v;
+      }
+}
+
+/* rho phi1[phi2] in a volume, by the same BFS as vlo_reach. */
+VLO_EXPORT int vlo_reach3(const uint8_t* phi1, const uint8_t* phi2, int D, int H,
+                          int W, int conn, uint8_t* out) {
+  int64_t n = (int64_t)D * H * W, hw = (int64_t)H * W;
+  int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  uint8_t* pushed = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!queue || !pushed) { free(queue); free(pushed); return -1; }
+  int64_t head = 0, tail = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    out[i] = phi1[i] ? 1 : 0;
+    if (phi1[i]) { queue[tail++] = i; pushed[i] = 1; }
+  }
+  while (head < tail) {
+    int64_t v = queue[head++];
+    int z = (int)(v / hw), y = (int)((v % hw) / W), x = (int)(v % W);
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (dz == 0 && dy == 0 && dx == 0) continue;
+          if (!is_offset3(dz, dy, dx, conn)) continue;
+          int zz = z + dz, yy = y + dy, xx = x + dx;
+          if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+          int64_t u = ((int64_t)zz * H + yy) * W + xx;
+          out[u] = 1;                       /* u = pi_0, v = pi_1 */
+          if (phi2[u] && !pushed[u]) {      /* u may serve as an intermediate */
+            pushed[u] = 1;
+            queue[tail++] = u;
+          }
+        }
+  }
+  free(queue);
+  free(pushed);
+  return 0;
+}
+
+/* Flood fill of a volume; label = minimum linear index of the component
+ * (the first voxel met in raster order), background -1.  Returns the
+ * number of components, or -1 when memory runs out. */
+VLO_EXPORT int64_t vlo_ccl3(const uint8_t* m, int D, int H, int W, int conn,
+                            int32_t* labels) {
+  int64_t n = (int64_t)D * H * W, hw = (int64_t)H * W;
+  int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!queue) return -1;
+  for (int64_t i = 0; i < n; ++i) labels[i] = -1;
+  int64_t count = 0;
+  for (int64_t s = 0; s < n; ++s) {
+    if (!m[s] || labels[s] != -1) continue;
+    ++count;
+    int64_t head = 0, tail = 0;
+    queue[tail++] = s;
+    labels[s] = (int32_t)s;
+    while (head < tail) {
+      int64_t v = queue[head++];
+      int z = (int)(v / hw), y = (int)((v % hw) / W), x = (int)(v % W);
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dz == 0 && dy == 0 && dx == 0) continue;
+            if (!is_offset3(dz, dy, dx, conn)) continue;
+            int zz = z + dz, yy = y + dy, xx = x + dx;
+            if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+            int64_t u = ((int64_t)zz * H + yy) * W + xx;
+            if (m[u] && labels[u] == -1) {
+              labels[u] = (int32_t)s;
+              queue[tail++] = u;
+            }
+          }
+    }
+  }
+  free(queue);
+  return count;
+}

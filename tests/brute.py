@@ -245,3 +245,67 @@ def all_masks(H: int, W: int):
 
 def bits_to_mask(bits: int, H: int, W: int) -> np.ndarray:
     return np.array([(bits >> i) & 1 for i in range(H * W)], dtype=np.uint8).reshape(H, W)
+
+
+# ------------------------------------------------------------ 3D volumes ---
+
+def neighbours3(D: int, H: int, W: int, conn: int) -> List[List[int]]:
+    """Adjacency lists (voxel itself excluded) of a D x H x W volume: 26 =
+    every voxel of the 3x3x3 cube around, 6 = the voxels sharing a face."""
+    out = []
+    for z in range(D):
+        for y in range(H):
+            for x in range(W):
+                lst = []
+                for dz, dy, dx in itertools.product((-1, 0, 1), repeat=3):
+                    if (dz, dy, dx) == (0, 0, 0):
+                        continue
+                    if conn == 6 and abs(dz) + abs(dy) + abs(dx) != 1:
+                        continue
+                    zz, yy, xx = z + dz, y + dy, x + dx
+                    if 0 <= zz < D and 0 <= yy < H and 0 <= xx < W:
+                        lst.append((zz * H + yy) * W + xx)
+                out.append(lst)
+    return out
+
+
+def reach_by_paths_nb(f1: np.ndarray, f2: np.ndarray, nb: List[List[int]]) -> np.ndarray:
+    """rho phi1[phi2] on any graph given by adjacency lists, by DFS over
+    simple paths (flat 0/1 arrays)."""
+    n = len(nb)
+    f1 = f1.astype(bool)
+    f2 = f2.astype(bool)
+    out = np.zeros(n, dtype=np.uint8)
+
+    def dfs(cur: int, visited: int) -> bool:
+        for u in nb[cur]:
+            if visited >> u & 1:
+                continue
+            if f1[u]:
+                return True
+            if f2[u] and dfs(u, visited | (1 << u)):
+                return True
+        return False
+
+    for x in range(n):
+        out[x] = 1 if (f1[x] or dfs(x, 1 << x)) else 0
+    return out
+
+
+def components_nb(m: np.ndarray, nb: List[List[int]]) -> np.ndarray:
+    """Component ids by repeated relaxation to the minimum index over the
+    graph's edges until nothing changes (a fixed-point definition, no queue):
+    label = minimum index of the component, background -1."""
+    f = m.astype(bool)
+    lab = np.where(f, np.arange(len(nb)), -1)
+    changed = True
+    while changed:
+        changed = False
+        for v in range(len(nb)):
+            if not f[v]:
+                continue
+            for u in nb[v]:
+                if f[u] and lab[u] < lab[v]:
+                    lab[v] = lab[u]
+                    changed = True
+    return lab
