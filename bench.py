@@ -450,7 +450,8 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
     """Query stream: square U[0,1) images with sides log-uniform over
     [128, 4096] resident in HBM, formulas of 10-2000 nodes drawn like the
     random formula; first all queries at once (saturated throughput), then
-    Poisson arrivals at `load` x that rate (latency), then the plain form one
+    Poisson arrivals at `load` x that rate (latency; also at 0.5 and 0.95 of
+    it), then the plain form one
     query at a time on a sample."""
     import torch
     import paper_2010_07284_gb300 as vg
@@ -494,9 +495,20 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
 
     wall_sat, st_sat = run(None)
     rate = n_queries / wall_sat
-    gaps = rng.exponential(1.0 / (load * rate), size=n_queries)
-    arrivals = np.cumsum(gaps) - gaps[0]
-    wall_p, st_p = run(arrivals)
+
+    def poisson(ld):
+        gaps = rng.exponential(1.0 / (ld * rate), size=n_queries)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        wall, st = run(arrivals)
+        return wall, st
+
+    wall_p, st_p = poisson(load)
+    # the other arrival rates the workload names (0.5 and 0.95 of saturation)
+    others = []
+    for ld in (0.5, 0.95):
+        w, st = poisson(ld)
+        others.append({"load": ld, "rate_per_s": ld * rate, "queries_per_s": n_queries / w,
+                       "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "batches": st["batches"]})
     # plain form, one query at a time, on a sample
     sample = range(0, n_queries, max(1, n_queries // 100))
     swork = float(sum(prims[qf[k]] * int(sides[qi[k]]) ** 2 for k in sample))
@@ -530,6 +542,7 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
             "poisson": {"load": load, "rate_per_s": load * rate, "queries_per_s": n_queries / wall_p,
                         "value": work / wall_p / 1e9, "unit": "Gpixel-ops/s",
                         "p50_ms": st_p["p50_ms"], "p99_ms": st_p["p99_ms"], "batches": st_p["batches"]},
+            "poisson_other_loads": others,
             "plain_one_at_a_time": {"queries": len(sample), "queries_per_s": len(sample) / plain_s,
                                     "value": swork / plain_s / 1e9, "unit": "Gpixel-ops/s"},
             "cpu_oracle_all_cores": {"kind": "oracle", "cores": cpu["cores"],
