@@ -38,6 +38,13 @@ MUTANTS = {
     "add_rounds_to_half": ("case VLO_ARITH_ADD: r = x + y;",
                            "case VLO_ARITH_ADD: r = (float)(_Float16)(x + y);"),
     "nan_sorts_first": ("if (nx || ny) return nx - ny;", "if (nx || ny) return ny - nx;"),
+    "faces_as_cube_3d": ("if (conn == 6) return (dz != 0) + (dy != 0) + (dx != 0) <= 1;",
+                         "(void)conn;"),
+    "near3_skips_z": ("if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;\n              if (a[",
+                      "if (zz != z || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;\n              if (a["),
+    "reach3_ignores_phi2": ("          if (phi2[u] && !pushed[u]) {", "          if (!pushed[u]) {"),
+    "ccl3_labels_by_voxel": ("              labels[u] = (int32_t)s;\n              queue[tail++] = u;\n            }\n          }\n    }\n  }\n  free(queue);\n  return count;\n}\n",
+                             "              labels[u] = (int32_t)u;\n              queue[tail++] = u;\n            }\n          }\n    }\n  }\n  free(queue);\n  return count;\n}\n"),
 }
 
 
@@ -59,6 +66,10 @@ def _build(tmp, name, old, new):
     lib.vlo_percentile.argtypes = [P, C.c_int64, C.c_double]
     lib.vlo_percentile.restype = C.c_float
     lib.vlo_arith.argtypes = [C.c_int, P, P, C.c_float, C.c_int64, P]
+    lib.vlo_near3.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P]
+    lib.vlo_reach3.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P]
+    lib.vlo_ccl3.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P]
+    lib.vlo_ccl3.restype = C.c_int64
     return lib
 
 
@@ -134,6 +145,26 @@ def _pins_pass(lib) -> bool:
                 bs = second.tolist()
             want = [round_f32(fn(Fraction(a), Fraction(b))) for a, b in zip(xs.tolist(), bs)]
             if out.tolist() != want:
+                return False
+    # volumes: dilation by definition, reach by simple paths, labels by a
+    # fixed-point relaxation, on small random volumes
+    for conn in (6, 26):
+        nb = brute.neighbours3(2, 3, 2, conn)
+        for _ in range(12):
+            a = (rng.random((2, 3, 2)) < 0.2).astype(np.uint8)
+            b = (rng.random((2, 3, 2)) < 0.5).astype(np.uint8)
+            o = np.empty_like(a)
+            lib.vlo_near3(a.ctypes.data, 2, 3, 2, conn, o.ctypes.data)
+            af = a.ravel()
+            exp = np.array([af[v] or any(af[u] for u in nb[v]) for v in range(12)], np.uint8)
+            if not np.array_equal(o.ravel(), exp):
+                return False
+            lib.vlo_reach3(a.ctypes.data, b.ctypes.data, 2, 3, 2, conn, o.ctypes.data)
+            if not np.array_equal(o.ravel(), brute.reach_by_paths_nb(af, b.ravel(), nb)):
+                return False
+            lab = np.empty((2, 3, 2), np.int32)
+            lib.vlo_ccl3(b.ctypes.data, 2, 3, 2, conn, lab.ctypes.data)
+            if not np.array_equal(lab.ravel(), brute.components_nb(b.ravel(), nb)):
                 return False
     # NaN sorts after every number in a percentile: -1, 0.5, 2, NaN, NaN
     v = np.array([np.nan, 2.0, -1.0, np.nan, 0.5], np.float32)
