@@ -1,0 +1,38 @@
+"""The compiler fuzz formulas (every operator of the ABI, constants, mask
+atoms, percentiles and number terms, roots of every kind) evaluated on the
+GPU, fused and plain, against the oracle on float32 and uint16 images."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_same, context, torch_cuda
+from test_compiler_fuzz import random_formula
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("seed", range(int(__import__("os").environ.get("VL_GPU_FUZZ_SEEDS", "60"))))
+def test_random_formulas_on_the_gpu(seed):
+    torch_cuda()
+    rng = np.random.default_rng(5000 + seed)
+    n_channels = int(rng.integers(1, 3))
+    with_mask = seed % 3 == 0
+    recs, roots = random_formula(rng, int(rng.integers(5, 120)), n_channels, with_mask)
+    H, W = int(rng.integers(1, 90)), int(rng.integers(1, 700))
+    conn = 8 if seed % 2 == 0 else 4
+    img = rng.random((n_channels, H, W)).astype(np.float32)
+    if seed % 4 == 1:
+        img = (img * 65535).astype(np.uint16)
+    mask = rng.random((H, W)) < 0.4
+    recs_o = [(op, a, b, (0 if op == "MASK" else im), ch, t, q)
+              for (op, a, b, im, ch, t, q) in recs]
+    exp = oracle.evaluate(recs_o, roots, [img], [mask] if with_mask else [], conn=conn).masks
+    ctx = context()
+    F = ctx.compile(recs, roots, conn)
+    ims = [ctx.image(img)] + ([ctx.mask(mask)] if with_mask else [])
+    for mode in ("fused", "plain"):
+        res = ctx.eval(F, ims, mode=mode)
+        assert res.sync() == 0, ctx.last_error()
+        assert_same([res.mask(r) for r in range(len(roots))], exp, f"seed {seed} {mode}")
