@@ -36,3 +36,38 @@ def test_random_formulas_on_the_gpu(seed):
         res = ctx.eval(F, ims, mode=mode)
         assert res.sync() == 0, ctx.last_error()
         assert_same([res.mask(r) for r in range(len(roots))], exp, f"seed {seed} {mode}")
+
+
+@pytest.mark.parametrize("batch", range(6))
+def test_random_formula_batches_in_one_launch(batch):
+    """Twelve fuzz jobs of different formulas, image sizes, formats and
+    adjacencies in one persistent launch (and replayed), against the
+    oracle."""
+    torch_cuda()
+    rng = np.random.default_rng(9000 + batch)
+    ctx = context()
+    jobs, expect = [], []
+    for k in range(12):
+        n_channels = int(rng.integers(1, 3))
+        with_mask = rng.random() < 0.3
+        recs, roots = random_formula(rng, int(rng.integers(5, 150)), n_channels, with_mask)
+        H, W = int(rng.integers(1, 300)), int(rng.integers(1, 900))
+        conn = 8 if rng.random() < 0.5 else 4
+        img = rng.random((n_channels, H, W)).astype(np.float32)
+        if rng.random() < 0.3:
+            img = (img * 65535).astype(np.uint16)
+        mask = rng.random((H, W)) < 0.4
+        recs_o = [(op, a, b, (0 if op == "MASK" else im), ch, t, q)
+                  for (op, a, b, im, ch, t, q) in recs]
+        expect.append(oracle.evaluate(recs_o, roots, [img], [mask] if with_mask else [],
+                                      conn=conn).masks)
+        F = ctx.compile(recs, roots, conn)
+        jobs.append((F, [ctx.image(img)] + ([ctx.mask(mask)] if with_mask else [])))
+    b = ctx.batch(jobs)
+    for _ in range(2):
+        b.run()
+        for k, exp in enumerate(expect):
+            res = b.result(k)
+            assert res.status_word() == 0, ctx.last_error()
+            assert_same([res.mask(r) for r in range(len(exp))], exp, f"batch {batch} job {k}")
+    b.close()
