@@ -71,3 +71,39 @@ def test_random_formula_batches_in_one_launch(batch):
             assert res.status_word() == 0, ctx.last_error()
             assert_same([res.mask(r) for r in range(len(exp))], exp, f"batch {batch} job {k}")
     b.close()
+
+
+def test_random_formula_queries_through_the_server():
+    """Forty fuzz queries (formulas, sizes, formats, adjacencies) submitted
+    to the serving loop in bursts, so that later ones join batches in
+    flight; every result equals the oracle's."""
+    torch_cuda()
+    import time
+    import paper_2010_07284_gb300 as vg
+    rng = np.random.default_rng(777)
+    ctx = context()
+    srv = vg.Server(ctx, max_inflight_batches=3, max_batch_jobs=8, batch_window_us=100)
+    pending = []
+    for k in range(40):
+        n_channels = int(rng.integers(1, 3))
+        with_mask = rng.random() < 0.3
+        recs, roots = random_formula(rng, int(rng.integers(5, 150)), n_channels, with_mask)
+        H, W = int(rng.integers(1, 260)), int(rng.integers(1, 800))
+        conn = 8 if rng.random() < 0.5 else 4
+        img = rng.random((n_channels, H, W)).astype(np.float32)
+        if rng.random() < 0.3:
+            img = (img * 65535).astype(np.uint16)
+        mask = rng.random((H, W)) < 0.4
+        recs_o = [(op, a, b, (0 if op == "MASK" else im), ch, t, q)
+                  for (op, a, b, im, ch, t, q) in recs]
+        exp = oracle.evaluate(recs_o, roots, [img], [mask] if with_mask else [], conn=conn).masks
+        F = ctx.compile(recs, roots, conn)
+        ims = [ctx.image(img)] + ([ctx.mask(mask)] if with_mask else [])
+        pending.append((srv.submit(F, ims), exp, F, ims))
+        if k % 8 == 7:
+            time.sleep(0.002)
+    for t, exp, F, ims in pending:
+        st, res = srv.wait(t, timeout_us=60_000_000)
+        assert st == 0, f"ticket {t}: status {st}"
+        assert_same([res.mask(r) for r in range(len(exp))], exp, f"ticket {t}")
+    srv.close()
