@@ -38,7 +38,7 @@ def test_random_formulas_on_the_gpu(seed):
         assert_same([res.mask(r) for r in range(len(roots))], exp, f"seed {seed} {mode}")
 
 
-@pytest.mark.parametrize("batch", range(6))
+@pytest.mark.parametrize("batch", range(int(__import__("os").environ.get("VL_GPU_FUZZ_BATCHES", "6"))))
 def test_random_formula_batches_in_one_launch(batch):
     """Twelve fuzz jobs of different formulas, image sizes, formats and
     adjacencies in one persistent launch (and replayed), against the
