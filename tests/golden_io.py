@@ -20,7 +20,8 @@ def _ints(lines: List[str]) -> np.ndarray:
 
 def load(path: str) -> Dict:
     """Parse a fixture: "//" comments, 'op NAME', named grids ('phi',
-    'phi1', 'phi2'), 'expect conn=K' grids, or key/value lines."""
+    'phi1', 'phi2'), an integer 'image' grid, 'expect conn=K' grids, or
+    key/value lines."""
     out: Dict = {"path": path, "expect": {}, "kv": []}
     cur = None
     buf: List[str] = []
@@ -32,6 +33,8 @@ def load(path: str) -> Dict:
         if cur.startswith("expect"):
             conn = int(cur.split("conn=")[1])
             out["expect"][conn] = _ints(buf) if out["op"] == "ccl" else _grid(buf)
+        elif cur == "image":
+            out[cur] = _ints(buf)
         else:
             out[cur] = _grid(buf)
         cur, buf = None, []
@@ -44,7 +47,7 @@ def load(path: str) -> Dict:
             head = ln.split()[0]
             if head == "op":
                 out["op"] = ln.split()[1]
-            elif head in ("phi", "phi1", "phi2") or head == "expect":
+            elif head in ("phi", "phi1", "phi2", "image") or head == "expect":
                 flush()
                 cur = ln.strip()
             elif head in ("values", "q", "scale", "const"):

@@ -133,3 +133,22 @@ def test_grow_spec_uint16_7680():
         res = ctx.eval(F, [ctx.image(img)])
         assert res.sync() == 0, ctx.last_error()
         assert_same([res.mask(0)], [exp], f"grow u16 7680 {mode}")
+
+
+def test_hand_worked_spec_u16_fixture():
+    """The case-study spec on the hand-worked 16-bit fixture (pixels on and
+    next to both thresholds, a diagonal-only contact): the GPU gives the
+    fixture's masks under both adjacencies, fused and plain."""
+    torch_cuda()
+    import golden_io
+    import os
+    fx = golden_io.load(os.path.join(golden_io.GOLDEN, "spec_u16.txt"))
+    img = fx["image"].astype(np.uint16)[None]
+    f = wl.grow_spec_u16_formula()
+    for conn, exp in fx["expect"].items():
+        check_formula(wl.formula_to_records(f), f.roots, [img], conn=conn)
+        ctx = context()
+        F = ctx.compile(wl.formula_to_records(f), f.roots, conn)
+        res = ctx.eval(F, [ctx.image(img)])
+        assert res.sync() == 0
+        assert_same([res.mask(0)], [exp], f"fixture conn={conn}")

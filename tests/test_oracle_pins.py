@@ -53,6 +53,12 @@ def test_golden_fixture(fx):
         spec = wl.grow_spec_formula()
         assert np.float32(spec.nodes[0].t) == np.float32(62258.0 / 65535.0)
         assert np.float32(spec.nodes[1].t) == np.float32(56360.0 / 65535.0)
+    elif op == "spec_u16":
+        img = fx["image"].astype(np.uint16)[None]
+        spec = wl.grow_spec_u16_formula()
+        for conn, exp in fx["expect"].items():
+            got = oracle.evaluate(wl.formula_to_records(spec), spec.roots, [img], conn=conn).masks[0]
+            np.testing.assert_array_equal(got, exp)
     else:
         raise AssertionError(f"unknown fixture op {op}")
 
