@@ -202,19 +202,25 @@ def test_bad_inputs_are_rejected():
 # ------------------------------------------------------------ full sizes ---
 
 def test_config2_full_size_repeated_replays():
-    """2048 x 2048 uniform image, 2000-node random formula: the fused batch
-    replayed several times (graph replays reuse scratch memory) must keep a
-    clean status and equal the oracle on every root each time."""
+    """2048 x 2048 uniform image, 2000-node random formula, in the launch
+    configuration the benchmark times (the autotuner's tile shape for this
+    job): the fused batch replayed several times (graph replays reuse
+    scratch memory) must keep a clean status and equal the oracle on every
+    root each time."""
     torch = torch_cuda()
+    import paper_2010_07284_gb300 as vg
     f = wl.random_dag(2000, seed=0)
     rec = wl.formula_to_records(f)
     img = wl.uniform_image(2048, 2048, seed=0)
     exp = oracle.evaluate(rec, f.roots, [img], conn=8).masks
-    ctx = context()
+    ctx = vg.Context()
     F = ctx.compile(rec, f.roots, 8)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         im = ctx.image(img, s)
+        tune = ctx.autotune([(F, [im])], stream=s, reps=1)
+        assert all(t["status"] == 0 for t in tune["trials"]), tune
+        assert ctx.tile_shape([(F, [im])])["tuned"]
         b = ctx.batch([(F, [im])], s)
         for k in range(3):
             b.run(s)
