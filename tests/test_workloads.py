@@ -49,3 +49,45 @@ def test_stream_shapes():
     assert np.all(np.diff(t) >= 0)
     sizes = np.array([x.n_nodes for x in q])
     assert sizes.min() >= 10 and sizes.max() <= 2000
+
+
+def test_sequential_chains_and_taps():
+    for mix in ("mixed", "near", "reach"):
+        f = wl.sequential_dag(400, seed=2, mix=mix, taps=25)
+        g = wl.sequential_dag(400, seed=2, mix=mix, taps=25)
+        assert f.nodes == g.nodes and f.roots == g.roots
+        # every operator takes the node before it as its first operand,
+        # binary ones a fresh threshold as the second
+        for i, n in enumerate(f.nodes[1:], start=1):
+            if n.op in ("NOT", "NEAR"):
+                assert n.a == i - 1
+            elif n.op in ("AND", "REACH"):
+                assert n.b == i - 1 and f.nodes[i - 1].op in ("THR_GT", "THR_LT")
+        assert f.roots[-1] == len(f.nodes) - 1 and f.roots[:3] == [0, 25, 50]
+    ops = [n.op for n in wl.sequential_dag(2000, seed=0, mix="near").nodes]
+    assert ops.count("REACH") == 0 and ops.count("NEAR") > ops.count("NOT")
+    assert wl.sequential_dag(300, seed=5).roots == [len(wl.sequential_dag(300, seed=5).nodes) - 1]
+
+
+def test_arith_dag_kinds():
+    f = wl.arith_dag(80, seed=1)
+    num = set()
+    for i, n in enumerate(f.nodes):
+        if n.op in wl.NUMBER_OPS:
+            num.add(i)
+            if n.op != "VALUE":
+                assert n.a in num and (n.b < 0 or n.b in num)
+        elif n.op in ("THR_GT", "THR_LT", "PCT_GT", "PCT_LT"):
+            assert n.a in num
+        else:
+            assert n.a not in num and n.b not in num
+    assert all(r not in num for r in f.roots)
+
+
+def test_uint16_generators():
+    u = wl.uniform_image_u16(7, 9, channels=2, seed=1)
+    assert u.dtype == np.uint16 and u.shape == (2, 7, 9)
+    q = wl.to_u16(np.array([[-0.1, 0.0, 0.5, 1.0, 1.2]], np.float32))
+    assert q.tolist() == [[0, 0, 32768, 65535, 65535]]
+    spec = wl.grow_spec_u16_formula()
+    assert [n.t for n in spec.nodes[:2]] == [62258.0, 56360.0]
