@@ -91,3 +91,11 @@ def test_uint16_generators():
     assert q.tolist() == [[0, 0, 32768, 65535, 65535]]
     spec = wl.grow_spec_u16_formula()
     assert [n.t for n in spec.nodes[:2]] == [62258.0, 56360.0]
+
+
+def test_mri_volume_phantom():
+    v = wl.mri_phantom_volume(12, 40, 36, seed=2)
+    assert v.shape == (4, 12, 40, 36) and v.dtype == np.float32
+    assert np.array_equal(v, wl.mri_phantom_volume(12, 40, 36, seed=2))
+    # the core is brighter than the background in channel 2, in 3D
+    assert v[2].max() > 0.7 and np.median(v[2]) < 0.45

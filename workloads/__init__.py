@@ -18,7 +18,7 @@ from .formulas import (Node, Formula, OPS, PRIMITIVE_OPS, DERIVED_OPS, NUMBER_OP
 from .images import (gaussian_field_image, uniform_image, uniform_image_u16, to_u16,
                      bernoulli_mask, spiral_mask, checkerboard_mask, rings_mask, rings_count,
                      mri_phantom_batch, mri_phantom_batch_parallel, mri_side_lengths,
-                     seed_mask)
+                     mri_phantom_volume, seed_mask)
 from .streams import poisson_queries
 
 __all__ = [
@@ -27,5 +27,6 @@ __all__ = [
     "grow_spec_u16_formula", "formula_to_records", "gaussian_field_image", "uniform_image",
     "uniform_image_u16", "to_u16", "bernoulli_mask",
     "spiral_mask", "checkerboard_mask", "rings_mask", "rings_count",
-    "mri_phantom_batch", "mri_phantom_batch_parallel", "mri_side_lengths", "seed_mask", "poisson_queries",
+    "mri_phantom_batch", "mri_phantom_batch_parallel", "mri_side_lengths", "mri_phantom_volume",
+    "seed_mask", "poisson_queries",
 ]

@@ -248,3 +248,36 @@ def uniform_image_u16(h: int, w: int, channels: int = 1, seed: int = 0) -> np.nd
     """(C, H, W) uint16 pixels, uniform over 0..65535."""
     rng = np.random.default_rng(seed)
     return rng.integers(0, 65536, size=(channels, h, w), dtype=np.uint16)
+
+
+def _smooth_ellipsoid(zz, yy, xx, c, r, soft):
+    """Logistic-edged axis-aligned ellipsoid, centre c = (z, y, x), radii r."""
+    d = np.sqrt(((zz - c[0]) / r[0]) ** 2 + ((yy - c[1]) / r[1]) ** 2 + ((xx - c[2]) / r[2]) ** 2)
+    return 1.0 / (1.0 + np.exp((d - 1.0) / soft))
+
+
+def mri_phantom_volume(d: int, h: int, w: int, seed: int = 0) -> np.ndarray:
+    """A 4-channel MRI-volume-shaped phantom (the paper's scans are 3D
+    volumes of which it keeps one slice, Sec. 4.2), shape (4, d, h, w)
+    float32: a brain ellipsoid and a tumour of core, rim shell and oedema
+    halo as in the slice phantom, plus N(0, 0.05) noise on every channel."""
+    rng = np.random.default_rng(seed)
+    zz, yy, xx = np.mgrid[0:d, 0:h, 0:w].astype(np.float64)
+    brain = _smooth_ellipsoid(zz, yy, xx, (d / 2, h / 2, w / 2),
+                              (d * rng.uniform(0.36, 0.44), h * rng.uniform(0.36, 0.44),
+                               w * rng.uniform(0.34, 0.42)), 0.03)
+    c = (d / 2 + rng.uniform(-0.15, 0.15) * d, h / 2 + rng.uniform(-0.18, 0.18) * h,
+         w / 2 + rng.uniform(-0.18, 0.18) * w)
+    rc = min(d, h, w) * rng.uniform(0.07, 0.12)
+    core = _smooth_ellipsoid(zz, yy, xx, c, (rc, rc, rc * rng.uniform(0.7, 1.0)), 0.08)
+    outer = _smooth_ellipsoid(zz, yy, xx, c, (rc * 1.45, rc * 1.45, rc * 1.45), 0.06)
+    rim = np.clip(outer - core, 0, 1)
+    halo = np.clip(_smooth_ellipsoid(zz, yy, xx, c, (rc * 2.6, rc * 2.6, rc * 2.9), 0.15) - outer, 0, 1)
+    base = 0.35 * brain
+    ch = np.empty((4, d, h, w), dtype=np.float64)
+    ch[0] = base + 0.45 * halo + 0.55 * core + 0.30 * rim
+    ch[1] = base + 0.60 * rim
+    ch[2] = base + 0.60 * core
+    ch[3] = 0.30 + 0.40 * brain - 0.20 * (core + rim)
+    ch += rng.normal(0.0, 0.05, size=ch.shape)
+    return ch.astype(np.float32)
