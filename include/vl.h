@@ -4,7 +4,7 @@
  *
  * What it computes (paper "A spatial model checker in GPU", Sec. 2): a
  * formula phi ::= p | not phi | phi1 and phi2 | N phi | rho phi1[phi2]
- * (Eq. def:syntax) is interpreted on the pixels of an image of fixed size,
+ * (Eq. (1) of Sec. 2) is interpreted on the pixels of an image of fixed size,
  * and its value is the binary image of the pixels satisfying it.  Atomic
  * propositions are thresholds on an image feature; not / and are pixel-wise;
  * N phi is the dilation of phi by the Moore neighbourhood (8-adjacency) or by
@@ -164,7 +164,7 @@ VL_API vl_status vl_image_format(const vl_image* img, int32_t* format);
 
 /* ---------------------------------------------------------------- formulas */
 
-/* Operators of a formula node.  The primitive ones follow Eq. (def:syntax);
+/* Operators of a formula node.  The primitive ones follow Eq. (1) of Sec. 2;
  * the derived ones are expanded by the compiler into primitives:
  *   OR(a,b)         = not(not a and not b)
  *   INTERIOR(a)     = not N not a                    (erosion, Sec. 2)

@@ -1,7 +1,7 @@
 """Expansion of derived connectives into the primitive grammar, with
 structural sharing -- oracle side (test infrastructure only).
 
-The primitive grammar is Eq. (def:syntax): p | not | and | N | rho.  The paper
+The primitive grammar is Eq. (1) of Sec. 2: p | not | and | N | rho.  The paper
 names interior, surroundedness, contact (Sec. 2) and grow (Sec. 4.2) as derived
 from these without printing the formulas; the definitions used here are the
 readings listed below.

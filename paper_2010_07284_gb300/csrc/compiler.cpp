@@ -2,7 +2,7 @@
 //
 // 1. Expansion with sharing (Sec. 3.2: macros are expanded without
 //    duplicating sub-expressions).  Derived connectives become primitives
-//    (Eq. def:syntax); identical nodes become one.  The resulting primitive
+//    (Eq. (1) of Sec. 2); identical nodes become one.  The resulting primitive
 //    DAG is what the pixel-operation metric counts.
 // 2. Lowering for execution: rho phi1[phi2] = N(phi1 or Z) with Z the
 //    phi2-components meeting N phi1 (the reduction of Sec. 3.2), plus

@@ -103,6 +103,38 @@ def reach_by_paths(phi1: np.ndarray, phi2: np.ndarray, conn: int) -> np.ndarray:
     return out.reshape(H, W)
 
 
+def touch_by_paths(phi1: np.ndarray, phi2: np.ndarray, conn: int) -> np.ndarray:
+    """Contact by its meaning: x is in phi1 and a path pi_0 = x, ..., pi_l
+    (l >= 0) exists that stays inside phi1 up to pi_{l-1} and ends on a phi2
+    pixel pi_l -- phi1's region around x meets phi2 or borders it (Sec. 2
+    names contact among the derived connectives).  DFS over phi1 pixels."""
+    H, W = phi1.shape
+    f1 = phi1.ravel().astype(bool)
+    f2 = phi2.ravel().astype(bool)
+    nb = neighbours(H, W, conn)
+    out = np.zeros(H * W, dtype=np.uint8)
+    for x in range(H * W):
+        if not f1[x]:
+            continue
+        seen = {x}
+        stack = [x]
+        hit = False
+        while stack and not hit:
+            v = stack.pop()
+            if f2[v]:
+                hit = True
+                break
+            for u in nb[v]:
+                if f2[u]:
+                    hit = True
+                    break
+                if f1[u] and u not in seen:
+                    seen.add(u)
+                    stack.append(u)
+        out[x] = 1 if hit else 0
+    return out.reshape(H, W)
+
+
 def surrounded_by_paths(phi1: np.ndarray, phi2: np.ndarray, conn: int) -> np.ndarray:
     """Direct definition: x in phi1 and no path pi from x with l >= 1,
     pi_1..pi_l outside phi2 and pi_l outside phi1 (every way out of phi1

@@ -188,3 +188,75 @@ def test_unmutated_source_passes(tmpdir_mod):
 def test_mutant_is_rejected(tmpdir_mod, name):
     old, new = MUTANTS[name]
     assert not _pins_pass(_build(tmpdir_mod, name, old, new)), f"pins missed mutant {name}"
+
+
+# ----------------------------------------------- expansion of connectives --
+# Planted mistakes in the oracle's expansion of the contact connective
+# (oracle/expand.py): a modified copy of the module replaces the expansion
+# for the duration of one check; the touch pins must then fail.
+
+EXPAND_SRC = os.path.join(os.path.dirname(SRC), "expand.py")
+
+EXPAND_MUTANTS = {
+    "touch_arguments_swapped": ("return self.AND(a, self.REACH(b, a))",
+                                "return self.AND(a, self.REACH(a, b))"),
+    "touch_without_and": ("return self.AND(a, self.REACH(b, a))", "return self.REACH(b, a)"),
+    "touch_is_grow": ("return self.AND(a, self.REACH(b, a))",
+                      "return self.OR(a, self.AND(b, self.REACH(a, b)))"),
+    "touch_via_near": ("return self.AND(a, self.REACH(b, a))",
+                       "return self.AND(a, self.NEAR(b))"),
+}
+
+
+def _touch_pins_pass(expand_fn) -> bool:
+    """The touch pins (hand-worked fixture, path search, region contact)
+    with the oracle's evaluator running on `expand_fn`."""
+    import oracle.oracle as oo
+    saved = oo.expand
+    oo.expand = expand_fn
+    try:
+        def touch(a, b, conn):
+            nodes = [("MASK", -1, -1, 0, 0, 0.0, 0.0), ("MASK", -1, -1, 1, 0, 0.0, 0.0),
+                     ("TOUCH", 0, 1, 0, 0, 0.0, 0.0)]
+            return oo.evaluate(nodes, [2], masks=[a, b], conn=conn).masks[0]
+
+        for fx in golden_io.all_fixtures():
+            if fx["op"] != "touch":
+                continue
+            for conn, exp in fx["expect"].items():
+                if not np.array_equal(touch(fx["phi1"], fx["phi2"], conn), exp):
+                    return False
+        rng = np.random.default_rng(7)
+        for conn in (4, 8):
+            for shape in [(4, 4)] * 15 + [(5, 5)] * 10:
+                a = (rng.random(shape) < 0.6).astype(np.uint8)
+                b = (rng.random(shape) < 0.15).astype(np.uint8)
+                if not np.array_equal(touch(a, b, conn), brute.touch_by_paths(a, b, conn)):
+                    return False
+        return True
+    finally:
+        oo.expand = saved
+
+
+def _load_expand(tmp, name, old, new):
+    import importlib.util
+    src = open(EXPAND_SRC).read()
+    assert old in src, f"mutation {name} no longer applies"
+    path = os.path.join(tmp, f"expand_{name}.py")
+    with open(path, "w") as fh:
+        fh.write(src.replace(old, new, 1))
+    spec = importlib.util.spec_from_file_location(f"expand_{name}", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.expand
+
+
+def test_unmutated_expansion_passes_touch_pins(tmpdir_mod):
+    assert _touch_pins_pass(_load_expand(tmpdir_mod, "clean", "", ""))
+
+
+@pytest.mark.parametrize("name", sorted(EXPAND_MUTANTS))
+def test_expansion_mutant_is_rejected(tmpdir_mod, name):
+    old, new = EXPAND_MUTANTS[name]
+    assert not _touch_pins_pass(_load_expand(tmpdir_mod, name, old, new)), \
+        f"touch pins missed mutant {name}"

@@ -34,7 +34,7 @@ def test_golden_fixture(fx):
     elif op == "reach":
         for conn, exp in fx["expect"].items():
             np.testing.assert_array_equal(oracle.reach(fx["phi1"], fx["phi2"], conn), exp)
-    elif op in ("surrounded", "grow"):
+    elif op in ("surrounded", "grow", "touch"):
         for conn, exp in fx["expect"].items():
             got = _eval_binary(op.upper(), fx["phi1"], fx["phi2"], conn)
             np.testing.assert_array_equal(got, exp)
@@ -251,6 +251,50 @@ def test_grow_against_region_contact(conn):
         hit = np.unique(lab[touch & (lab > 0)])
         exp = a.astype(bool) | (np.isin(lab, hit) & (lab > 0))
         np.testing.assert_array_equal(_eval_binary("GROW", a, b, conn), exp.astype(np.uint8))
+
+
+@pytest.mark.parametrize("conn", CONNS)
+def test_touch_against_region_contact(conn):
+    """touch(a, b): the a pixels whose a-component contains a b pixel or is
+    adjacent to one.  Written from the components of a (scipy's labeller)
+    and the dilation of b, not from reachability."""
+    nd = pytest.importorskip("scipy.ndimage")
+    st = np.ones((3, 3), bool) if conn == 8 else nd.generate_binary_structure(2, 1)
+    rng = np.random.default_rng(80 + conn)
+    for shape in [(16, 16), (40, 23), (7, 50), (1, 30), (30, 1)]:
+        for pa, pb in [(0.55, 0.02), (0.4, 0.05), (0.7, 0.01)]:
+            a = (rng.random(shape) < pa).astype(np.uint8)
+            b = (rng.random(shape) < pb).astype(np.uint8)
+            lab, _ = nd.label(a, structure=st)
+            near_b = nd.binary_dilation(b, structure=st, border_value=0)
+            hit = np.unique(lab[near_b & (lab > 0)])
+            exp = np.isin(lab, hit) & (lab > 0)
+            np.testing.assert_array_equal(_eval_binary("TOUCH", a, b, conn), exp.astype(np.uint8))
+
+
+@pytest.mark.parametrize("conn", CONNS)
+def test_touch_against_paths(conn):
+    """touch(a, b) on small grids against its meaning by path search: from x
+    in a, walk inside a until a b pixel is entered."""
+    rng = np.random.default_rng(90 + conn)
+    for shape in [(3, 3)] * 60 + [(4, 4)] * 60 + [(5, 5)] * 40 + [(2, 6)] * 20:
+        a = (rng.random(shape) < rng.uniform(0.3, 0.8)).astype(np.uint8)
+        b = (rng.random(shape) < rng.uniform(0.05, 0.4)).astype(np.uint8)
+        np.testing.assert_array_equal(_eval_binary("TOUCH", a, b, conn),
+                                      brute.touch_by_paths(a, b, conn))
+
+
+def test_touch_special_cases():
+    """touch(a, false) = false; touch(a, true) = a; touch(a, a) = a;
+    touch(false, b) = false."""
+    rng = np.random.default_rng(99)
+    for conn in CONNS:
+        a = (rng.random((9, 11)) < 0.5).astype(np.uint8)
+        z, o = np.zeros_like(a), np.ones_like(a)
+        np.testing.assert_array_equal(_eval_binary("TOUCH", a, z, conn), z)
+        np.testing.assert_array_equal(_eval_binary("TOUCH", a, o, conn), a)
+        np.testing.assert_array_equal(_eval_binary("TOUCH", a, a, conn), a)
+        np.testing.assert_array_equal(_eval_binary("TOUCH", z, a, conn), z)
 
 
 @pytest.mark.parametrize("conn", CONNS)

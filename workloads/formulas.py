@@ -1,6 +1,6 @@
 """Formula DAGs shaped like the paper's test formulas.
 
-Grammar of the logic (Eq. def:syntax, Sec. 2): p | not phi | phi1 and phi2 |
+Grammar of the logic (Eq. (1) of Sec. 2): p | not phi | phi1 and phi2 |
 N phi | rho phi1[phi2].  Atomic propositions are thresholds on an image
 feature (Sec. 2 and the segmentation spec of Fig. "specification").  Derived
 connectives (interior, surrounded, grow, touch, or) are kept as named nodes
