@@ -85,6 +85,36 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def formula_alg_bytes(info: dict, P: float) -> float:
+    """Algorithmic bytes of one evaluation of a formula over P pixels: each
+    image channel read once (4 B/px), each materialised mask written once and
+    read back once per consumer (1/8 B/px each), and 8.25 B/px per rho select
+    (int32 labels written and read once, plus its flag mask)."""
+    return (4.0 * P * info["n_channels_read"]
+            + P / 8.0 * (info["mask_writes"] + info["mask_reads"])
+            + P * (8.0 + 2.0 / 8.0) * info["n_selects"])
+
+
+def sig(x, digits: int = 4):
+    """Floats rounded to `digits` significant digits, recursively (keeps the
+    printed line short)."""
+    if isinstance(x, float):
+        if x != x or x in (float("inf"), float("-inf")) or x == 0.0:
+            return x
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, dict):
+        return {k: sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(v, digits) for v in x]
+    return x
+
+
+def emit_leg(name: str, obj: dict) -> None:
+    """A leg's full figures on a line of its own, before the result line
+    (prefixed, so that it is not taken for the result line)."""
+    print(f"# leg {name} " + json.dumps(sig(obj)), flush=True)
+
+
 class ClockSampler:
     FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -186,7 +216,7 @@ def oracle_all_cores(tasks) -> dict:
             "pixel_ops": float(sum(r[1] for r in res)), "cores": cores, "tasks": len(tasks)}
 
 
-def leg_grow_7680(ctx, stream, flush, runs: int = 5) -> dict:
+def leg_grow_7680(ctx, stream, flush, peak: float, runs: int = 5) -> dict:
     """The case-study spec (two thresholds and grow, Sec. 4.2) on a 7680 x
     7680 upscaled MRI-shaped slice, the scale of the paper's only published
     timings: device time with the image resident, and end to end through the
@@ -197,7 +227,8 @@ def leg_grow_7680(ctx, stream, flush, runs: int = 5) -> dict:
     f = wl.grow_spec_formula()
     img = upscaled_slice(7680)
     F = ctx.compile(wl.formula_to_records(f), f.roots, 8)
-    n_prim = F.info()["n_primitive"]
+    finfo = F.info()
+    n_prim = finfo["n_primitive"]
     P = img.shape[1] * img.shape[2]
     pin = torch.from_numpy(img).pin_memory()
     out = np.empty((img.shape[1], ((img.shape[2] + 127) // 128) * 4), dtype=np.uint32)
@@ -258,8 +289,12 @@ def leg_grow_7680(ctx, stream, flush, runs: int = 5) -> dict:
         u16_ms = float(np.mean([a.elapsed_time(z) for a, z in ev16]))
         bu.close()
         im16.close()
+    alg = formula_alg_bytes(finfo, P)
+    ach = alg / (dev_ms / 1e3) / 1e9
     return {"workload": "grow(I > 0.95, I > 0.86) on a 7680x7680 upscaled MRI-shaped slice (59 Mpx)",
             "device_ms": dev_ms, "e2e_ms": float(np.mean(e2e)),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "algorithmic_bytes": alg, "kernel": "k_exec"},
             "uint16": {"device_ms": u16_ms, "thresholds": [62258, 56360],
                        "value": n_prim * P / (u16_ms / 1e3) / 1e9},
             "value": n_prim * P / (dev_ms / 1e3) / 1e9, "unit": "Gpixel-ops/s",
@@ -346,11 +381,14 @@ def leg_ccl(ctx, stream, flush, peak: float, S: int = 8192, runs: int = 6) -> di
             raise SystemExit("ccl failed: " + ctx.last_error())
     cms = float(np.mean([a.elapsed_time(b) for a, b in ce]))
     mimg.close()
+    ach = 4.125 * S * S / (cms / 1e3) / 1e9
     return {"value": S * S / (cms / 1e3) / 1e9, "unit": "Gpix/s", "ms": cms,
             "mask": f"{S}x{S} Bernoulli(0.5), 8-adjacency",
-            "achieved_GBps": 4.125 * S * S / (cms / 1e3) / 1e9,
-            "frac": 4.125 * S * S / (cms / 1e3) / 1e9 / peak,
-            "traffic": profiled_traffic("ccl", "dram_bytes_per_labelling") if S == 8192 else None}
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "algorithmic_bytes": 4.125 * S * S,
+                         "kernel": "k_ccl_local + k_ccl_merge + k_ccl_final_labels",
+                         "traffic": profiled_traffic("ccl", "dram_bytes_per_labelling")
+                         if S == 8192 else None}}
 
 
 def leg_pointer_jumping(ctx, stream, union_find_ms: float, S: int = 8192, runs: int = 3) -> dict:
@@ -378,7 +416,7 @@ def leg_pointer_jumping(ctx, stream, union_find_ms: float, S: int = 8192, runs: 
             "union_find_speedup": pj / union_find_ms}
 
 
-def leg_mri_batch(ctx, stream, flush, n_images: int = 4096, reps: int = 5) -> dict:
+def leg_mri_batch(ctx, stream, flush, peak: float, n_images: int = 4096, reps: int = 5) -> dict:
     """4096 MRI-shaped 4-channel images of uneven sizes, the fixed 40-primitive
     segmentation formula with percentile thresholds, one persistent launch
     (autotuned tiles, CUDA graph) per step; beside it the plain per-operator
@@ -390,7 +428,8 @@ def leg_mri_batch(ctx, stream, flush, n_images: int = 4096, reps: int = 5) -> di
     sides = wl.mri_side_lengths(n_images, seed=0)
     imgs = wl.mri_phantom_batch_parallel(sides, seed=0)
     F = ctx.compile(rec, f.roots, 8)
-    n_prim = F.info()["n_primitive"]
+    finfo = F.info()
+    n_prim = finfo["n_primitive"]
     px = float(sum(int(im.shape[1]) * int(im.shape[2]) for im in imgs))
     with torch.cuda.stream(stream):
         handles = [ctx.image(im, stream) for im in imgs]
@@ -428,12 +467,17 @@ def leg_mri_batch(ctx, stream, flush, n_images: int = 4096, reps: int = 5) -> di
         h.close()
     val = n_prim * px / (float(np.mean(ms)) / 1e3) / 1e9
     plain = n_prim * spx / plain_s / 1e9
+    alg = formula_alg_bytes(finfo, px)
+    ach = alg / (float(np.mean(ms)) / 1e3) / 1e9
     # the oracle on every host core over every 16th image
     cpu = oracle_all_cores([(rec, f.roots, imgs[k]) for k in range(0, n_images, 16)])
     return {"workload": f"{n_images} MRI-shaped images 160-512 px (median 240), 4 channels, "
                         "40-primitive formula with percentile thresholds, 8-adjacency",
             "value": val, "unit": "Gpixel-ops/s", "images_per_s": n_images / (float(np.mean(ms)) / 1e3),
             "ms_per_launch": float(np.mean(ms)), "p99_ms": float(np.percentile(ms, 99)),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "algorithmic_bytes": alg, "kernel": "k_exec",
+                         "note": "each image's working set fits in L2"},
             "tiles": {k: tune["best"][k] for k in ("tile_rows", "tile_words", "ctas_per_sm")},
             "plain_one_at_a_time": {"value": plain, "unit": "Gpixel-ops/s",
                                     "images": len(sample), "wall_s": plain_s},
@@ -534,7 +578,8 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
         sd = int(sides[qi[k]])
         tasks.append((wl.formula_to_records(fd), fd.roots, wl.uniform_image(sd, sd, seed=100 + int(qi[k]))))
     cpu = oracle_all_cores(tasks)
-    return {"workload": f"{n_queries} queries over {n_images} resident images (sides log-uniform "
+    return {"queries": n_queries, "pool_images": n_images,
+            "workload": f"{n_queries} queries over {n_images} resident images (sides log-uniform "
                         f"128-4096), {n_formulas} formulas of 10-2000 nodes, 8-adjacency",
             "saturated": {"queries_per_s": rate, "value": work / wall_sat / 1e9,
                           "unit": "Gpixel-ops/s", "p50_ms": st_sat["p50_ms"], "p99_ms": st_sat["p99_ms"],
@@ -679,23 +724,18 @@ def main():
     ms_per_step = total_max / args.steps
 
     # roofline of the persistent executor (the only kernel of a step):
-    # algorithmic bytes of the whole DAG per launch: each image channel read
-    # once, each materialised mask written once and read back once per
-    # consumer, and 8.375 B/px per rho (masks plus int32 labels written and
-    # read once)
-    alg_bytes = (4.0 * P * info["n_channels_read"]
-                 + P / 8.0 * (info["mask_writes"] + info["mask_reads"])
-                 + P * (8.0 + 2.0 / 8.0) * info["n_selects"])
+    # algorithmic bytes of the whole DAG per launch (formula_alg_bytes)
+    alg_bytes = formula_alg_bytes(info, P)
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (float(np.mean(step_ms)) / 1e3) / 1e9
     traffic = profiled_traffic("k_exec", "dram_bytes_per_launch")
+    tiles = {k: tune["best"][k] for k in ("tile_rows", "tile_words", "ctas_per_sm")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": dict(workload_config(world),
-                           tiles={k: tune["best"][k] for k in ("tile_rows", "tile_words", "ctas_per_sm")}),
+            "config": dict(workload_config(world), tiles=tiles),
             "gpu_launches": args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -703,10 +743,10 @@ def main():
                          "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": clk,
             "formula": {"n_primitive": n_prim, "n_reach": info["n_reach"],
-                        "n_steps": info["n_steps"], "n_groups": info["n_groups"],
-                        "n_roots": info["n_roots"]},
-            "autotune": [(t["tile_rows"], t["tile_words"], t["ctas_per_sm"], round(t["ms"], 3))
-                         for t in tune["trials"]]}
+                        "n_steps": info["n_steps"], "n_roots": info["n_roots"]}}
+    if rank == 0:
+        emit_leg("autotune", {"best": tiles, "trials": [
+            (t["tile_rows"], t["tile_words"], t["ctas_per_sm"], t["ms"]) for t in tune["trials"]]})
 
     if not args.no_extras:
         # ---- plain per-operator form, same workload and image
@@ -725,12 +765,11 @@ def main():
                     pe.append(a.elapsed_time(b))
                 r.close()
         line["plain"] = {"value": n_prim * P / (np.mean(pe) / 1e3) / 1e9, "unit": UNIT,
-                         "ms_per_step": float(np.mean(pe)), "steps": len(pe),
-                         "launches_per_step": "one per primitive (4 per rho select + 2)"}
+                         "ms_per_step": float(np.mean(pe))}
         line["batched_over_plain"] = line["value"] / world / line["plain"]["value"]
         # ---- full CCL on an 8192 x 8192 Bernoulli(0.5) mask
-        line["ccl"] = leg_ccl(ctx, stream, flush, peak)
-        line["ccl"]["pointer_jumping"] = leg_pointer_jumping(ctx, stream, line["ccl"]["ms"])
+        ccl = leg_ccl(ctx, stream, flush, peak)
+        ccl["pointer_jumping"] = leg_pointer_jumping(ctx, stream, ccl["ms"])
         # ---- end to end through the public API with host buffers
         import torch as _t
         pin_in = _t.from_numpy(host_img).pin_memory()
@@ -755,11 +794,36 @@ def main():
                        "h2d_bytes_per_step": int(host_img.nbytes),
                        "d2h_bytes_per_step": int(res_words * 4),
                        "ms_per_step": 1e3 * float(np.mean(e2e))}
-        # ---- MRI-shaped batch and the serving stream
-        line["mri_batch"] = leg_mri_batch(ctx, stream, flush)
-        line["serving"] = leg_serving(ctx, stream)
-        line["grow_7680"] = leg_grow_7680(ctx, stream, flush)
-        line["formula_scaling"] = leg_formula_scaling(ctx, stream, flush, image)
+        # ---- MRI-shaped batch, the serving stream, the case study, formula size
+        mri = leg_mri_batch(ctx, stream, flush, peak)
+        serving = leg_serving(ctx, stream)
+        grow = leg_grow_7680(ctx, stream, flush, peak)
+        scaling = leg_formula_scaling(ctx, stream, flush, image)
+        if rank == 0:
+            for name, obj in (("ccl", ccl), ("mri_batch", mri), ("serving", serving),
+                              ("grow_7680", grow), ("formula_scaling", scaling)):
+                emit_leg(name, obj)
+        # the headline figures of every leg, short enough that the whole
+        # result line survives a truncated log
+        line["ccl"] = {"value": ccl["value"], "unit": "Gpix/s", "ms": ccl["ms"],
+                       "frac": ccl["roofline"]["frac"], "mask": ccl["mask"],
+                       "pointer_jumping_ms": ccl["pointer_jumping"]["ms"]}
+        line["mri_batch"] = {"value": mri["value"], "images_per_s": mri["images_per_s"],
+                             "ms": mri["ms_per_launch"], "frac": mri["roofline"]["frac"],
+                             "batched_over_plain": mri["batched_over_plain"]}
+        sv = serving
+        line["serving"] = {"queries": sv["queries"], "sat_qps": sv["saturated"]["queries_per_s"],
+                           "load": sv["poisson"]["load"], "qps": sv["poisson"]["queries_per_s"],
+                           "p50_ms": sv["poisson"]["p50_ms"], "p99_ms": sv["poisson"]["p99_ms"],
+                           "plain_qps": sv["plain_one_at_a_time"]["queries_per_s"]}
+        line["grow_7680"] = {"ms": grow["device_ms"], "e2e_ms": grow["e2e_ms"],
+                             "u16_ms": grow["uint16"]["device_ms"],
+                             "frac": grow["roofline"]["frac"]}
+        rows = scaling["rows"]
+        line["formula_scaling"] = {
+            "min_fused_over_plain": min(r["fused_over_plain"] for r in rows),
+            "fused_plain_ms": [[r["kind"][:12], r["nodes"], r["fused_ms"], r["plain_ms"]]
+                               for r in rows]}
         # ---- CPU oracle on a bounded sample (rank 0 only)
         if rank == 0:
             v, dt, _ = oracle_sample(CPU_ROWS_BASE)
@@ -767,7 +831,7 @@ def main():
                                     "sample": f"full formula on the top {CPU_ROWS_BASE} rows "
                                               f"(of 2048) of the image, {dt:.1f} s"}
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(sig(line)), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -523,18 +523,22 @@ VL_API vl_status vl_ccl_status(vl_context* ctx, void* stream);
  * grow behind its back; such callers pass their own buffers and this call
  * allocates nothing, needs no context, and calls no allocating routine.
  *   mask_dev   -- device, h * Wp packed words (layout at the top of this
- *                 file); padding bits must be 0 (as vl_result_mask gives)
+ *                 file); padding bits (columns >= w) are ignored
  *   labels_dev -- device, h * w int32, written (minimum linear index per
  *                 component, -1 background)
- *   wait       -- 0: enqueue on `stream` and return; nonzero: wait for the
- *                 stream and return the device status (VL_ERR_TIMEOUT,
- *                 VL_ERR_INTERNAL) of this call
+ *   wait       -- 0: enqueue on `stream` and return VL_OK; a device
+ *                 status of the call (VL_ERR_TIMEOUT, VL_ERR_INTERNAL) is
+ *                 then not reported, since the next call clears it;
+ *                 nonzero: wait for the stream and return that status
  * Working memory is one fixed array inside the library (about 5 MiB, held
  * by every GPU that loads the library until exit), shared by all calls on a
  * device: calls whose work overlaps on the GPU (different streams, or
  * different host threads) race and must be serialised by the caller.  The
  * array keeps the last call's contents; the call clears what must start at
- * zero.
+ * zero.  The array's device address is looked up on every call (no cache
+ * outlives a device reset).  The first call on a device loads the library's
+ * device code and sets a kernel attribute: make it before any stream
+ * capture.
  * Limit: ceil(h/32) * ceil(Wp/32) tiles of 16 * min(32, Wp) * 32 entries
  * must fit in 2^20 entries -- any image up to 2048 x 1024 or 1024 x 2048,
  * for example.  Larger images return VL_ERR_SHAPE; bad pointers or sizes

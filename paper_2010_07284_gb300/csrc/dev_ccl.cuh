@@ -11,8 +11,10 @@
 //   2. publish: every foreground pixel on the tile border, and every local
 //      root that reaches the border, gets an entry G[gid] in a global
 //      union-find array indexed by linear pixel id gid = y*W + x.
-//   3. merge: pixels adjacent across tile borders are united in G with
-//      atomicMin (links always point to smaller gids, so no cycles).
+//   3. merge: pixels adjacent across tile borders are united in G; a root
+//      is linked under the smaller root by compare-and-swap, so only a node
+//      that is still a root is ever re-pointed and links always point to
+//      smaller gids (no cycles).
 //   4. final: each tile relabels again and resolves its border roots in G.
 // Labels are canonical: the minimum linear index of each component.
 #pragma once
@@ -278,8 +280,11 @@ VL_DEV int ccl_tile_strips(CclSmem& s, const uint32_t* mask, const CclGeom& g, i
     const int r0 = 2 * k, r1 = 2 * k + 1;
     uint32_t a = 0, b = 0;
     if (lane < g.tww) {
-      a = ldcg(&mask[(size_t)(g.r0 + r0) * g.Wp + g.w0 + lane]);
-      if (r1 < g.th) b = ldcg(&mask[(size_t)(g.r0 + r1) * g.Wp + g.w0 + lane]);
+      // padding bits (columns >= W) are cleared here, so that no later pass
+      // can see a pixel outside the image whatever the caller's buffer holds
+      const uint32_t vm = vmask(g.w0 + lane, g.W);
+      a = ldcg(&mask[(size_t)(g.r0 + r0) * g.Wp + g.w0 + lane]) & vm;
+      if (r1 < g.th) b = ldcg(&mask[(size_t)(g.r0 + r1) * g.Wp + g.w0 + lane]) & vm;
     }
     uint32_t al = __shfl_up_sync(FULL, a, 1), bl = __shfl_up_sync(FULL, b, 1);
     if (lane == 0) al = bl = 0;
@@ -756,7 +761,9 @@ VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int npx, int32_t* s
 // runs that touch always have a start of one run inside the other's window.
 // A vertical border pairs each set pixel left of it with the pixel right of
 // it, or, for 8-adjacency when that one is clear, with its diagonal
-// neighbours.  Must be called by the whole warp.
+// neighbours (both border columns lie inside the image: a tile border is a
+// multiple of 1024 columns, below W).  Padding bits of the loaded words are
+// cleared.  Must be called by the whole warp.
 VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y, int unit,
                            int conn, int32_t* G, int npx, int32_t* status) {
   const int lane = threadIdx.x & 31;
@@ -767,7 +774,7 @@ VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y,
     uint32_t v = 0;
     if (lane < 6) {
       const int ww = w - 1 + lane % 3;
-      if (ww >= 0 && ww < Wp) v = ldcg(&m[(size_t)(lane < 3 ? yu : yd) * Wp + ww]);
+      if (ww >= 0 && ww < Wp) v = ldcg(&m[(size_t)(lane < 3 ? yu : yd) * Wp + ww]) & vmask(ww, W);
     }
     const uint32_t mul = __shfl_sync(FULL, v, 0), mu = __shfl_sync(FULL, v, 1),
                    mur = __shfl_sync(FULL, v, 2), mdl = __shfl_sync(FULL, v, 3),

@@ -1,6 +1,7 @@
 // Plain per-operator kernels: one launch per primitive over a whole image.
 // They are the baseline execution form and the building blocks of vl_ccl.
 #include <algorithm>
+#include <mutex>
 
 #include "dev_ccl.cuh"
 #include "dev_common.cuh"
@@ -292,11 +293,23 @@ int ccl_flist_cap(int H, int Wp) {
 }
 size_t ccl_smem_bytes() { return sizeof(CclSmem); }
 
+// The labelling kernels need more than 48 KB of dynamic shared memory; the
+// attribute is set once per device (guarded: host threads may call the
+// labelling entry points concurrently, on different devices).
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_attr_mu;
+bool g_attr_done[kMaxDevices] = {};
+}  // namespace
+
 static cudaError_t ccl_set_attrs() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (g_attr_done[dev]) return cudaSuccess;
   const int sm = (int)sizeof(CclSmem);
-  cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_ccl_local, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
     return e;
   if ((e = cudaFuncSetAttribute(k_ccl_final_labels,
@@ -304,7 +317,7 @@ static cudaError_t ccl_set_attrs() {
     return e;
   if ((e = cudaFuncSetAttribute(k_rz_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
     return e;
-  done = true;
+  g_attr_done[dev] = true;
   return cudaSuccess;
 }
 

@@ -13,11 +13,15 @@
 // The array is a file-scope __device__ variable: every GPU that loads this
 // library holds it (kBytes, about 5 MiB) until the process exits.
 // Host code must not use the symbol as a pointer -- on the host it is only a
-// stand-in -- so the first call on each device looks up its device address
-// with cudaGetSymbolAddress (with that device current) and caches it.
+// stand-in -- so every call looks up its device address with
+// cudaGetSymbolAddress, with the caller's device current.  The lookup is a
+// host-side table read once the module is loaded (it allocates nothing); it
+// is repeated on every call instead of cached so that a call made after
+// cudaDeviceReset, or under another context of the same device, gets the
+// address that is valid now.  The first call on a device loads the module
+// and sets the labelling kernels' shared-memory attribute: make it before
+// any stream capture.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "../../include/vl.h"
 #include "kernels.h"
@@ -32,10 +36,6 @@ constexpr size_t kStatusBytes = 256;  // the status word, padded
 constexpr size_t kBytes = kStatusBytes + kEntries * 4 + kEntries;
 
 __device__ __align__(256) unsigned char g_ccl_scratch[kBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char* g_base[kMaxDevices] = {};
 
 vl_status from_cuda(cudaError_t e) {
   cudaGetLastError();
@@ -55,21 +55,10 @@ extern "C" VL_API vl_status vl_ccl_noalloc(const uint32_t* mask_dev, int32_t h, 
   const size_t tiles = (size_t)vl::ccl_tiles_y(h) * vl::ccl_tiles_x(Wp);
   const int tcap = vl::ccl_tile_cap_host(Wp);
   if (tiles * (size_t)tcap > kEntries) return VL_ERR_SHAPE;  // beyond the fixed array
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_ccl_scratch);
   if (e) return from_cuda(e);
-  if (dev < 0 || dev >= kMaxDevices) return VL_ERR_ARG;
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_base[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_ccl_scratch);
-      if (e) return from_cuda(e);
-      g_base[dev] = static_cast<unsigned char*>(p);
-    }
-    base = g_base[dev];
-  }
+  unsigned char* base = static_cast<unsigned char*>(p);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int32_t* status = reinterpret_cast<int32_t*>(base);
   vl::CclScratch sc{};
