@@ -233,14 +233,17 @@ VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes,
 /* Introspection of a compiled plan (debugging and host-side tests).  Call
  * with NULL arrays to get the sizes, then again with arrays of at least
  * those lengths.  Steps run in order; a step of kind 1 (fused group) runs
- * its instructions on every tile; kinds 2-5 are the four passes of a batch
- * of component selects (tile labelling, border merge, flag propagation,
- * final select); kind 0 computes percentiles; kind 6 computes rank codes
+ * its instructions on every tile; kinds 2, 3 and 5 are the three passes of
+ * a batch of component selects (tile labelling, border merge, final
+ * select; kind 4 is not used); kind 0 computes percentiles; kind 6 computes rank codes
  * (below); kind 7 evaluates number terms (vl_formula_arith).  Steps are
  * listed in an order that respects their dependencies
  * (vl_formula_step_deps).  Instruction opcodes: 1 threshold, 2 load slot, 3 not, 4 and,
  * 5 or, 6 N, 7 constant, 8 store slot, 9 and-not, 10 threshold by rank
- * code.  Slots: [0, n_inter) intermediates, then one per distinct root,
+ * code; bit 7 (0x80) of the opcode marks an instruction that a block
+ * barrier precedes (each buffer word has one owning thread, and the
+ * compiler puts a barrier only where a thread would touch a word another
+ * thread touched since the last one).  Slots: [0, n_inter) intermediates, then one per distinct root,
  * then one per mask image.
  *
  * Rank codes (an evaluation strategy, not part of the logic): when many
@@ -450,9 +453,9 @@ VL_API vl_status vl_result_sync(vl_result* res);
 
 /* Wait, then the raw device status word: 0, VL_ERR_TIMEOUT, or VL_ERR_INTERNAL
  * in the low byte with the failed check in bits 8.. (1 global find bound,
- * 2 global union bound, 3 flagged-root list overflow, 4 saved tile state out
- * of range, 5 tile strip-run capacity, 6 shared union-find bound, 7 global
- * union-find entry outside the image). */
+ * 2 global union bound, 3 not used, 4 saved tile state out of range, 5 tile
+ * strip-run capacity, 6 shared union-find bound, 7 global union-find entry
+ * outside its array). */
 VL_API vl_status vl_result_status_word(vl_result* res, int32_t* word);
 
 /* Shape of a result (any pointer may be NULL); words_per_row = Wp. */

@@ -326,7 +326,9 @@ class Formula(_Handle):
             "rank_values": np.array(rv[:sz.n_rank_values], dtype=np.float32),
             "sizes": rec(sz),
             "steps": [rec(steps[i]) for i in range(sz.n_steps)],
-            "insns": [rec(insns[i]) for i in range(sz.n_insns)],
+            # opcode bit 7: a block barrier precedes the instruction
+            "insns": [dict(rec(insns[i]), op=insns[i].op & 0x7F, sync=bool(insns[i].op & 0x80))
+                      for i in range(sz.n_insns)],
             "selects": [rec(sels[i]) for i in range(sz.n_selects)],
             "pct": [rec(pct[i]) for i in range(sz.n_pct)],
             "root_slots": [roots[i] for i in range(sz.n_roots)],

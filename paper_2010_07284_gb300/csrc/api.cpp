@@ -124,6 +124,10 @@ vl_status check_job_images(vl_context* ctx, const Plan& P, vl_image* const* imgs
         return set_err(ctx, VL_ERR_SHAPE, "image " + std::to_string(i) + " must be a mask");
     }
   }
+  // the component select keys pixels and unseeded components apart: its
+  // union-find holds 2 * H * W int32 entries
+  if (!P.rz.empty() && (long long)h * w > (1LL << 30))
+    return set_err(ctx, VL_ERR_SHAPE, "reachability needs images of at most 2^30 pixels");
   *H = h;
   *W = w;
   return VL_OK;
@@ -133,9 +137,6 @@ int ccl_merge_chunks(int H, int Wp) {
   const long long n = ccl_merge_units(H, Wp);  // one warp each
   const int warps = EXEC_THREADS / 32;
   return (int)std::max<long long>(1, (n + warps - 1) / warps);
-}
-int ccl_flag_chunks(int H, int Wp) {
-  return std::max(1, std::min(64, ccl_tiles_y(H) * ccl_tiles_x(Wp) / 4));
 }
 
 }  // namespace
@@ -175,11 +176,10 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     int H, W, Wp, pitch;
     int gty, gtx, cty, ctx_, ctiles;
     std::vector<int> need;
-    size_t off_images, off_slotptrs, off_pct, off_slots, off_rz, set_bytes, set_off[5];
-    size_t off_roots, off_status, off_fcount, off_planes, off_num;
+    size_t off_images, off_slotptrs, off_pct, off_slots, off_rz, set_bytes, set_off[3];
+    size_t off_roots, off_status, off_planes, off_num;
     int n_table;  // image table: the formula's images, then its number images
-    int step_base, fcount_base;
-    int flist_cap;
+    int step_base;
     int formula_idx;
   };
   std::vector<JobInfo> J(n_jobs);
@@ -221,7 +221,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   const TileShape ts = force ? *force : pick_tile_shape(ctx, jobs, n_jobs);
   if (!tile_shape_fits(ctx, ts)) return set_err(ctx, VL_ERR_ARG, "tile shape does not fit shared memory");
   const int cps = ts.ctas_per_sm > 0 ? std::min(ts.ctas_per_sm, ctx->ctas_per_sm) : ctx->ctas_per_sm;
-  int total_steps = 0, total_rz = 0;
+  int total_steps = 0;
   std::vector<WorkItem> items;
   const int grid = std::max(1, ctx->sm_count * cps);
   for (int j = 0; j < n_jobs; ++j) {
@@ -234,11 +234,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.cty = ccl_tiles_y(I.H);
     I.ctx_ = ccl_tiles_x(I.Wp);
     I.ctiles = I.cty * I.ctx_;
-    I.flist_cap = ccl_flist_cap(I.H, I.Wp);
     I.step_base = total_steps;
-    I.fcount_base = total_rz;
     total_steps += (int)P.steps.size();
-    total_rz += (int)P.rz.size();
     for (const StepDesc& s : P.steps) {
       int n = 1;
       switch (s.kind) {
@@ -246,7 +243,6 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
         case SK_GROUP: n = I.gty * I.gtx; break;
         case SK_RZ_LOCAL: case SK_RZ_FINAL: n = s.rz_cnt * I.ctiles; break;
         case SK_RZ_MERGE: n = s.rz_cnt * ccl_merge_chunks(I.H, I.Wp); break;
-        case SK_RZ_FLAGS: n = s.rz_cnt * ccl_flag_chunks(I.H, I.Wp); break;
         case SK_RANK: n = (int)P.rtab.size() * ((I.H + RANK_ROWS - 1) / RANK_ROWS); break;
         case SK_ARITH: n = (I.H + ARITH_ROWS - 1) / ARITH_ROWS; break;
       }
@@ -283,7 +279,6 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
           case SK_GROUP: len = waves * (5.0 + 1.0 * P.steps[s].insn_cnt); break;
           case SK_RZ_LOCAL: len = waves * 50.0; break;
           case SK_RZ_MERGE: len = 30.0; break;
-          case SK_RZ_FLAGS: len = 8.0; break;
           case SK_RZ_FINAL: len = waves * 25.0; break;
           case SK_RANK: len = 20.0 + waves * 5.0; break;
           case SK_ARITH: len = 10.0 + waves * 2.0 * P.steps[s].insn_cnt; break;
@@ -313,9 +308,9 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
   }
   const size_t off_items = take(sizeof(WorkItem) * std::max<size_t>(1, items.size()));
   const size_t off_need = take(sizeof(int32_t) * std::max(1, total_steps));
-  // counters: head, done[steps], fcount[rz] -- zeroed before every run
-  const size_t off_counters = take(sizeof(int32_t) * (1 + total_steps + std::max(1, total_rz)));
-  const size_t counters_bytes = sizeof(int32_t) * (1 + total_steps + std::max(1, total_rz));
+  // counters: head, done[steps] -- zeroed before every run
+  const size_t off_counters = take(sizeof(int32_t) * (1 + total_steps));
+  const size_t counters_bytes = sizeof(int32_t) * (1 + total_steps);
   const size_t tables_end = off;
   // buffers
   for (int j = 0; j < n_jobs; ++j) {
@@ -328,15 +323,13 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.off_num = take(sizeof(float) * (size_t)I.H * I.pitch * P.n_num_images);
     I.off_slots = take(mask_bytes * P.n_inter_slots);
     const size_t tstate = (size_t)I.ctiles * ccl_tile_cap_host(I.Wp);
-    // select scratch sets: G, F, flist, tpar, tflag, each 256-byte aligned
+    // select scratch sets: G (2 * P_px keys), tpar, tflag, each 256-byte aligned
     {
       size_t o = 0;
       auto sub = [&](size_t bytes) { o = align_up(o, 256); size_t r = o; o += bytes; return r; };
-      I.set_off[0] = sub(P_px * 4);
-      I.set_off[1] = sub(P_px);
-      I.set_off[2] = sub((size_t)I.flist_cap * 4);
-      I.set_off[3] = sub(tstate * 4);
-      I.set_off[4] = sub(tstate);
+      I.set_off[0] = sub(2 * P_px * 4);
+      I.set_off[1] = sub(tstate * 4);
+      I.set_off[2] = sub(tstate);
       I.set_bytes = align_up(o, 256);
       I.off_rz = take(I.set_bytes * (size_t)P.max_rz_batch);
     }
@@ -430,12 +423,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     d.planes = reinterpret_cast<uint32_t*>(tb + I.off_planes);
     d.rzs = reinterpret_cast<unsigned char*>(tb + I.off_rz);
     d.set_bytes = (int64_t)I.set_bytes;
-    d.off_F = (int64_t)I.set_off[1];
-    d.off_flist = (int64_t)I.set_off[2];
-    d.off_tpar = (int64_t)I.set_off[3];
-    d.off_tflag = (int64_t)I.set_off[4];
-    d.fcount = counters_dev + 1 + total_steps + I.fcount_base;
-    d.flist_cap = I.flist_cap;
+    d.off_tpar = (int64_t)I.set_off[1];
+    d.off_tflag = (int64_t)I.set_off[2];
     d.tile_cap = ccl_tile_cap_host(I.Wp);
     d.status = status_dev + j;
     hj[j] = d;
@@ -664,21 +653,15 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
   CclScratch sc{};
   if (!P.rz.empty()) {
     const size_t px = (size_t)H * W;
-    const int cap = ccl_flist_cap(H, Wp);
     const size_t tiles = (size_t)ccl_tiles_y(H) * ccl_tiles_x(Wp);
     const int tcap = ccl_tile_cap_host(Wp);
     size_t off = 0;
     auto take = [&](size_t b) { off = align_up(off, 256); size_t o = off; off += b; return o; };
-    const size_t oG = take(px * 4), oF = take(px), oL = take((size_t)cap * 4), oC = take(4),
-                 oP = take(tiles * tcap * 4), oT = take(tiles * tcap);
+    const size_t oG = take(2 * px * 4), oP = take(tiles * tcap * 4), oT = take(tiles * tcap);
     if ((e = dev_alloc(ctx, align_up(off, 256), st, &scratch)))
       return cuda_err(ctx, e, "allocating select scratch");
     char* p = static_cast<char*>(scratch->ptr);
     sc.G = reinterpret_cast<int32_t*>(p + oG);
-    sc.F = reinterpret_cast<uint8_t*>(p + oF);
-    sc.flist = reinterpret_cast<int32_t*>(p + oL);
-    sc.fcount = reinterpret_cast<int32_t*>(p + oC);
-    sc.flist_cap = cap;
     sc.tile_cap = tcap;
     sc.tpar = reinterpret_cast<int32_t*>(p + oP);
     sc.tflag = reinterpret_cast<uint8_t*>(p + oT);
@@ -1128,8 +1111,8 @@ VL_API vl_status vl_formula_stats_get(const vl_formula* f, vl_formula_stats* st)
     if (e.op == E_THR || e.op == E_PCT) ch[{e.img, e.ch}] = 1;
   st->n_channels_read = (int32_t)ch.size();
   for (const Insn& in : P.insns) {
-    if (in.op == I_STORE) st->mask_writes++;
-    if (in.op == I_LOAD) st->mask_reads++;
+    if (insn_op(in) == I_STORE) st->mask_writes++;
+    if (insn_op(in) == I_LOAD) st->mask_reads++;
   }
   st->mask_writes += (int64_t)P.rz.size();  // each select writes Z
   st->max_halo = P.max_group_halo;

@@ -680,12 +680,14 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
         r.z_slot = (int16_t)z; r.scratch = (int16_t)j;
         P.rz.push_back(r);
         if (!mat[X[z].a] || !mat[X[z].b]) { *err = "internal: select operand not materialised"; return VL_ERR_INTERNAL; }
-        note_read(X[z].a, base_step + 3);
-        note_read(X[z].b, base_step + 3);
+        note_read(X[z].a, base_step + 2);
+        note_read(X[z].b, base_step + 2);
         mat[z] = 1;
-        def_step[z] = base_step + 3;
+        def_step[z] = base_step + 2;
       }
-      for (int kind = SK_RZ_LOCAL; kind <= SK_RZ_FINAL; ++kind) {
+      // three phases: tile labelling, border merge, select (the seed flags
+      // travel with the union-find keys, so no phase gathers them)
+      for (int kind : {SK_RZ_LOCAL, SK_RZ_MERGE, SK_RZ_FINAL}) {
         StepDesc s{}; s.kind = kind; s.rz_off = rz_off; s.rz_cnt = cnt;
         P.steps.push_back(s);
       }
@@ -813,6 +815,45 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
       P.steps.insert(P.steps.begin(), r);
     }
   }
+  // ---- 5b. block barriers inside groups.  Every instruction but the float
+  // threshold writes (and a store reads) each buffer word from the thread
+  // that owns it -- one fixed owner per buffer word -- so a value read at
+  // its own word right after it was written needs no barrier.  A barrier
+  // (bit I_SYNC of the opcode) goes before an instruction only where a
+  // thread could touch a word another thread touched since the last one:
+  // N reads the neighbours of its operand's words, and the float threshold
+  // writes its words from the lanes that assembled them.  Tracked per
+  // buffer since the last barrier: own-mapped writes, threshold writes,
+  // own-word reads and neighbour reads.
+  for (StepDesc& s : P.steps) {
+    if (s.kind != SK_GROUP) continue;
+    uint64_t w_own = 0, w_thr = 0, r_own = 0, r_nbr = 0;  // <= 64 buffers
+    for (int k = s.insn_off; k < s.insn_off + s.insn_cnt; ++k) {
+      Insn& in = P.insns[k];
+      const uint64_t A = in.op == I_NOT || in.op == I_NEAR || in.op == I_STORE ? 1ull << in.a
+                         : (in.op == I_AND || in.op == I_OR || in.op == I_ANDNOT)
+                             ? (1ull << in.a) | (1ull << in.b)
+                             : 0ull;
+      const uint64_t D = in.op == I_STORE ? 0ull : 1ull << in.dst;
+      bool need;
+      if (in.op == I_NEAR) {
+        if (in.a == in.dst) { *err = "internal: N in place"; return VL_ERR_INTERNAL; }
+        need = (A & (w_own | w_thr)) || (D & (r_nbr | w_thr));
+      } else if (in.op == I_THR) {
+        need = D & (w_own | w_thr | r_own | r_nbr);
+      } else {
+        need = (A & w_thr) || (D & (r_nbr | w_thr));
+      }
+      if (need) {
+        in.op |= I_SYNC;
+        w_own = w_thr = r_own = r_nbr = 0;
+      }
+      if ((in.op & ~I_SYNC) == I_NEAR) r_nbr |= A;
+      else r_own |= A;
+      if ((in.op & ~I_SYNC) == I_THR) w_thr |= D;
+      else w_own |= D;
+    }
+  }
   // ---- 6. number terms run first: everything that compares them waits
   if (!P.arith.empty()) {
     StepDesc a{};
@@ -841,11 +882,12 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
         case SK_GROUP:
           for (int k = s.insn_off; k < s.insn_off + s.insn_cnt; ++k) {
             const Insn& in = P.insns[k];
-            if (in.op == I_LOAD) R[i].push_back(in.slot);
-            if (in.op == I_STORE) Wr[i].push_back(in.slot);
-            if (in.op == I_RTHR) R[i].push_back(ps_rank);
-            if (in.op == I_THR && in.slot >= 0) R[i].push_back(ps_pct);
-            if (in.op == I_THR && in.img >= first_num) R[i].push_back(ps_num);
+            const int op = insn_op(in);
+            if (op == I_LOAD) R[i].push_back(in.slot);
+            if (op == I_STORE) Wr[i].push_back(in.slot);
+            if (op == I_RTHR) R[i].push_back(ps_rank);
+            if (op == I_THR && in.slot >= 0) R[i].push_back(ps_pct);
+            if (op == I_THR && in.img >= first_num) R[i].push_back(ps_num);
           }
           break;
         case SK_PCT:
@@ -880,7 +922,7 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
     for (int i = 0; i < n; ++i) {
       std::vector<int> d;
       const int kind = P.steps[i].kind;
-      if (kind == SK_RZ_MERGE || kind == SK_RZ_FLAGS || kind == SK_RZ_FINAL) d.push_back(i - 1);
+      if (kind == SK_RZ_MERGE || kind == SK_RZ_FINAL) d.push_back(i - 1);
       for (int sl : R[i]) {
         auto it = last_w.find(sl);
         if (it != last_w.end()) d.push_back(it->second);

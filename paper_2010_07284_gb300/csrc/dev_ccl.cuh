@@ -106,11 +106,13 @@ VL_DEV bool s_union(int32_t* par, int a, int b, int cap) {
 // to one of its ancestors: g_union links a node only while it is a root
 // (compare-and-swap), and nodes on the path from x, and the root found, all
 // lie on x's single chain of ancestors, the root above them (ids decrease
-// along the chain).  The final relabelling pass must not compress: there,
-// entries of finished tiles already hold their final labels.
-// npx: pixels of the image (G's length).  An entry outside [0, npx) can
-// only come from corrupted state; it is reported (reason RS_GRANGE) and the
-// walk stops at the last valid node instead of reading out of bounds.
+// along the chain).  In the final labelling pass G is the label array and
+// finished tiles have written their labels into it: the label of every
+// node on a path is the root the path ends at, the value a compression
+// writes there too.
+// npx: entries of G.  An entry outside [0, npx) can only come from
+// corrupted state; it is reported (reason RS_GRANGE) and the walk stops at
+// the last valid node instead of reading out of bounds.
 VL_DEV int g_find(int32_t* G, int x, int npx, int32_t* status, bool compress = true) {
   const int cap = min(npx + 64, 1 << 22);
   if ((unsigned)x >= (unsigned)npx) {
@@ -588,16 +590,33 @@ VL_DEV int pixel_value(const CclSmem& s, int r, int x) {
 }
 
 // Modes of ccl_encode_roots.
-constexpr int ENC_PUBLISH = 0;  // value = representative; publish border roots
-constexpr int ENC_LABEL = 1;    // value = global label (border roots resolved in G)
-constexpr int ENC_SELECT = 2;   // flag bit2 = component selected (rho)
+constexpr int ENC_PUBLISH = 0;     // labels: value = minimum pixel; publish border roots
+constexpr int ENC_PUBLISH_RZ = 1;  // rho: value = key (below); publish border roots
+constexpr int ENC_LABEL = 2;       // value = global label (border roots resolved in G)
+constexpr int ENC_SELECT = 3;      // flag bit2 = component selected (rho)
+
+// Keys of the component select.  A tile-local component is keyed by the
+// first pixel v of its root strip run when it holds a seed pixel, and by
+// v + npx when it does not; G then has 2 * npx entries.  The global merge
+// links the larger root under the smaller, so a merged component's root is
+// a seeded key (< npx) exactly when one of its parts was seeded: the seed
+// flag travels with the union itself and no separate pass has to gather it.
+VL_DEV int rz_key(int v, bool seeded, int npx) { return seeded ? v : v + npx; }
 
 // Visit every local root once (at its start pixel) and replace parent[root]
-// by -(value + 2).  The representative of a component is its minimum pixel
-// (`min_pixel`, for labels) or the first pixel of its root strip run.  Block
-// barrier at the end.
-VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, bool min_pixel, int32_t* G,
-                             uint8_t* F, int32_t* flist, int32_t* fcount, int flist_cap,
+// by -(value + 2).  Block barrier at the end.
+//   ENC_PUBLISH     value = the component's minimum pixel (computed by the
+//                   labelling); border components publish G[value] = value
+//   ENC_PUBLISH_RZ  value = rz_key of the first pixel of the root strip run;
+//                   border components publish G[value] = value
+//   ENC_LABEL       value = the global root of the saved value (border
+//                   components), else the saved value
+//   ENC_SELECT      flag bit2 set when the component is selected: seeded
+//                   locally, or its global root is a seeded key
+// glen: entries of G (npx for labels, 2 * npx for rho).  Finds compress
+// their paths: a node only ever moves to an ancestor, and in the labelling
+// the final label of every node on a path is the root it is moved to.
+VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, int32_t* G, int glen,
                              int npx, int32_t* status) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
@@ -612,25 +631,20 @@ VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, bool min_pi
       const int S = sid(s, k, x);
       if (s.parent[S] >= 0) continue;  // not a root
       const uint8_t fl = s.flag[S];
-      int v = min_pixel ? -s.parent[S] - 2
-                        : (g.r0 + (mbit(s, 2 * k, x) ? 2 * k : 2 * k + 1)) * g.W + 32 * g.w0 + x;
-      if (mode == ENC_PUBLISH) {
-        if (fl & 2) {
-          G[v] = v;
-          if (F) {
-            F[v] = fl & 1;
-            if (fl & 1) {
-              const int q = atomicAdd(fcount, 1);
-              if (q < flist_cap) flist[q] = v;
-              else set_status(status, ST_INTERNAL | RS_FLIST);
-            }
-          }
-        }
-      } else if (mode == ENC_LABEL) {
-        if (fl & 2) v = g_find(G, v, npx, status, false);
+      int v;
+      if (mode == ENC_PUBLISH_RZ) {
+        v = rz_key((g.r0 + (mbit(s, 2 * k, x) ? 2 * k : 2 * k + 1)) * g.W + 32 * g.w0 + x,
+                   fl & 1, npx);
       } else {
-        uint8_t sel = fl & 1;
-        if (fl & 2) sel = ldcg(&F[g_find(G, v, npx, status, false)]);
+        v = -s.parent[S] - 2;
+      }
+      if (mode == ENC_PUBLISH || mode == ENC_PUBLISH_RZ) {
+        if (fl & 2) G[v] = v;
+      } else if (mode == ENC_LABEL) {
+        if (fl & 2) v = g_find(G, v, glen, status);
+      } else {
+        bool sel = fl & 1;
+        if (fl & 2) sel = g_find(G, v, glen, status) < npx;
         if (sel) s.flag[S] = fl | 4;
       }
       s.parent[S] = -(v + 2);
@@ -742,7 +756,7 @@ VL_DEV int window_hit(uint32_t l, uint32_t c, uint32_t r, int b, int conn) {
 // representative in G, so a plain read gives a key without a find); equal
 // key pairs in the warp are united once, by the lowest lane holding them.
 // Must be called by the whole warp.
-VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int npx, int32_t* status) {
+VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int glen, int32_t* status) {
   int ka = 0, kb = 0;
   if (valid) {
     ka = ldcg(&G[a]);
@@ -752,7 +766,7 @@ VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int npx, int32_t* s
   const unsigned long long key =
       valid ? (((unsigned long long)(unsigned)max(ka, kb) << 32) | (unsigned)min(ka, kb)) : ~0ull;
   const unsigned peers = __match_any_sync(FULL, key);
-  if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) g_union(G, ka, kb, npx, status);
+  if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) g_union(G, ka, kb, glen, status);
 }
 
 // Unite the components that touch across the tile border of merge unit
@@ -765,7 +779,7 @@ VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int npx, int32_t* s
 // multiple of 1024 columns, below W).  Padding bits of the loaded words are
 // cleared.  Must be called by the whole warp.
 VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y, int unit,
-                           int conn, int32_t* G, int npx, int32_t* status) {
+                           int conn, int32_t* G, int glen, int32_t* status) {
   const int lane = threadIdx.x & 31;
   const int nh = (tiles_y - 1) * Wp;
   if (unit < nh) {
@@ -783,9 +797,9 @@ VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y,
     const uint32_t su = mu & ~((mu << 1) | (mul >> 31));
     const int x = 32 * w + lane;
     int dx = (sd >> lane) & 1u ? window_hit(mul, mu, mur, lane, conn) : 2;
-    warp_unite(G, dx != 2, yd * W + x, yu * W + x + dx, npx, status);
+    warp_unite(G, dx != 2, yd * W + x, yu * W + x + dx, glen, status);
     dx = (su >> lane) & 1u ? window_hit(mdl, md, mdr, lane, conn) : 2;
-    warp_unite(G, dx != 2, yu * W + x, yd * W + x + dx, npx, status);
+    warp_unite(G, dx != 2, yu * W + x, yd * W + x + dx, glen, status);
   } else {
     const int nv = (H + 31) >> 5;
     const int j = unit - nh;
@@ -807,8 +821,8 @@ VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y,
     // (lane-dependent choices go into the arguments: every lane calls)
     const int a = y * W + x0 - 1;
     const bool straight = R || conn == 4;
-    warp_unite(G, L && (straight ? R : Ru), a, (straight ? y : y - 1) * W + x0, npx, status);
-    warp_unite(G, L && !straight && Rd, a, (y + 1) * W + x0, npx, status);
+    warp_unite(G, L && (straight ? R : Ru), a, (straight ? y : y - 1) * W + x0, glen, status);
+    warp_unite(G, L && !straight && Rd, a, (y + 1) * W + x0, glen, status);
   }
 }
 

@@ -81,11 +81,21 @@ VL_DEV bool rank_stage_begin(const GroupCtx& c) {
 constexpr int kRankMaxBits = 14;
 
 
+// Word ownership: buffer word idx (row-major, idx = row * bw + word) is
+// always read and written by thread idx mod EXEC_THREADS, by every
+// instruction except the float threshold, so that the compiler needs a
+// block barrier (I_SYNC) only where a thread touches a word another thread
+// touched since the previous one.  First word of [lo, ...) this thread owns.
+VL_DEV int own_first(int lo, int tid) {
+  return lo <= tid ? tid : tid + ((lo - tid + EXEC_THREADS - 1) / EXEC_THREADS) * EXEC_THREADS;
+}
+
 // BH, BW > 0: the buffer shape as compile-time constants (index arithmetic
 // and divisions by the row length fold into multiplies); 0: read from c.
+// Launched with EXEC_THREADS threads.
 template <int BH, int BW>
 VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x, nthr = EXEC_THREADS;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   const int bw = BW > 0 ? BW : c.bw;
   const int bhbw = (BH > 0 ? BH : c.bh) * bw;
@@ -94,10 +104,13 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
   int stage = rank_stage_begin(c) ? 1 : 0;
   for (int k = 0; k < n_insn; ++k) {
     const Insn I = insns[k];
+    if (I.op & I_SYNC) __syncthreads();  // uniform: one instruction stream per CTA
+    const int op = I.op & ~I_SYNC;
     const int h = I.h;
     const int i_lo = c.halo - h, i_hi = c.halo + c.th + h;  // buffer rows
     const int rows = i_hi - i_lo;
-    if (I.op == I_RTHR) {
+    const int w_lo = i_lo * bw, w_hi = i_hi * bw;           // buffer words
+    if (op == I_RTHR) {
       if (stage == 1) {  // uniform: every thread waits for its copies, then all
         cp_async_wait_all();
         __syncthreads();
@@ -110,9 +123,8 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
       const uint32_t* sp = c.stage + rank_stage_words(c, I.a);
       const int s_row0 = c.halo - c.rank_halo;  // buffer row of stage row 0
       uint32_t* d = gbuf(I.dst);
-      const int nwords = rows * bw;
-      for (int idx = tid; idx < nwords; idx += nthr) {
-        const int i = i_lo + idx / bw, j = idx - (idx / bw) * bw;
+      for (int idx = own_first(w_lo, tid); idx < w_hi; idx += nthr) {
+        const int i = idx / bw, j = idx - (idx / bw) * bw;
         const int y = c.r0 - c.halo + i, wg = c.w0 - 1 + j;
         uint32_t word = 0;
         if (y >= 0 && y < c.H && wg >= 0 && wg < c.Wp) {
@@ -152,9 +164,9 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
           word = lt ? (~ge & ~nan) : ge;
           word &= vmask(wg, c.W);
         }
-        d[i * bw + j] = word;
+        d[idx] = word;
       }
-    } else if (I.op == I_THR) {
+    } else if (op == I_THR) {
       const DevImage im = c.images[I.img];
       const void* plane = chan_ptr(im, I.ch, (size_t)c.H * c.pitch);
       const int fmt = im.format;
@@ -231,27 +243,27 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
           }
         }
       }
-    } else if (I.op == I_STORE) {
+    } else if (op == I_STORE) {
+      // the core words, each from the thread that owns it in the buffer
       const uint32_t* a = gbuf(I.a);
       uint32_t* g = c.slots[I.slot];
-      const int nwords = c.th * c.tww;
-      for (int idx = tid; idx < nwords; idx += nthr) {
-        int r = idx / c.tww, w = idx - r * c.tww;
-        g[(size_t)(c.r0 + r) * c.Wp + c.w0 + w] = a[(c.halo + r) * bw + 1 + w];
+      const int s_hi = (c.halo + c.th) * bw;
+      for (int idx = own_first(c.halo * bw, tid); idx < s_hi; idx += nthr) {
+        const int i = idx / bw, j = idx - (idx / bw) * bw;
+        if (j >= 1 && j <= c.tww) g[(size_t)(c.r0 + i - c.halo) * c.Wp + c.w0 + j - 1] = a[idx];
       }
     } else {
       uint32_t* d = gbuf(I.dst);
       const uint32_t* a = gbuf(I.a);
       const uint32_t* b = gbuf(I.b);
-      const uint32_t* g = (I.op == I_LOAD) ? c.slots[I.slot] : nullptr;
-      const int nwords = rows * bw;
-      for (int idx = tid; idx < nwords; idx += nthr) {
-        int i = i_lo + idx / bw, j = idx - (idx / bw) * bw;
-        int y = c.r0 - c.halo + i, wg = c.w0 - 1 + j;
+      const uint32_t* g = (op == I_LOAD) ? c.slots[I.slot] : nullptr;
+      for (int idx = own_first(w_lo, tid); idx < w_hi; idx += nthr) {
+        const int i = idx / bw, j = idx - (idx / bw) * bw;
+        const int y = c.r0 - c.halo + i, wg = c.w0 - 1 + j;
         uint32_t word = 0;
         if (y >= 0 && y < c.H && wg >= 0 && wg < c.Wp) {
-          const int o = i * bw + j;
-          switch (I.op) {
+          const int o = idx;
+          switch (op) {
             case I_LOAD: word = ldcg(&g[(size_t)y * c.Wp + wg]); break;
             case I_NOT: word = ~a[o] & vmask(wg, c.W); break;
             case I_AND: word = a[o] & b[o]; break;
@@ -269,10 +281,9 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
             default: break;
           }
         }
-        d[i * bw + j] = word;
+        d[idx] = word;
       }
     }
-    __syncthreads();
   }
   if (stage == 1) cp_async_wait_all();  // no copy may outlive the tile
 }

@@ -172,14 +172,12 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       uint8_t* tflag = rz_tflag(J, k) + (size_t)tile * J.tile_cap;
       if (S.kind == SK_RZ_LOCAL) {
         if (!ccl_tile_label(s, phi2, phi1, geo, J.conn, false, J.status)) break;
-        ccl_encode_roots(s, geo, ENC_PUBLISH, false, rz_G(J, k), rz_F(J, k), rz_flist(J, k),
-                         J.fcount + S.rz_off + j, J.flist_cap, npx, J.status);
+        ccl_encode_roots(s, geo, ENC_PUBLISH_RZ, rz_G(J, k), 2 * npx, npx, J.status);
         ccl_publish_border(s, geo, rz_G(J, k));
         ccl_tile_save(s, tpar, tflag);
       } else {
         if (!ccl_tile_load(s, phi2, geo, J.conn, tpar, tflag, J.status)) break;
-        ccl_encode_roots(s, geo, ENC_SELECT, true, rz_G(J, k), rz_F(J, k), nullptr, nullptr, 0, npx,
-                         J.status);
+        ccl_encode_roots(s, geo, ENC_SELECT, rz_G(J, k), 2 * npx, npx, J.status);
         ccl_write_select(s, geo, J.slots[r.z_slot]);
       }
       break;
@@ -191,18 +189,7 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       const int nw = blockDim.x >> 5;
       for (int u = chunk * nw + (threadIdx.x >> 5); u < n; u += per_rz * nw)
         ccl_merge_unit(J.slots[r.phi2_slot], J.H, J.W, J.Wp, J.c_tiles_y, u, J.conn,
-                       rz_G(J, r.scratch), npx, J.status);
-      break;
-    }
-    case SK_RZ_FLAGS: {
-      const int j = sub / per_rz, chunk = sub - j * per_rz;
-      const RzDesc r = J.rz[S.rz_off + j];
-      const int n = min(ldcg(J.fcount + S.rz_off + j), J.flist_cap);
-      int32_t* G = rz_G(J, r.scratch);
-      uint8_t* F = rz_F(J, r.scratch);
-      const int32_t* fl = rz_flist(J, r.scratch);
-      for (int i = chunk * blockDim.x + threadIdx.x; i < n; i += per_rz * blockDim.x)
-        F[g_find(G, ldcg(fl + i), npx, J.status)] = 1;
+                       rz_G(J, r.scratch), 2 * npx, J.status);
       break;
     }
     default:
@@ -256,7 +243,8 @@ __global__ void __launch_bounds__(EXEC_THREADS, 2) k_exec(ExecLaunch L) {
     __syncthreads();
     if (!s_skip) {
       int per_rz = 1;
-      if (S.kind >= SK_RZ_LOCAL && S.kind <= SK_RZ_FINAL) per_rz = L.need[ci] / S.rz_cnt;
+      if (S.kind == SK_RZ_LOCAL || S.kind == SK_RZ_MERGE || S.kind == SK_RZ_FINAL)
+        per_rz = L.need[ci] / S.rz_cnt;
       for (int k = 0; k < it.count; ++k) {
         run_subitem(J, S, it.first + k, per_rz, smem_raw, L);
         __syncthreads();

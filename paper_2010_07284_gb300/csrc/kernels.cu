@@ -139,29 +139,22 @@ k_ccl_local(const uint32_t* mask, const uint32_t* phi1, MaskGeom g, int tiles_x,
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
   const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x);
   const int npx = g.H * g.W;
-  const bool labels = sc.F == nullptr;  // full labelling: canonical minimum pixel
+  const bool labels = phi1 == nullptr;  // full labelling: canonical minimum pixel
   if (!ccl_tile_label(s, mask, phi1, geo, conn, labels, status)) return;
-  ccl_encode_roots(s, geo, ENC_PUBLISH, labels, sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap,
+  ccl_encode_roots(s, geo, labels ? ENC_PUBLISH : ENC_PUBLISH_RZ, sc.G, labels ? npx : 2 * npx,
                    npx, status);
   ccl_publish_border(s, geo, sc.G);
   ccl_tile_save(s, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
                 sc.tflag + (size_t)blockIdx.x * sc.tile_cap);
 }
 
+// glen: entries of G (H*W for labels, 2*H*W for rho keys).
 __global__ void k_ccl_merge(const uint32_t* mask, MaskGeom g, int tiles_y, int tiles_x,
-                            int conn, int32_t* G, int32_t* status) {
+                            int conn, int32_t* G, int glen, int32_t* status) {
   const int n = merge_units(g.H, g.Wp, tiles_y, tiles_x);
-  const int npx = g.H * g.W;
   const int wpb = blockDim.x >> 5;
   for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n; u += gridDim.x * wpb)
-    ccl_merge_unit(mask, g.H, g.W, g.Wp, tiles_y, u, conn, G, npx, status);
-}
-
-__global__ void k_ccl_flags(int32_t* G, uint8_t* F, const int32_t* flist,
-                            const int32_t* fcount, int flist_cap, int npx, int32_t* status) {
-  const int n = min(*fcount, flist_cap);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    F[g_find(G, flist[i], npx, status)] = 1;
+    ccl_merge_unit(mask, g.H, g.W, g.Wp, tiles_y, u, conn, G, glen, status);
 }
 
 __global__ void __launch_bounds__(EXEC_THREADS, 2)
@@ -174,7 +167,7 @@ k_ccl_final_labels(const uint32_t* mask, MaskGeom g, int tiles_x, int conn, CclS
   if (!ccl_tile_load(s, mask, geo, conn, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
                      sc.tflag + (size_t)blockIdx.x * sc.tile_cap, status))
     return;
-  ccl_encode_roots(s, geo, ENC_LABEL, true, sc.G, nullptr, nullptr, nullptr, 0, npx, status);
+  ccl_encode_roots(s, geo, ENC_LABEL, sc.G, npx, npx, status);
   ccl_write_labels(s, geo, sc.G);
 }
 
@@ -188,7 +181,7 @@ k_rz_final(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int tiles_x, 
   if (!ccl_tile_load(s, phi2, geo, conn, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
                      sc.tflag + (size_t)blockIdx.x * sc.tile_cap, status))
     return;
-  ccl_encode_roots(s, geo, ENC_SELECT, true, sc.G, sc.F, nullptr, nullptr, 0, npx, status);
+  ccl_encode_roots(s, geo, ENC_SELECT, sc.G, 2 * npx, npx, status);
   ccl_write_select(s, geo, Z);
 }
 
@@ -288,9 +281,6 @@ cudaError_t launch_arith(int op, const void* a, int a_format, const void* b, int
 
 int ccl_tiles_y(int H) { return (H + CCL_TH - 1) / CCL_TH; }
 int ccl_tiles_x(int Wp) { return (Wp + CCL_TWW - 1) / CCL_TWW; }
-int ccl_flist_cap(int H, int Wp) {
-  return ccl_tiles_y(H) * ccl_tiles_x(Wp) * (2 * 32 * CCL_TWW + 2 * CCL_TH);
-}
 size_t ccl_smem_bytes() { return sizeof(CclSmem); }
 
 // The labelling kernels need more than 48 KB of dynamic shared memory; the
@@ -332,17 +322,13 @@ cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScr
   if (e) return e;
   const int ty = ccl_tiles_y(g.H), tx = ccl_tiles_x(g.Wp);
   const size_t sm = sizeof(CclSmem);
-  sc.F = nullptr;
-  sc.flist = nullptr;
-  sc.fcount = nullptr;
-  sc.flist_cap = 0;
   int32_t* labels = sc.G;
   k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, nullptr, g, tx, conn, sc, status);
   if ((e = cudaGetLastError())) return e;
   const long long nm = ccl_merge_units(g.H, g.Wp) * 32LL;
   if (nm > 0) {
     k_ccl_merge<<<grid_for(nm, kThreads), kThreads, 0, st>>>(mask, g, ty, tx, conn, labels,
-                                                             status);
+                                                             g.H * g.W, status);
     if ((e = cudaGetLastError())) return e;
   }
   k_ccl_final_labels<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, g, tx, conn, sc, status);
@@ -355,19 +341,14 @@ cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, in
   if (e) return e;
   const int ty = ccl_tiles_y(g.H), tx = ccl_tiles_x(g.Wp);
   const size_t sm = sizeof(CclSmem);
-  const int npx = g.H * g.W;
-  if ((e = cudaMemsetAsync(sc.fcount, 0, sizeof(int32_t), st))) return e;
   k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(phi2, phi1, g, tx, conn, sc, status);
   if ((e = cudaGetLastError())) return e;
   const long long nm = ccl_merge_units(g.H, g.Wp) * 32LL;
   if (nm > 0) {
     k_ccl_merge<<<grid_for(nm, kThreads), kThreads, 0, st>>>(phi2, g, ty, tx, conn, sc.G,
-                                                             status);
+                                                             2 * g.H * g.W, status);
     if ((e = cudaGetLastError())) return e;
   }
-  k_ccl_flags<<<grid_for(sc.flist_cap, kThreads), kThreads, 0, st>>>(
-      sc.G, sc.F, sc.flist, sc.fcount, sc.flist_cap, npx, status);
-  if ((e = cudaGetLastError())) return e;
   k_rz_final<<<ty * tx, EXEC_THREADS, sm, st>>>(phi1, phi2, g, tx, conn, sc, Z, status);
   return cudaGetLastError();
 }

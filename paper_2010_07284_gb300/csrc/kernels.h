@@ -35,18 +35,15 @@ cudaError_t launch_arith(int op, const void* a, int a_format, const void* b, int
 
 // ---- connected components (tile-local, merge, flags, final) ----
 struct CclScratch {
-  int32_t* G;       // H*W int32 (union-find by gid); may alias the labels
-  uint8_t* F;       // H*W bytes (component flags), rho only
-  int32_t* flist;   // flagged border roots, rho only
-  int32_t* fcount;  // its length (zeroed by the caller before the local pass)
-  int32_t flist_cap;
+  int32_t* G;       // union-find: H*W int32 for labels (the label array
+                    // itself), 2*H*W for rho (pixel ids, then the keys of
+                    // unseeded components)
   int32_t tile_cap; // per-tile capacity of tpar / tflag (ccl_tile_cap_host)
   int32_t* tpar;    // tiles * tile_cap int32: saved tile union-find state
   uint8_t* tflag;   // tiles * tile_cap bytes: saved tile flags
 };
 int ccl_tiles_y(int H);
 int ccl_tiles_x(int Wp);
-int ccl_flist_cap(int H, int Wp);
 int ccl_tile_cap_host(int Wp);
 // Border merge units (one warp each): words of horizontal tile borders and
 // 32-row pieces of vertical ones.

@@ -55,8 +55,7 @@ int64_t estimate_bytes(const Plan& P, int H, int W) {
   const size_t tstate = tiles * ccl_tile_cap_host(Wp);
   size_t b = align256(mask * (P.n_inter_slots + P.n_root_slots));
   b += (size_t)P.max_rz_batch *
-       (align256(px * 4) + align256(px) + align256((size_t)ccl_flist_cap(H, Wp) * 4) +
-        align256(tstate * 4) + align256(tstate));
+       (align256(2 * px * 4) + align256(tstate * 4) + align256(tstate));
   b += align256(sizeof(Insn) * P.insns.size()) + align256(sizeof(StepDesc) * P.steps.size()) +
        64 * 1024;
   return (int64_t)b;

@@ -34,7 +34,7 @@ constexpr int ST_INTERNAL = 8;
 // ST_INTERNAL in the low byte).
 constexpr int RS_GFIND = 1 << 8;     // global find ran past its bound
 constexpr int RS_GUNION = 2 << 8;    // global union ran past its bound
-constexpr int RS_FLIST = 3 << 8;     // flagged-root list overflow
+constexpr int RS_FLIST = 3 << 8;     // (unused: no flagged-root list any more)
 constexpr int RS_TLOAD = 4 << 8;     // saved tile state out of range
 constexpr int RS_TRUNS = 5 << 8;     // more strip runs than a tile holds
 constexpr int RS_SUNION = 6 << 8;    // shared union-find ran past its bound
@@ -61,8 +61,13 @@ enum InsnOp : uint8_t {
                  //   bit0: lt (see RankTab)
 };
 
+// Bit of Insn::op: a block barrier precedes the instruction (the compiler
+// places one only where a thread may touch a buffer word that another
+// thread touched since the previous barrier).
+constexpr uint8_t I_SYNC = 0x80;
+
 struct Insn {        // 16 bytes
-  uint8_t op;
+  uint8_t op;        // InsnOp, with I_SYNC
   uint8_t dst;
   uint8_t a;
   uint8_t b;
@@ -73,6 +78,7 @@ struct Insn {        // 16 bytes
   float t;           // threshold constant (THR)
 };
 static_assert(sizeof(Insn) == 16, "Insn layout");
+VL_HD_INLINE int insn_op(const Insn& in) { return in.op & ~I_SYNC; }
 
 // -------------------------------------------------------------- plan steps
 enum StepKind : int32_t {
@@ -80,7 +86,7 @@ enum StepKind : int32_t {
   SK_GROUP = 1,      // fused pointwise/N tile group: one item per tile
   SK_RZ_LOCAL = 2,   // rho batch, tile-local labelling + publish: item = (rz, tile)
   SK_RZ_MERGE = 3,   // rho batch, union across tile borders: item = (rz, chunk)
-  SK_RZ_FLAGS = 4,   // rho batch, flags to global roots: item = (rz, chunk)
+  SK_RZ_UNUSED = 4,  // (no longer emitted: the seed flag travels with the keys)
   SK_RZ_FINAL = 5,   // rho batch, relabel + write Z: item = (rz, tile)
   SK_RANK = 6,       // rank codes of threshold tables: item = (table, row block)
   SK_ARITH = 7,      // number terms: item = row block, writes the number images
@@ -189,14 +195,14 @@ struct DevJob {
   const PctDesc* pct;
   float* pct_val;               // percentile values by slot
   // CCL scratch sets, one per select of a batch step, `set_bytes` apart:
-  // union-find over gids (G), component flags by gid (F), flagged border
-  // roots (flist), saved tile union-find state and flags (tiles x tile_cap)
+  // union-find over keys (G, 2 * H * W entries: pixel ids and the keys of
+  // unseeded components), saved tile union-find state and flags (tiles x
+  // tile_cap)
   unsigned char* rzs;
   int64_t set_bytes;
-  int64_t off_F, off_flist, off_tpar, off_tflag;
-  int32_t* fcount;              // flagged-root count per select (zeroed per launch)
-  int32_t flist_cap;
+  int64_t off_tpar, off_tflag;
   int32_t tile_cap;
+  int32_t pad0_;
   int32_t* status;              // device status word of this job
   const RankTab* rtab;          // rank tables of the formula
   const float* rvals;           //   their sorted threshold values
@@ -210,10 +216,6 @@ struct DevJob {
 
 VL_HD_INLINE int32_t* rz_G(const DevJob& J, int k) {
   return reinterpret_cast<int32_t*>(J.rzs + k * J.set_bytes);
-}
-VL_HD_INLINE uint8_t* rz_F(const DevJob& J, int k) { return J.rzs + k * J.set_bytes + J.off_F; }
-VL_HD_INLINE int32_t* rz_flist(const DevJob& J, int k) {
-  return reinterpret_cast<int32_t*>(J.rzs + k * J.set_bytes + J.off_flist);
 }
 VL_HD_INLINE int32_t* rz_tpar(const DevJob& J, int k) {
   return reinterpret_cast<int32_t*>(J.rzs + k * J.set_bytes + J.off_tpar);
