@@ -104,7 +104,7 @@ bool valid(const void* h, uint32_t tag) {
 
 // Check the images of a job against a plan; returns shape in H, W.
 vl_status check_job_images(vl_context* ctx, const Plan& P, vl_image* const* imgs, int n_imgs,
-                           int* H, int* W) {
+                           int* H, int* W, int* D = nullptr) {
   if (n_imgs < (int)P.img_kind.size())
     return set_err(ctx, VL_ERR_ARG, "formula reads image " + std::to_string(P.img_kind.size() - 1) +
                                         " but only " + std::to_string(n_imgs) + " were given");
@@ -114,8 +114,8 @@ vl_status check_job_images(vl_context* ctx, const Plan& P, vl_image* const* imgs
     const vl_image* im = imgs[i];
     if (!valid(im, TAG_IMG)) return set_err(ctx, VL_ERR_ARG, "bad image handle " + std::to_string(i));
     if (h < 0) { h = im->H; w = im->W; }
-    if (im->H != h || im->W != w)
-      return set_err(ctx, VL_ERR_SHAPE, "images of one evaluation must share H x W");
+    if (im->H != h || im->W != w || im->D != imgs[0]->D)
+      return set_err(ctx, VL_ERR_SHAPE, "images of one evaluation must share D x H x W");
     if (i < (int)P.img_kind.size()) {
       if (P.img_kind[i] == 1 && (im->is_mask || im->C < P.img_channels[i]))
         return set_err(ctx, VL_ERR_SHAPE, "image " + std::to_string(i) +
@@ -128,10 +128,16 @@ vl_status check_job_images(vl_context* ctx, const Plan& P, vl_image* const* imgs
   // union-find holds 2 * H * W int32 entries
   if (!P.rz.empty() && (long long)h * w > (1LL << 30))
     return set_err(ctx, VL_ERR_SHAPE, "reachability needs images of at most 2^30 pixels");
+  if (imgs[0]->D > 1 && P.conn != 6 && P.conn != 26)
+    return set_err(ctx, VL_ERR_SHAPE, "a volume needs a formula compiled with adjacency 6 or 26");
   *H = h;
   *W = w;
+  if (D) *D = imgs[0]->D;
   return VL_OK;
 }
+
+// Formulas over volumes (adjacency 6 or 26) run in the per-operator form.
+inline bool volume_plan(const Plan& P) { return P.conn == 6 || P.conn == 26; }
 
 int ccl_merge_chunks(int H, int Wp) {
   const long long n = ccl_merge_units(H, Wp);  // one warp each
@@ -190,6 +196,10 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     if (!valid(f, TAG_FML)) return set_err(ctx, VL_ERR_ARG, "bad formula handle in job " + std::to_string(j));
     if (f->pp.group_buffers != ctx->pp.group_buffers || f->pp.hmax != ctx->pp.hmax)
       return set_err(ctx, VL_ERR_ARG, "formula was planned for another tile configuration");
+    if (volume_plan(f->plan))
+      return set_err(ctx, VL_ERR_ARG, "job " + std::to_string(j) +
+                                          ": formulas over volumes (adjacency 6 or 26) run in the "
+                                          "per-operator form (vl_eval)");
     vl_status s = check_job_images(ctx, f->plan, jobs[j].images, jobs[j].n_images, &J[j].H, &J[j].W);
     if (s != VL_OK) return s;
     J[j].P = &f->plan;
@@ -290,6 +300,9 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& a, const Pair& b) { return a.t < b.t; });
     // with work for many waves (thousands of small images), items of short
     // tiles are merged up to ~40 us so that popping stays cheap beside work
+    // -- but only as far as the jobs running side by side still offer four
+    // items per CTA: the steps of one job mostly wait on each other, and
+    // merging the tiles of a step there only serialises them on fewer CTAs
     long long subitems = 0;
     for (const Pair& p : pairs) subitems += J[p.j].need[p.s];
     const bool plenty = subitems > 32LL * grid;
@@ -300,7 +313,9 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
         const StepDesc& sd = J[p.j].P->steps[p.s];
         const double tile_us = sd.kind == SK_GROUP ? 5.0 + 1.0 * sd.insn_cnt
                                : sd.kind == SK_RZ_FINAL ? 20.0 : 40.0;
-        chunk = std::max(chunk, std::min(n, (int)std::ceil(40.0 / tile_us)));
+        const long long side_by_side = std::max<long long>(1, (long long)n * n_jobs / (4LL * grid));
+        chunk = std::max<long long>(chunk, std::min<long long>(
+            {(long long)n, (long long)std::ceil(40.0 / tile_us), side_by_side}));
       }
       for (int first = 0; first < n; first += chunk)
         items.push_back(WorkItem{p.j, p.s, first, std::min(chunk, n - first)});
@@ -331,7 +346,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
       I.set_off[1] = sub(tstate * 4);
       I.set_off[2] = sub(tstate);
       I.set_bytes = align_up(o, 256);
-      I.off_rz = take(I.set_bytes * (size_t)P.max_rz_batch);
+      I.off_rz = take(I.set_bytes * (size_t)P.n_scratch_sets);
     }
   }
   const size_t trans_bytes = align_up(off, 256);
@@ -577,11 +592,13 @@ namespace {
 vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs, int n_imgs,
                      cudaStream_t st, vl_result** out) {
   const Plan& P = f->plan;
-  int H, W;
-  vl_status s = check_job_images(ctx, P, imgs, n_imgs, &H, &W);
+  int H, W, D;
+  vl_status s = check_job_images(ctx, P, imgs, n_imgs, &H, &W, &D);
   if (s != VL_OK) return s;
   const int Wp = words_per_row(W), pitch = 32 * Wp;
-  const MaskGeom g{H, W, Wp};
+  const bool vol = volume_plan(P);
+  MaskGeom g{H, W, Wp};
+  if (vol) g.Hs = H / D;
   const size_t mask_bytes = (size_t)H * Wp * 4;
   cudaError_t e;
   if ((e = wait_images(imgs, n_imgs, st))) return cuda_err(ctx, e, "waiting for image uploads");
@@ -651,7 +668,26 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
   // rho scratch
   DevBlockPtr scratch;
   CclScratch sc{};
-  if (!P.rz.empty()) {
+  Rz3Scratch sc3{};
+  if (!P.rz.empty() && vol) {
+    // labels of phi2, a flag per component, the seed voxels, tile state
+    const size_t px = (size_t)H * W;
+    const size_t tiles = (size_t)ccl_tiles_y(H, g.Hs) * ccl_tiles_x(Wp);
+    const int tcap = ccl_tile_cap_host(Wp);
+    size_t off = 0;
+    auto take = [&](size_t b) { off = align_up(off, 256); size_t o = off; off += b; return o; };
+    const size_t oL = take(px * 4), oF = take(px), oS = take(mask_bytes), oP = take(tiles * tcap * 4),
+                 oT = take(tiles * tcap);
+    if ((e = dev_alloc(ctx, align_up(off, 256), st, &scratch)))
+      return cuda_err(ctx, e, "allocating select scratch");
+    char* p = static_cast<char*>(scratch->ptr);
+    sc3.ccl.G = reinterpret_cast<int32_t*>(p + oL);
+    sc3.ccl.tile_cap = tcap;
+    sc3.ccl.tpar = reinterpret_cast<int32_t*>(p + oP);
+    sc3.ccl.tflag = reinterpret_cast<uint8_t*>(p + oT);
+    sc3.F = reinterpret_cast<uint8_t*>(p + oF);
+    sc3.seed = reinterpret_cast<uint32_t*>(p + oS);
+  } else if (!P.rz.empty()) {
     const size_t px = (size_t)H * W;
     const size_t tiles = (size_t)ccl_tiles_y(H) * ccl_tiles_x(Wp);
     const int tcap = ccl_tile_cap_host(Wp);
@@ -705,9 +741,14 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
       case E_AND: e = launch_and(val[x.a], val[x.b], g, o, st); break;
       case E_OR: e = launch_or(val[x.a], val[x.b], g, o, st); break;
       case E_ANDNOT: e = launch_andnot(val[x.a], val[x.b], g, o, st); break;
-      case E_NEAR: e = launch_near(val[x.a], g, P.conn, o, st); break;
+      case E_NEAR:
+        e = vol ? launch_near3(val[x.a], g, P.conn, o, st) : launch_near(val[x.a], g, P.conn, o, st);
+        break;
       case E_COPY: e = cudaMemcpyAsync(o, val[x.a], mask_bytes, cudaMemcpyDeviceToDevice, st); break;
-      case E_RZ: e = launch_rz(val[x.a], val[x.b], g, P.conn, sc, o, status, st); break;
+      case E_RZ:
+        e = vol ? launch_rz3(val[x.a], val[x.b], g, P.conn, sc3, o, status, st)
+                : launch_rz(val[x.a], val[x.b], g, P.conn, sc, o, status, st);
+        break;
       default: return set_err(ctx, VL_ERR_INTERNAL, "plain form: unknown node");
     }
     if (e) return cuda_err(ctx, e, "launching a plain operator");
@@ -722,6 +763,7 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
   auto* r = new vl_result();
   r->ctx = ctx;
   r->H = H; r->W = W; r->Wp = Wp;
+  r->D = D;
   r->n_roots = P.n_roots;
   for (int q = 0; q < P.n_roots; ++q) r->roots.push_back(root_buf(P.root_slot[q]));
   r->status = status;
@@ -867,10 +909,14 @@ VL_API void vl_free(void* h) {
 
 // ---------------------------------------------------------------- images
 
-static vl_status image_common(vl_context* ctx, int32_t h, int32_t w, int32_t c) {
+// max_rows: 65535 for an image; a volume stores depth x height rows, up to
+// 2^20 of them.
+static vl_status image_common(vl_context* ctx, int32_t h, int32_t w, int32_t c,
+                              int32_t max_rows = 65535) {
   if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
-  if (h < 1 || w < 1 || c < 1 || h > 65535 || w > 65535 || c > 4096)
-    return set_err(ctx, VL_ERR_ARG, "image sides must be in [1, 65535], channels in [1, 4096]");
+  if (h < 1 || w < 1 || c < 1 || h > max_rows || w > 65535 || c > 4096)
+    return set_err(ctx, VL_ERR_ARG, "image sides must be in [1, 65535] (a volume's depth x height "
+                                    "in [1, 2^20]), channels in [1, 4096]");
   if ((long long)h * w > 0x7FFFFFFFLL)
     return set_err(ctx, VL_ERR_ARG, "image has more than 2^31 - 1 pixels");
   return VL_OK;
@@ -878,8 +924,8 @@ static vl_status image_common(vl_context* ctx, int32_t h, int32_t w, int32_t c) 
 
 static vl_status image_create(vl_context* ctx, int32_t h, int32_t w, int32_t channels,
                               const void* data, int format, int32_t data_on_device, void* stream,
-                              vl_image** out) {
-  vl_status s = image_common(ctx, h, w, channels);
+                              vl_image** out, int32_t max_rows = 65535) {
+  vl_status s = image_common(ctx, h, w, channels, max_rows);
   if (s != VL_OK) return s;
   if (!data || !out) return set_err(ctx, VL_ERR_ARG, "null data or output");
   DeviceGuard dg(ctx->device);
@@ -918,9 +964,10 @@ VL_API vl_status vl_image_create_u16(vl_context* ctx, int32_t h, int32_t w, int3
   return image_create(ctx, h, w, channels, data, PX_U16, data_on_device, stream, out);
 }
 
-VL_API vl_status vl_mask_create(vl_context* ctx, int32_t h, int32_t w, const uint8_t* data,
-                                int32_t data_on_device, void* stream, vl_image** out) {
-  vl_status s = image_common(ctx, h, w, 1);
+static vl_status mask_create(vl_context* ctx, int32_t h, int32_t w, const uint8_t* data,
+                             int32_t data_on_device, void* stream, vl_image** out,
+                             int32_t max_rows) {
+  vl_status s = image_common(ctx, h, w, 1, max_rows);
   if (s != VL_OK) return s;
   if (!data || !out) return set_err(ctx, VL_ERR_ARG, "null data or output");
   DeviceGuard dg(ctx->device);
@@ -945,6 +992,11 @@ VL_API vl_status vl_mask_create(vl_context* ctx, int32_t h, int32_t w, const uin
   if ((e = record_ready(im.get(), S(stream)))) return cuda_err(ctx, e, "recording an event");
   *out = im.release();
   return VL_OK;
+}
+
+VL_API vl_status vl_mask_create(vl_context* ctx, int32_t h, int32_t w, const uint8_t* data,
+                                int32_t data_on_device, void* stream, vl_image** out) {
+  return mask_create(ctx, h, w, data, data_on_device, stream, out, 65535);
 }
 
 VL_API vl_status vl_mask_create_packed(vl_context* ctx, int32_t h, int32_t w, const uint32_t* words,
@@ -986,6 +1038,60 @@ VL_API vl_status vl_image_info(const vl_image* img, int32_t* h, int32_t* w, int3
 VL_API vl_status vl_image_format(const vl_image* img, int32_t* format) {
   if (!valid(img, TAG_IMG) || img->is_mask) return VL_ERR_ARG;
   if (format) *format = img->format;
+  return VL_OK;
+}
+
+// Volumes: D slices of h x w stored as one image of D * h rows.
+constexpr int32_t kVolumeMaxRows = 1 << 20;
+
+static vl_status volume_common(vl_context* ctx, int32_t d, int32_t h) {
+  if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
+  if (d < 1 || h < 1 || (long long)d * h > kVolumeMaxRows)
+    return set_err(ctx, VL_ERR_ARG, "a volume needs depth >= 1 and depth x height <= 2^20");
+  return VL_OK;
+}
+
+static vl_status as_volume(vl_status s, int32_t d, vl_image** out) {
+  if (s == VL_OK) (*out)->D = d;
+  return s;
+}
+
+VL_API vl_status vl_volume_create(vl_context* ctx, int32_t d, int32_t h, int32_t w, int32_t channels,
+                                  const float* data, int32_t data_on_device, void* stream,
+                                  vl_image** out) {
+  vl_status s = volume_common(ctx, d, h);
+  if (s != VL_OK) return s;
+  return as_volume(image_create(ctx, d * h, w, channels, data, PX_F32, data_on_device, stream, out,
+                                kVolumeMaxRows), d, out);
+}
+
+VL_API vl_status vl_volume_create_u16(vl_context* ctx, int32_t d, int32_t h, int32_t w,
+                                      int32_t channels, const uint16_t* data,
+                                      int32_t data_on_device, void* stream, vl_image** out) {
+  vl_status s = volume_common(ctx, d, h);
+  if (s != VL_OK) return s;
+  return as_volume(image_create(ctx, d * h, w, channels, data, PX_U16, data_on_device, stream, out,
+                                kVolumeMaxRows), d, out);
+}
+
+VL_API vl_status vl_mask_volume_create(vl_context* ctx, int32_t d, int32_t h, int32_t w,
+                                       const uint8_t* data, int32_t data_on_device, void* stream,
+                                       vl_image** out) {
+  vl_status s = volume_common(ctx, d, h);
+  if (s != VL_OK) return s;
+  return as_volume(mask_create(ctx, d * h, w, data, data_on_device, stream, out, kVolumeMaxRows), d,
+                   out);
+}
+
+VL_API vl_status vl_image_depth(const vl_image* img, int32_t* d) {
+  if (!valid(img, TAG_IMG) || !d) return VL_ERR_ARG;
+  *d = img->D;
+  return VL_OK;
+}
+
+VL_API vl_status vl_result_depth(const vl_result* r, int32_t* d) {
+  if (!valid(r, TAG_RES) || !d) return VL_ERR_ARG;
+  *d = r->D;
   return VL_OK;
 }
 
@@ -1130,8 +1236,11 @@ VL_API vl_status vl_eval_mode(vl_context* ctx, const vl_formula* f, vl_image* co
   if (f->pp.group_buffers != ctx->pp.group_buffers || f->pp.hmax != ctx->pp.hmax)
     return set_err(ctx, VL_ERR_ARG, "formula was planned for another tile configuration");
   DeviceGuard dg(ctx->device);
-  if (exec_mode == VL_EXEC_PLAIN) return eval_plain(ctx, f, imgs, n_imgs, S(stream), out);
-  if (exec_mode != VL_EXEC_FUSED) return set_err(ctx, VL_ERR_ARG, "unknown execution form");
+  if (exec_mode != VL_EXEC_PLAIN && exec_mode != VL_EXEC_FUSED)
+    return set_err(ctx, VL_ERR_ARG, "unknown execution form");
+  // formulas over volumes have the per-operator form only
+  if (exec_mode == VL_EXEC_PLAIN || volume_plan(f->plan))
+    return eval_plain(ctx, f, imgs, n_imgs, S(stream), out);
   vl_job job{f, imgs, n_imgs, 0};
   vl_batch* b = nullptr;
   vl_status s = batch_build(ctx, &job, 1, S(stream), &b);
@@ -1310,9 +1419,14 @@ VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask, int32_t connectiv
   if (!valid(ctx, TAG_CTX)) return VL_ERR_ARG;
   if (!valid(mask, TAG_IMG) || !mask->is_mask) return set_err(ctx, VL_ERR_ARG, "vl_ccl needs a mask image");
   if (!labels_dev) return set_err(ctx, VL_ERR_ARG, "null labels buffer");
-  if (connectivity != 4 && connectivity != 8) return set_err(ctx, VL_ERR_ARG, "connectivity must be 4 or 8");
+  const bool vol = connectivity == 6 || connectivity == 26;
+  if (connectivity != 4 && connectivity != 8 && !vol)
+    return set_err(ctx, VL_ERR_ARG, "connectivity must be 4 or 8 (images), 6 or 26 (volumes)");
+  if (mask->D > 1 && !vol) return set_err(ctx, VL_ERR_ARG, "a volume needs connectivity 6 or 26");
   DeviceGuard dg(ctx->device);
-  const size_t tiles = (size_t)ccl_tiles_y(mask->H) * ccl_tiles_x(mask->Wp);
+  MaskGeom g{mask->H, mask->W, mask->Wp};
+  if (vol) g.Hs = mask->H / mask->D;
+  const size_t tiles = (size_t)ccl_tiles_y(mask->H, g.Hs) * ccl_tiles_x(mask->Wp);
   const int tcap = ccl_tile_cap_host(mask->Wp);
   DevBlockPtr tmp;  // per-tile labelling state, released in stream order
   cudaError_t e = dev_alloc(ctx, align_up(tiles * tcap * 4, 256) + tiles * tcap, S(stream), &tmp);
@@ -1325,8 +1439,9 @@ VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask, int32_t connectiv
   vl_image* mi = const_cast<vl_image*>(mask);
   e = wait_images(&mi, 1, S(stream));
   if (!e) e = cudaMemsetAsync(ctx->ccl_status, 0, sizeof(int32_t), S(stream));
-  if (!e) e = launch_ccl_labels(mask->mask, MaskGeom{mask->H, mask->W, mask->Wp}, connectivity,
-                                sc, ctx->ccl_status, S(stream));
+  if (!e)
+    e = vol ? launch_labels3(mask->mask, g, connectivity, sc, ctx->ccl_status, S(stream))
+            : launch_ccl_labels(mask->mask, g, connectivity, sc, ctx->ccl_status, S(stream));
   if (e) return cuda_err(ctx, e, "launching connected components");
   return VL_OK;
 }

@@ -187,8 +187,12 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
                     const PlanParams& pp, Plan* out, std::string* err) {
   if (n_nodes < 1 || !in) { *err = "formula needs at least one node"; return VL_ERR_ARG; }
   if (n_roots < 1 || !roots) { *err = "formula needs at least one root"; return VL_ERR_ARG; }
-  if (conn != 4 && conn != 8) { *err = "connectivity must be 4 or 8"; return VL_ERR_ARG; }
-  if (pp.group_buffers < 4 || pp.hmax < 1 || pp.hmax > 31) { *err = "bad plan parameters"; return VL_ERR_ARG; }
+  if (conn != 4 && conn != 8 && conn != 6 && conn != 26) {
+    *err = "connectivity must be 4 or 8 (images), 6 or 26 (volumes)";
+    return VL_ERR_ARG;
+  }
+  if (pp.group_buffers < 4 || pp.hmax < 1 || pp.hmax > 31 || pp.scratch_sets < 1 ||
+      pp.scratch_sets > 4096) { *err = "bad plan parameters"; return VL_ERR_ARG; }
   Plan P;
   P.conn = conn;
   P.params = pp;
@@ -547,6 +551,7 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
   }
 
   const int NB = pp.group_buffers;
+  int next_set = 0, n_selects_total = 0;  // select scratch pool (round robin)
   for (int level = 0; level <= maxL; ++level) {
     // ---- groups of this level
     std::vector<int> nodes;
@@ -671,13 +676,14 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
     for (int i = 0; i < N; ++i)
       if (X[i].op == E_RZ && L[i] == level + 1) rzs.push_back(i);
     for (size_t k0 = 0; k0 < rzs.size(); k0 += MAX_RZ_BATCH) {
+      // (selects of a batch take consecutive sets of the pool, round robin)
       int cnt = (int)std::min<size_t>(MAX_RZ_BATCH, rzs.size() - k0);
       int base_step = (int)P.steps.size();
       int rz_off = (int)P.rz.size();
       for (int j = 0; j < cnt; ++j) {
         int z = rzs[k0 + j];
         RzDesc r{}; r.phi1_slot = (int16_t)X[z].a; r.phi2_slot = (int16_t)X[z].b;  // value ids for now
-        r.z_slot = (int16_t)z; r.scratch = (int16_t)j;
+        r.z_slot = (int16_t)z; r.scratch = (int16_t)((next_set + j) % pp.scratch_sets);
         P.rz.push_back(r);
         if (!mat[X[z].a] || !mat[X[z].b]) { *err = "internal: select operand not materialised"; return VL_ERR_INTERNAL; }
         note_read(X[z].a, base_step + 2);
@@ -691,7 +697,9 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
         StepDesc s{}; s.kind = kind; s.rz_off = rz_off; s.rz_cnt = cnt;
         P.steps.push_back(s);
       }
-      P.max_rz_batch = std::max(P.max_rz_batch, cnt);
+      next_set = (next_set + cnt) % pp.scratch_sets;
+      n_selects_total += cnt;
+      P.n_scratch_sets = std::min(pp.scratch_sets, n_selects_total);
     }
   }
   // roots must be materialised

@@ -34,6 +34,10 @@ struct PlanParams {
   // after the last read of its previous value: reuse adds write-after-read
   // dependencies, which a distant reader keeps off the critical path
   int reuse_distance = 32;
+  // select scratch sets (union-find, saved tile state) are handed out round
+  // robin from a pool of this many, so consecutive select batches use
+  // different sets and need not wait for each other
+  int scratch_sets = 64;
 };
 
 struct Plan {
@@ -55,7 +59,7 @@ struct Plan {
   std::vector<RzDesc> rz;
   std::vector<PctDesc> pct;
   int n_pct_slots = 0;
-  int max_rz_batch = 0;
+  int n_scratch_sets = 0;         // select scratch sets used (allocated per job)
   int max_group_halo = 0;
   // image requirements: kind per image index (0 unused, 1 float, 2 mask)
   std::vector<int> img_kind;

@@ -54,7 +54,7 @@ int64_t estimate_bytes(const Plan& P, int H, int W) {
   const size_t tiles = (size_t)ccl_tiles_y(H) * ccl_tiles_x(Wp);
   const size_t tstate = tiles * ccl_tile_cap_host(Wp);
   size_t b = align256(mask * (P.n_inter_slots + P.n_root_slots));
-  b += (size_t)P.max_rz_batch *
+  b += (size_t)P.n_scratch_sets *
        (align256(2 * px * 4) + align256(tstate * 4) + align256(tstate));
   b += align256(sizeof(Insn) * P.insns.size()) + align256(sizeof(StepDesc) * P.steps.size()) +
        64 * 1024;
