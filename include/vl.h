@@ -162,6 +162,41 @@ VL_API vl_status vl_image_info(const vl_image* img, int32_t* h, int32_t* w,
 /* Pixel format (vl_pixel_format) of a number image; VL_ERR_ARG for masks. */
 VL_API vl_status vl_image_format(const vl_image* img, int32_t* format);
 
+/* ----------------------------------------------------------------- volumes
+ * The logic of Sec. 2 on D x H x W voxel grids (the paper's 3D outlook,
+ * Sec. 1 and Sec. 5).  A volume is stored as its D slices stacked into one
+ * image of D*h rows (slice z = rows z*h .. z*h + h - 1); vl_image_info
+ * reports h as D*h and vl_image_depth gives D.  Formulas over volumes are
+ * compiled with adjacency 26 (the 3 x 3 x 3 cube: voxels differing by at
+ * most 1 in every coordinate) or 6 (the faces: differing by 1 in exactly
+ * one coordinate); N, rho and labelling then use it, clipped at the
+ * volume's border.  Volumes evaluate in the per-operator form (vl_eval
+ * takes it whatever the context's exec_mode; vl_eval_batch and the server
+ * refuse them).  Results hold D*h x Wp words per root (slice after slice);
+ * vl_result_depth gives D.  A percentile ranks all D*h*w values of the
+ * channel.  vl_ccl with connectivity 6 or 26 labels a mask volume: label =
+ * the minimum linear index z*h*w + y*w + x of the component, -1 for
+ * background.
+ *   data: channels*d*h*w values (channel-major, then slice, row, column),
+ *   host or device as for vl_image_create.
+ * Errors: VL_ERR_ARG for sizes < 1, d*h > 2^20, w > 65535 or more than
+ * 2^31 - 1 voxels. */
+VL_API vl_status vl_volume_create(vl_context* ctx, int32_t d, int32_t h, int32_t w,
+                                  int32_t channels, const float* data,
+                                  int32_t data_on_device, void* stream,
+                                  vl_image** out);
+VL_API vl_status vl_volume_create_u16(vl_context* ctx, int32_t d, int32_t h, int32_t w,
+                                      int32_t channels, const uint16_t* data,
+                                      int32_t data_on_device, void* stream,
+                                      vl_image** out);
+/* A binary volume (d*h*w bytes, nonzero = true) used as an atom. */
+VL_API vl_status vl_mask_volume_create(vl_context* ctx, int32_t d, int32_t h, int32_t w,
+                                       const uint8_t* data, int32_t data_on_device,
+                                       void* stream, vl_image** out);
+/* Depth D of an image (1 for a 2D image) or of a result. */
+VL_API vl_status vl_image_depth(const vl_image* img, int32_t* d);
+VL_API vl_status vl_result_depth(const vl_result* res, int32_t* d);
+
 /* ---------------------------------------------------------------- formulas */
 
 /* Operators of a formula node.  The primitive ones follow Eq. (1) of Sec. 2;
@@ -218,8 +253,8 @@ typedef struct {
 
 /* Compile a formula DAG given as `n_nodes` nodes in topological order and
  * `n_roots` output node indices (a root may be any node; Sec. 3.2 "output
- * instructions").  connectivity is 4 or 8 and governs both N and the paths
- * of rho.  The compiler expands derived operators, shares identical
+ * instructions").  connectivity is 4 or 8 for images, 6 or 26 for volumes,
+ * and governs both N and the paths of rho.  The compiler expands derived operators, shares identical
  * sub-expressions, and plans fused execution.  Host-only; no device work.
  * Errors: VL_ERR_FORMULA (operand out of order, unknown op, bad arity,
  * percentile level outside [0,1]), VL_ERR_ARG.  ctx may be NULL: the plan is
@@ -489,8 +524,10 @@ VL_API vl_status vl_result_device_ptr(const vl_result* res, int32_t root,
  * reduces to, Sec. 3.2-3.3): labels_dev receives H*W int32 labels (minimum
  * linear index per component, -1 background).  labels_dev is a caller-owned
  * device buffer of at least H*W int32.  Union-find: tile-local labelling in
- * shared memory, then a global merge with atomics.  Enqueue only; device
- * errors are reported by vl_ccl_status. */
+ * shared memory, then a global merge with atomics.  A mask volume takes
+ * connectivity 6 or 26 (labels = minimum linear index of the 3D component;
+ * see the volumes section).  Enqueue only; device errors are reported by
+ * vl_ccl_status. */
 VL_API vl_status vl_ccl(vl_context* ctx, const vl_image* mask,
                         int32_t connectivity, int32_t* labels_dev,
                         void* stream);

@@ -124,6 +124,11 @@ SIGNATURES = [
     ("vl_image_create", C.c_int, [_P, _I32, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_image_create_u16", C.c_int, [_P, _I32, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_image_format", C.c_int, [_P, C.POINTER(_I32)]),
+    ("vl_volume_create", C.c_int, [_P, _I32, _I32, _I32, _I32, _P, _I32, _P, _PP]),
+    ("vl_volume_create_u16", C.c_int, [_P, _I32, _I32, _I32, _I32, _P, _I32, _P, _PP]),
+    ("vl_mask_volume_create", C.c_int, [_P, _I32, _I32, _I32, _P, _I32, _P, _PP]),
+    ("vl_image_depth", C.c_int, [_P, C.POINTER(_I32)]),
+    ("vl_result_depth", C.c_int, [_P, C.POINTER(_I32)]),
     ("vl_mask_create", C.c_int, [_P, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_mask_create_packed", C.c_int, [_P, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_image_info", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),

@@ -123,6 +123,31 @@ class Context(_Handle):
         self._check(rc)
         return Image(self, out.value, keep)
 
+    def volume(self, data, stream=None) -> "Image":
+        """Number volume (C, D, H, W) from a host numpy array: uint16 stays
+        uint16, anything else becomes float32.  Stored as D slices stacked."""
+        lib = N.load()
+        out = C.c_void_p()
+        a = np.asarray(data)
+        a = np.ascontiguousarray(a, dtype=np.uint16 if a.dtype == np.uint16 else np.float32)
+        if a.ndim == 3:
+            a = a[None]
+        c, d, h, w = a.shape
+        fn = lib.vl_volume_create_u16 if a.dtype == np.uint16 else lib.vl_volume_create
+        self._check(fn(self._ptr, d, h, w, c, a.ctypes.data, 0, _stream_handle(stream),
+                       C.byref(out)))
+        return Image(self, out.value, a)
+
+    def mask_volume(self, data, stream=None) -> "Image":
+        """Binary volume (D, H, W) from a host array (nonzero = true)."""
+        lib = N.load()
+        out = C.c_void_p()
+        a = np.ascontiguousarray(np.asarray(data) != 0, dtype=np.uint8)
+        d, h, w = a.shape
+        self._check(lib.vl_mask_volume_create(self._ptr, d, h, w, a.ctypes.data, 0,
+                                              _stream_handle(stream), C.byref(out)))
+        return Image(self, out.value, a)
+
     def mask_packed(self, words, h: int, w: int, stream=None) -> "Image":
         lib = N.load()
         out = C.c_void_p()
@@ -365,10 +390,17 @@ class Result(_Handle):
         return w.value
 
     def mask(self, root: int = 0, stream=None) -> np.ndarray:
-        """Root mask as (H, W) uint8 on the host (unpacked by a device kernel)."""
+        """Root mask as (H, W) uint8 on the host (unpacked by a device kernel);
+        (D, H, W) for a volume."""
         out = np.empty((self.h, self.w), dtype=np.uint8)
         self._check(N.load().vl_result_mask_u8(self._ptr, root, out.ctypes.data, 0, _stream_handle(stream)))
-        return out
+        d = self.depth()
+        return out.reshape(d, self.h // d, self.w) if d > 1 else out
+
+    def depth(self) -> int:
+        d = C.c_int32()
+        self._check(N.load().vl_result_depth(self._ptr, C.byref(d)))
+        return d.value
 
     def mask_packed(self, root: int = 0, stream=None) -> np.ndarray:
         out = np.empty((self.h, self.wp), dtype=np.uint32)

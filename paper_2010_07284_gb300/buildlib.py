@@ -19,7 +19,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels.cu", "executor.cu", "noalloc.cu", "pointer_jump.cu"]
+CU_SOURCES = ["kernels.cu", "executor.cu", "noalloc.cu", "pointer_jump.cu", "volume.cu"]
 CPP_SOURCES = ["api.cpp", "autotune.cpp", "compiler.cpp", "server.cpp"]
 
 

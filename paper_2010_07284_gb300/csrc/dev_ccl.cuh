@@ -45,13 +45,18 @@ struct CclGeom {
   int th, tww;  // rows and words of this tile
 };
 
-VL_DEV CclGeom ccl_geom(int H, int W, int Wp, int tile, int tiles_x) {
+// Tile `tile` of an image of H rows, or of a volume stored as its slices of
+// Hs rows stacked (H = depth * Hs; Hs = H for an image): tiles never
+// straddle two slices, so the tile-local labelling stays inside one slice.
+VL_DEV CclGeom ccl_geom(int H, int W, int Wp, int tile, int tiles_x, int Hs) {
   CclGeom g;
   g.H = H; g.W = W; g.Wp = Wp;
-  int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-  g.r0 = ty * CCL_TH;
+  const int tys = (Hs + CCL_TH - 1) / CCL_TH;  // tile rows per slice
+  const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+  const int z = ty / tys, tyz = ty - z * tys;
+  g.r0 = z * Hs + tyz * CCL_TH;
   g.w0 = tx * CCL_TWW;
-  g.th = min(CCL_TH, H - g.r0);
+  g.th = min(CCL_TH, Hs - tyz * CCL_TH);
   g.tww = min(CCL_TWW, Wp - g.w0);
   return g;
 }
@@ -732,8 +737,11 @@ VL_DEV void ccl_write_select(const CclSmem& s, const CclGeom& g, uint32_t* Z) {
 // and one per 32 rows of each vertical tile border.  A warp takes a unit,
 // one lane per column (or row), so the unions of a unit run side by side
 // instead of one after another.
-VL_DEV int merge_units(int H, int Wp, int tiles_y, int tiles_x) {
-  return (tiles_y - 1) * Wp + (tiles_x - 1) * ((H + 31) >> 5);
+// (Hs: slice rows of a volume, H for an image; horizontal borders are those
+// between the tile rows of one slice.)
+VL_DEV int merge_units(int H, int Wp, int tiles_x, int Hs) {
+  const int tys = (Hs + CCL_TH - 1) / CCL_TH;
+  return (H / Hs) * (tys - 1) * Wp + (tiles_x - 1) * ((H + 31) >> 5);
 }
 
 // Which of columns x-1, x, x+1 (8-adjacency) or x (4-adjacency) of a row is
@@ -778,28 +786,42 @@ VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int glen, int32_t* 
 // neighbours (both border columns lie inside the image: a tile border is a
 // multiple of 1024 columns, below W).  Padding bits of the loaded words are
 // cleared.  Must be called by the whole warp.
-VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y, int unit,
-                           int conn, int32_t* G, int glen, int32_t* status) {
+// Unite the components of row yu and row yd (rows of the stored image) that
+// touch in word w: with conn 8 a pixel meets the three pixels at x - 1, x,
+// x + 1 of the other row, with conn 4 only the one at x.  Every row-run start
+// of either row is checked against that window of the other row: two runs
+// that touch always have a start of one run inside the other's window.  Must
+// be called by the whole warp.
+VL_DEV void ccl_merge_rows(const uint32_t* m, int W, int Wp, int yu, int yd, int w, int conn,
+                           int32_t* G, int glen, int32_t* status) {
   const int lane = threadIdx.x & 31;
-  const int nh = (tiles_y - 1) * Wp;
+  uint32_t v = 0;
+  if (lane < 6) {
+    const int ww = w - 1 + lane % 3;
+    if (ww >= 0 && ww < Wp) v = ldcg(&m[(size_t)(lane < 3 ? yu : yd) * Wp + ww]) & vmask(ww, W);
+  }
+  const uint32_t mul = __shfl_sync(FULL, v, 0), mu = __shfl_sync(FULL, v, 1),
+                 mur = __shfl_sync(FULL, v, 2), mdl = __shfl_sync(FULL, v, 3),
+                 md = __shfl_sync(FULL, v, 4), mdr = __shfl_sync(FULL, v, 5);
+  const uint32_t sd = md & ~((md << 1) | (mdl >> 31));
+  const uint32_t su = mu & ~((mu << 1) | (mul >> 31));
+  const int x = 32 * w + lane;
+  int dx = (sd >> lane) & 1u ? window_hit(mul, mu, mur, lane, conn) : 2;
+  warp_unite(G, dx != 2, yd * W + x, yu * W + x + dx, glen, status);
+  dx = (su >> lane) & 1u ? window_hit(mdl, md, mdr, lane, conn) : 2;
+  warp_unite(G, dx != 2, yu * W + x, yd * W + x + dx, glen, status);
+}
+
+VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int unit, int conn,
+                           int32_t* G, int glen, int32_t* status, int Hs) {
+  const int lane = threadIdx.x & 31;
+  const int tys = (Hs + CCL_TH - 1) / CCL_TH;
+  const int nh = (H / Hs) * (tys - 1) * Wp;
   if (unit < nh) {
-    const int k = unit / Wp + 1, w = unit - (k - 1) * Wp;
-    const int yd = k * CCL_TH, yu = yd - 1;
-    uint32_t v = 0;
-    if (lane < 6) {
-      const int ww = w - 1 + lane % 3;
-      if (ww >= 0 && ww < Wp) v = ldcg(&m[(size_t)(lane < 3 ? yu : yd) * Wp + ww]) & vmask(ww, W);
-    }
-    const uint32_t mul = __shfl_sync(FULL, v, 0), mu = __shfl_sync(FULL, v, 1),
-                   mur = __shfl_sync(FULL, v, 2), mdl = __shfl_sync(FULL, v, 3),
-                   md = __shfl_sync(FULL, v, 4), mdr = __shfl_sync(FULL, v, 5);
-    const uint32_t sd = md & ~((md << 1) | (mdl >> 31));
-    const uint32_t su = mu & ~((mu << 1) | (mul >> 31));
-    const int x = 32 * w + lane;
-    int dx = (sd >> lane) & 1u ? window_hit(mul, mu, mur, lane, conn) : 2;
-    warp_unite(G, dx != 2, yd * W + x, yu * W + x + dx, glen, status);
-    dx = (su >> lane) & 1u ? window_hit(mdl, md, mdr, lane, conn) : 2;
-    warp_unite(G, dx != 2, yu * W + x, yd * W + x + dx, glen, status);
+    const int border = unit / Wp, w = unit - border * Wp;  // border: over all slices
+    const int z = border / (tys - 1), k = border - z * (tys - 1) + 1;
+    const int yd = z * Hs + k * CCL_TH, yu = yd - 1;
+    ccl_merge_rows(m, W, Wp, yu, yd, w, conn, G, glen, status);
   } else {
     const int nv = (H + 31) >> 5;
     const int j = unit - nh;
@@ -817,6 +839,9 @@ VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int tiles_y,
       Rd = __shfl_down_sync(FULL, R, 1);
       if (lane == 0) Ru = (y > 0 && y - 1 < H) ? ldcg(&m[(size_t)(y - 1) * Wp + wr]) & 1u : 0u;
       if (lane == 31) Rd = (y + 1 < H) ? ldcg(&m[(size_t)(y + 1) * Wp + wr]) & 1u : 0u;
+      // diagonals stay inside one slice of a volume
+      if (y % Hs == 0) Ru = 0;
+      if ((y + 1) % Hs == 0) Rd = 0;
     }
     // (lane-dependent choices go into the arguments: every lane calls)
     const int a = y * W + x0 - 1;

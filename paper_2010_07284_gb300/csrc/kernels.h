@@ -10,7 +10,10 @@ namespace vl {
 
 struct MaskGeom {
   int H, W, Wp;
+  int Hs = 0;  // a volume stored as its slices stacked: rows per slice (H =
+               // depth * Hs); 0 for an image
 };
+inline __host__ __device__ int slice_rows(const MaskGeom& g) { return g.Hs > 0 ? g.Hs : g.H; }
 
 // ---- plain per-operator kernels (one launch per primitive) ----
 // `plane`: one channel of H x pitch elements, float or uint16 by `format`.
@@ -42,12 +45,12 @@ struct CclScratch {
   int32_t* tpar;    // tiles * tile_cap int32: saved tile union-find state
   uint8_t* tflag;   // tiles * tile_cap bytes: saved tile flags
 };
-int ccl_tiles_y(int H);
+int ccl_tiles_y(int H, int Hs = 0);  // tile rows over all slices (Hs 0: an image)
 int ccl_tiles_x(int Wp);
 int ccl_tile_cap_host(int Wp);
 // Border merge units (one warp each): words of horizontal tile borders and
 // 32-row pieces of vertical ones.
-long long ccl_merge_units(int H, int Wp);
+long long ccl_merge_units(int H, int Wp, int Hs = 0);
 size_t ccl_smem_bytes();
 
 // Labels: sc.G is the labels array itself (it doubles as the union-find).
@@ -56,6 +59,21 @@ cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScr
 // Component select Z (rho core): Z = phi2-components meeting N phi1.
 cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int conn,
                       CclScratch sc, uint32_t* Z, int32_t* status, cudaStream_t st);
+
+// ---- volumes (D slices of Hs rows stacked; g.Hs set) ----
+// conn: 26 (cube) or 6 (faces).
+cudaError_t launch_near3(const uint32_t* a, MaskGeom g, int conn, uint32_t* out, cudaStream_t st);
+// Full labels: sc.G is the labels array; sc.tpar / sc.tflag sized for
+// ccl_tiles_y(H, Hs) * ccl_tiles_x(Wp) tiles.
+cudaError_t launch_labels3(const uint32_t* mask, MaskGeom g, int conn, CclScratch sc,
+                           int32_t* status, cudaStream_t st);
+struct Rz3Scratch {
+  CclScratch ccl;   // G: H*W int32 labels of phi2
+  uint8_t* F;       // H*W bytes: flag per component root
+  uint32_t* seed;   // H x Wp words
+};
+cudaError_t launch_rz3(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int conn,
+                       Rz3Scratch sc, uint32_t* Z, int32_t* status, cudaStream_t st);
 
 // ---- mask conversion ----
 cudaError_t launch_pack_u8(const uint8_t* src, MaskGeom g, uint32_t* out, cudaStream_t st);

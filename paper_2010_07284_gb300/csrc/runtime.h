@@ -74,7 +74,8 @@ struct EventHolder {
 struct vl_image {
   uint32_t tag = vl::TAG_IMG;
   vl_context* ctx = nullptr;
-  int H = 0, W = 0, C = 0, Wp = 0, pitch = 0;
+  int H = 0, W = 0, C = 0, Wp = 0, pitch = 0;  // H: stored rows (depth * slice rows)
+  int D = 1;                // volumes: slices stacked in the H rows (1: an image)
   int is_mask = 0;
   int format = vl::PX_F32;  // number images: PX_F32 or PX_U16 elements
   void* data = nullptr;     // number images: C planes of H x pitch elements
@@ -94,7 +95,8 @@ struct vl_formula {
 struct vl_result {
   uint32_t tag = vl::TAG_RES;
   vl_context* ctx = nullptr;
-  int H = 0, W = 0, Wp = 0;
+  int H = 0, W = 0, Wp = 0;       // H: stored rows (depth * slice rows)
+  int D = 1;                      // depth of a volume result
   int n_roots = 0;
   bool borrowed = false;          // owned by a batch
   std::vector<uint32_t*> roots;   // device mask per root

@@ -60,7 +60,7 @@ def test_primitive_count_matches_oracle(make):
     ([("THR_GT", -1, -1, 0, 0, 0.5, 0), ("AND", 0, 5, 0, 0, 0, 0)], [1], 8, N.ERR_FORMULA),
     ([("THR_GT", -1, -1, 0, 0, 0.5, 0)], [3], 8, N.ERR_FORMULA),                 # bad root
     ([("PCT_GT", -1, -1, 0, 0, 0, 1.5)], [0], 8, N.ERR_FORMULA),                 # q > 1
-    ([("THR_GT", -1, -1, 0, 0, 0.5, 0)], [0], 6, N.ERR_ARG),                     # conn
+    ([("THR_GT", -1, -1, 0, 0, 0.5, 0)], [0], 5, N.ERR_ARG),                     # conn
     ([(99, -1, -1, 0, 0, 0, 0)], [0], 8, N.ERR_FORMULA),                          # op code
     ([("THR_GT", -1, -1, 0, 0, 0.5, 0), ("MASK", -1, -1, 0, 0, 0, 0),
       ("AND", 0, 1, 0, 0, 0, 0)], [2], 8, N.ERR_FORMULA),                         # image kinds clash
