@@ -303,6 +303,62 @@ def leg_grow_7680(ctx, stream, flush, peak: float, runs: int = 5) -> dict:
                                  "Intel HD 630 (OpenCL)": 3000, "i7-7700 CPU tool": 1100}}
 
 
+def leg_volume(ctx, stream, flush, peak: float, shape=(155, 240, 240), runs: int = 5) -> dict:
+    """The 40-primitive segmentation formula on an MRI-volume-shaped
+    4-channel float32 phantom of 155 x 240 x 240 voxels (the size of the
+    paper's brain scans before it takes one slice, Sec. 4.2), 26-adjacency:
+    device time with the volume resident (volumes evaluate in the
+    per-operator form), Gvoxel-ops/s and the roofline of the step, and the
+    oracle on a bounded sub-volume on one core."""
+    import torch
+    import oracle
+    import workloads as wl
+    f = wl.config4_formula()
+    rec = wl.formula_to_records(f)
+    vol = wl.mri_phantom_volume(*shape, seed=0)
+    F = ctx.compile(rec, f.roots, 26)
+    finfo = F.info()
+    n_prim = finfo["n_primitive"]
+    P = float(np.prod(shape))
+    with torch.cuda.stream(stream):
+        im = ctx.volume(vol, stream)
+        for _ in range(2):
+            r = ctx.eval(F, [im], stream=stream)
+            if r.sync() != 0:
+                raise SystemExit("volume leg failed: " + ctx.last_error())
+            r.close()
+        ev = []
+        for _ in range(runs):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = ctx.eval(F, [im], stream=stream)
+            z.record(stream)
+            ev.append((a, z, r))
+        stream.synchronize()
+        for a, z, r in ev:
+            if r.sync() != 0:
+                raise SystemExit("volume leg failed")
+            r.close()
+        ms = float(np.mean([a.elapsed_time(z) for a, z, _ in ev]))
+        im.close()
+    alg = formula_alg_bytes(finfo, P)
+    ach = alg / (ms / 1e3) / 1e9
+    # the oracle on the first 8 slices, one core
+    sub = np.ascontiguousarray(vol[:, :8])
+    t0 = time.perf_counter()
+    oracle.evaluate3(rec, f.roots, volumes=[sub], conn=26)
+    cpu_s = time.perf_counter() - t0
+    return {"workload": f"segmentation formula on a {shape[0]}x{shape[1]}x{shape[2]} MRI-shaped "
+                        "4-channel volume, 26-adjacency",
+            "form": "per-operator kernels", "ms": ms,
+            "value": n_prim * P / (ms / 1e3) / 1e9, "unit": "Gvoxel-ops/s",
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "algorithmic_bytes": alg},
+            "cpu_oracle": {"kind": "oracle", "cores": 1, "sample": "first 8 slices",
+                           "value": n_prim * sub[0].size / cpu_s / 1e9, "unit": "Gvoxel-ops/s"}}
+
+
 def leg_formula_scaling(ctx, stream, flush, image, sizes=(10, 100, 500, 1000, 2000),
                         runs: int = 3) -> dict:
     """Time against formula size (Sec. 4.1): sequential formulas f(g(...(x)))
@@ -633,7 +689,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain/ccl/e2e/cpu legs")
-    ap.add_argument("--leg", default="", choices=["", "ccl", "scaling"],
+    ap.add_argument("--leg", default="", choices=["", "ccl", "scaling", "volume"],
                     help="run only this leg and print its figures (for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -663,6 +719,12 @@ def main():
         stream = torch.cuda.Stream()
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         print(json.dumps({"leg": "ccl", **leg_ccl(ctx, stream, flush, measured_peaks()[0])}), flush=True)
+        return
+    if args.leg == "volume":
+        stream = torch.cuda.Stream()
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        print(json.dumps({"leg": "volume", **leg_volume(ctx, stream, flush, measured_peaks()[0])}),
+              flush=True)
         return
     if args.leg == "scaling":
         stream = torch.cuda.Stream()
@@ -798,10 +860,12 @@ def main():
         mri = leg_mri_batch(ctx, stream, flush, peak)
         serving = leg_serving(ctx, stream)
         grow = leg_grow_7680(ctx, stream, flush, peak)
+        volume = leg_volume(ctx, stream, flush, peak)
         scaling = leg_formula_scaling(ctx, stream, flush, image)
         if rank == 0:
             for name, obj in (("ccl", ccl), ("mri_batch", mri), ("serving", serving),
-                              ("grow_7680", grow), ("formula_scaling", scaling)):
+                              ("grow_7680", grow), ("volume", volume),
+                              ("formula_scaling", scaling)):
                 emit_leg(name, obj)
         # the headline figures of every leg, short enough that the whole
         # result line survives a truncated log
@@ -819,6 +883,8 @@ def main():
         line["grow_7680"] = {"ms": grow["device_ms"], "e2e_ms": grow["e2e_ms"],
                              "u16_ms": grow["uint16"]["device_ms"],
                              "frac": grow["roofline"]["frac"]}
+        line["volume"] = {"value": volume["value"], "unit": volume["unit"], "ms": volume["ms"],
+                          "frac": volume["roofline"]["frac"], "shape": "155x240x240x4"}
         rows = scaling["rows"]
         line["formula_scaling"] = {
             "min_fused_over_plain": min(r["fused_over_plain"] for r in rows),

@@ -413,7 +413,11 @@ typedef struct {
 /* Evaluate many jobs (images of different sizes allowed between jobs) in
  * one persistent launch; outs[i] receives job i's result.  When the
  * context's use_graphs is set, the launch sequence is captured into a CUDA
- * graph cached by the batch's structure and replayed.  Enqueue only. */
+ * graph cached by the batch's structure and replayed.  A batch of a single
+ * job whose formula has at most 24 primitives (after expansion and
+ * sharing) runs the per-operator kernels instead, captured the same way: a
+ * handful of kernels beats a chain of executor steps (vl_eval_mode with
+ * VL_EXEC_FUSED always takes the persistent launch).  Enqueue only. */
 VL_API vl_status vl_eval_batch(vl_context* ctx, const vl_job* jobs,
                                int32_t n_jobs, void* stream, vl_result** outs);
 

@@ -139,8 +139,8 @@ vl_status check_job_images(vl_context* ctx, const Plan& P, vl_image* const* imgs
 // Formulas over volumes (adjacency 6 or 26) run in the per-operator form.
 inline bool volume_plan(const Plan& P) { return P.conn == 6 || P.conn == 26; }
 
-int ccl_merge_chunks(int H, int Wp) {
-  const long long n = ccl_merge_units(H, Wp);  // one warp each
+int ccl_merge_chunks(int H, int Wp, int cth) {
+  const long long n = ccl_merge_units(H, Wp, 0, cth);  // one warp each
   const int warps = EXEC_THREADS / 32;
   return (int)std::max<long long>(1, (n + warps - 1) / warps);
 }
@@ -168,6 +168,14 @@ struct vl_batch {
   std::vector<vl_image*> images;        // waited on before every run
   DevBlockPtr trace;                    // optional step timeline
   std::vector<int32_t> trace_meta;      // {job, step, kind} per timeline entry
+  // A lone job with a tiny plan runs in the per-operator form captured in
+  // the graph instead (the persistent launch's step latencies would
+  // dominate it): its plan, images and shape.
+  bool plain_form = false;
+  std::shared_ptr<vl::Plan> plain_plan;
+  std::vector<vl_image*> plain_imgs;
+  int plain_H = 0, plain_W = 0;
+  char* plain_roots = nullptr;
 };
 
 namespace vl {
@@ -175,12 +183,12 @@ namespace vl {
 int64_t batch_bytes(const vl_batch* b) { return b ? b->bytes : 0; }
 
 vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStream_t st,
-                      vl_batch** out, const TileShape* force) {
+                      vl_batch** out, const TileShape* force, bool persistent) {
   if (n_jobs < 1 || !jobs) return set_err(ctx, VL_ERR_ARG, "empty batch");
   struct JobInfo {
     const Plan* P;
     int H, W, Wp, pitch;
-    int gty, gtx, cty, ctx_, ctiles;
+    int gty, gtx, cty, ctx_, ctiles, cth;
     std::vector<int> need;
     size_t off_images, off_slotptrs, off_pct, off_slots, off_rz, set_bytes, set_off[3];
     size_t off_roots, off_status, off_planes, off_num;
@@ -241,7 +249,16 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.pitch = 32 * I.Wp;
     I.gty = (I.H + ts.rows - 1) / ts.rows;
     I.gtx = (I.Wp + ts.words - 1) / ts.words;
-    I.cty = ccl_tiles_y(I.H);
+    // labelling tiles of 16 rows when the job's selects would otherwise
+    // leave most of the grid idle (a lone small image, a chain of selects)
+    {
+      int maxbatch = 0;
+      for (const StepDesc& sd : P.steps)
+        if (sd.kind == SK_RZ_LOCAL) maxbatch = std::max(maxbatch, sd.rz_cnt);
+      const long long t32 = (long long)ccl_tiles_y(I.H) * ccl_tiles_x(I.Wp);
+      I.cth = (long long)n_jobs * t32 * maxbatch < grid ? 16 : CCL_TH;
+    }
+    I.cty = ccl_tiles_y(I.H, 0, I.cth);
     I.ctx_ = ccl_tiles_x(I.Wp);
     I.ctiles = I.cty * I.ctx_;
     I.step_base = total_steps;
@@ -252,7 +269,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
         case SK_PCT: n = s.pct_cnt; break;
         case SK_GROUP: n = I.gty * I.gtx; break;
         case SK_RZ_LOCAL: case SK_RZ_FINAL: n = s.rz_cnt * I.ctiles; break;
-        case SK_RZ_MERGE: n = s.rz_cnt * ccl_merge_chunks(I.H, I.Wp); break;
+        case SK_RZ_MERGE: n = s.rz_cnt * ccl_merge_chunks(I.H, I.Wp, I.cth); break;
         case SK_RANK: n = (int)P.rtab.size() * ((I.H + RANK_ROWS - 1) / RANK_ROWS); break;
         case SK_ARITH: n = (I.H + ARITH_ROWS - 1) / ARITH_ROWS; break;
       }
@@ -337,7 +354,7 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.off_planes = take(mask_bytes * P.n_planes);
     I.off_num = take(sizeof(float) * (size_t)I.H * I.pitch * P.n_num_images);
     I.off_slots = take(mask_bytes * P.n_inter_slots);
-    const size_t tstate = (size_t)I.ctiles * ccl_tile_cap_host(I.Wp);
+    const size_t tstate = (size_t)I.ctiles * ccl_tile_cap_host(I.Wp, I.cth);
     // select scratch sets: G (2 * P_px keys), tpar, tflag, each 256-byte aligned
     {
       size_t o = 0;
@@ -440,7 +457,8 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     d.set_bytes = (int64_t)I.set_bytes;
     d.off_tpar = (int64_t)I.set_off[1];
     d.off_tflag = (int64_t)I.set_off[2];
-    d.tile_cap = ccl_tile_cap_host(I.Wp);
+    d.tile_cap = ccl_tile_cap_host(I.Wp, I.cth);
+    d.c_th = I.cth;
     d.status = status_dev + j;
     hj[j] = d;
     for (size_t s = 0; s < I.need.size(); ++s) hneed[I.step_base + s] = I.need[s];
@@ -501,6 +519,14 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     r->keep.push_back(b->persist);
     b->results.push_back(r);
   }
+  if (!persistent && n_jobs == 1 && J[0].P->n_primitive <= kTinyPlanPrimitives && !ctx->cfg.trace) {
+    b->plain_form = true;
+    b->plain_plan = std::make_shared<Plan>(*J[0].P);
+    b->plain_imgs.assign(jobs[0].images, jobs[0].images + jobs[0].n_images);
+    b->plain_H = J[0].H;
+    b->plain_W = J[0].W;
+    b->plain_roots = pb + J[0].off_roots;
+  }
   *out = b.release();
   return VL_OK;
 }
@@ -518,6 +544,36 @@ vl_status batch_run(vl_batch* b, cudaStream_t st) {
     if ((e = cudaMemsetAsync(b->trace->ptr, 0, b->trace->bytes, st)) ||
         (e = cudaMemset2DAsync(b->trace->ptr, 32, 0xFF, 8, n, st)))
       return cuda_err(ctx, e, "clearing the step timeline");
+  }
+  if (b->plain_form) {  // per-operator form, captured like the executor
+    if ((e = ccl_configure())) return cuda_err(ctx, e, "setting kernel attributes");
+    auto enqueue = [&]() -> vl_status {
+      cudaError_t z = cudaMemsetAsync(b->status_base, 0, sizeof(int32_t), st);
+      if (z) return cuda_err(ctx, z, "zeroing the status word");
+      return plain_enqueue(ctx, *b->plain_plan, b->plain_imgs.data(), b->plain_H, b->plain_W, 1,
+                           b->plain_roots, b->status_base, st);
+    };
+    if (graphs && !b->gexec) {
+      if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)))
+        return cuda_err(ctx, e, "beginning graph capture");
+      const vl_status s1 = enqueue();
+      e = cudaStreamEndCapture(st, &b->graph);
+      if (s1 != VL_OK || e) {
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        return s1 != VL_OK ? s1 : cuda_err(ctx, e, "capturing the per-operator graph");
+      }
+      if ((e = cudaGraphInstantiate(&b->gexec, b->graph, 0)))
+        return cuda_err(ctx, e, "instantiating the per-operator graph");
+    }
+    if (b->gexec) {
+      if ((e = cudaGraphLaunch(b->gexec, st))) return cuda_err(ctx, e, "launching the graph");
+    } else {
+      const vl_status s1 = enqueue();
+      if (s1 != VL_OK) return s1;
+    }
+    if ((e = cudaEventRecord(b->done->ev, st))) return cuda_err(ctx, e, "recording an event");
+    for (vl_result* r : b->results) r->stream = st;
+    return VL_OK;
   }
   if (graphs && !b->gexec) {
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -587,30 +643,26 @@ void batch_destroy(vl_batch* b) {
 
 // ========================================================== plain form ==
 
-namespace {
+namespace vl {
 
-vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs, int n_imgs,
-                     cudaStream_t st, vl_result** out) {
-  const Plan& P = f->plan;
-  int H, W, D;
-  vl_status s = check_job_images(ctx, P, imgs, n_imgs, &H, &W, &D);
-  if (s != VL_OK) return s;
+// The per-operator form of plan P on `st`: one launch per primitive, the
+// roots written to `roots` (root slot s at roots + mask_bytes * (s -
+// n_inter_slots)), device errors to *status (which the caller clears).
+// Intermediate memory comes from the stream-ordered pool and is released in
+// stream order before returning; no host synchronisation and no event, so
+// the whole sequence can be captured into a CUDA graph (the allocations
+// become graph memory nodes, freed inside the graph).
+vl_status plain_enqueue(vl_context* ctx, const Plan& P, vl_image* const* imgs, int H, int W, int D,
+                        char* roots, int32_t* status, cudaStream_t st) {
   const int Wp = words_per_row(W), pitch = 32 * Wp;
   const bool vol = volume_plan(P);
   MaskGeom g{H, W, Wp};
   if (vol) g.Hs = H / D;
   const size_t mask_bytes = (size_t)H * Wp * 4;
   cudaError_t e;
-  if ((e = wait_images(imgs, n_imgs, st))) return cuda_err(ctx, e, "waiting for image uploads");
-  DevBlockPtr persist;
-  if ((e = dev_alloc(ctx, align_up(sizeof(int32_t), 256) + mask_bytes * P.n_root_slots, st, &persist)))
-    return cuda_err(ctx, e, "allocating results");
-  char* pb = static_cast<char*>(persist->ptr);
-  int32_t* status = reinterpret_cast<int32_t*>(pb);
   auto root_buf = [&](int slot) {
-    return reinterpret_cast<uint32_t*>(pb + 256 + mask_bytes * (slot - P.n_inter_slots));
+    return reinterpret_cast<uint32_t*>(roots + mask_bytes * (slot - P.n_inter_slots));
   };
-  if ((e = cudaMemsetAsync(status, 0, sizeof(int32_t), st))) return cuda_err(ctx, e, "zeroing status");
   // number terms: one launch per operation into register planes; the
   // compared terms are copied into number images, which follow the
   // formula's own images
@@ -654,15 +706,21 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
                 im->format};
   };
   // percentiles
-  DevBlockPtr pct;
+  DevBlockPtr pct, sel_scratch;
   if (P.n_pct_slots) {
     if ((e = dev_alloc(ctx, sizeof(float) * P.n_pct_slots, st, &pct))) return cuda_err(ctx, e, "allocating percentiles");
+    // channels of a million pixels and more take the grid-wide select
+    const bool wide = (long long)H * W >= (1LL << 20);
+    if (wide && (e = dev_alloc(ctx, select_wide_scratch_bytes(), st, &sel_scratch)))
+      return cuda_err(ctx, e, "allocating select scratch");
     for (const PctDesc& d : P.pct) {
       const long long n = (long long)H * W;
       const long long rank = (long long)(d.q * (double)(n - 1));
       const Chan c = chan(d.img, d.ch);
-      if ((e = launch_select(c.p, c.format, pitch, H, W, rank, static_cast<float*>(pct->ptr) + d.slot, st)))
-        return cuda_err(ctx, e, "launching a percentile select");
+      float* o = static_cast<float*>(pct->ptr) + d.slot;
+      e = wide ? launch_select_wide(c.p, c.format, pitch, H, W, rank, o, sel_scratch->ptr, st)
+               : launch_select(c.p, c.format, pitch, H, W, rank, o, st);
+      if (e) return cuda_err(ctx, e, "launching a percentile select");
     }
   }
   // rho scratch
@@ -760,12 +818,38 @@ vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs
     if (un || bin) release(x.a);
     if (bin) release(x.b);
   }
+  return VL_OK;
+}
+
+}  // namespace vl
+
+namespace {
+
+vl_status eval_plain(vl_context* ctx, const vl_formula* f, vl_image* const* imgs, int n_imgs,
+                     cudaStream_t st, vl_result** out) {
+  const Plan& P = f->plan;
+  int H, W, D;
+  vl_status s = check_job_images(ctx, P, imgs, n_imgs, &H, &W, &D);
+  if (s != VL_OK) return s;
+  const int Wp = words_per_row(W);
+  const size_t mask_bytes = (size_t)H * Wp * 4;
+  cudaError_t e;
+  if ((e = wait_images(imgs, n_imgs, st))) return cuda_err(ctx, e, "waiting for image uploads");
+  DevBlockPtr persist;
+  if ((e = dev_alloc(ctx, align_up(sizeof(int32_t), 256) + mask_bytes * P.n_root_slots, st, &persist)))
+    return cuda_err(ctx, e, "allocating results");
+  char* pb = static_cast<char*>(persist->ptr);
+  int32_t* status = reinterpret_cast<int32_t*>(pb);
+  if ((e = cudaMemsetAsync(status, 0, sizeof(int32_t), st))) return cuda_err(ctx, e, "zeroing status");
+  s = plain_enqueue(ctx, P, imgs, H, W, D, pb + 256, status, st);
+  if (s != VL_OK) return s;
   auto* r = new vl_result();
   r->ctx = ctx;
   r->H = H; r->W = W; r->Wp = Wp;
   r->D = D;
   r->n_roots = P.n_roots;
-  for (int q = 0; q < P.n_roots; ++q) r->roots.push_back(root_buf(P.root_slot[q]));
+  for (int q = 0; q < P.n_roots; ++q)
+    r->roots.push_back(reinterpret_cast<uint32_t*>(pb + 256 + mask_bytes * (P.root_slot[q] - P.n_inter_slots)));
   r->status = status;
   r->stream = st;
   r->keep.push_back(persist);
@@ -1243,7 +1327,7 @@ VL_API vl_status vl_eval_mode(vl_context* ctx, const vl_formula* f, vl_image* co
     return eval_plain(ctx, f, imgs, n_imgs, S(stream), out);
   vl_job job{f, imgs, n_imgs, 0};
   vl_batch* b = nullptr;
-  vl_status s = batch_build(ctx, &job, 1, S(stream), &b);
+  vl_status s = batch_build(ctx, &job, 1, S(stream), &b, nullptr, true);
   if (s != VL_OK) return s;
   s = batch_run(b, S(stream));
   if (s == VL_OK) batch_release_results(b, out);

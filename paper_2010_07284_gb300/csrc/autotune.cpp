@@ -161,7 +161,7 @@ extern "C" VL_API vl_status vl_autotune(vl_context* ctx, const vl_job* jobs, int
       TileShape t = base;
       t.ctas_per_sm = cps;
       vl_batch* b = nullptr;
-      vl_status s = batch_build(ctx, jobs, n_jobs, st, &b, &t);
+      vl_status s = batch_build(ctx, jobs, n_jobs, st, &b, &t, true);
       double ms = -1;
       if (s == VL_OK) s = batch_run(b, st);  // untimed: builds the graph, warms up
       int32_t word = 0;

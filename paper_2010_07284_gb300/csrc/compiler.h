@@ -86,6 +86,10 @@ struct Plan {
 };
 
 constexpr int MAX_RZ_BATCH = 32;  // selects of one level run together in one step
+// A batch of one job whose plan has at most this many primitives runs the
+// per-operator form (captured in the batch's graph) instead of the
+// persistent executor: a handful of kernels beats a chain of executor steps.
+constexpr int kTinyPlanPrimitives = 24;
 // Rank codes: a channel gets a table when at least this many constant
 // thresholds read it; tables hold at most kRankMaxValues values (codes fit
 // 14 bits) and a formula at most kRankMaxTables tables (one bit each in a

@@ -48,15 +48,17 @@ struct CclGeom {
 // Tile `tile` of an image of H rows, or of a volume stored as its slices of
 // Hs rows stacked (H = depth * Hs; Hs = H for an image): tiles never
 // straddle two slices, so the tile-local labelling stays inside one slice.
-VL_DEV CclGeom ccl_geom(int H, int W, int Wp, int tile, int tiles_x, int Hs) {
+// cth: rows of a tile (an even number up to CCL_TH; smaller tiles give small
+// images more tiles to spread over the GPU).
+VL_DEV CclGeom ccl_geom(int H, int W, int Wp, int tile, int tiles_x, int Hs, int cth = CCL_TH) {
   CclGeom g;
   g.H = H; g.W = W; g.Wp = Wp;
-  const int tys = (Hs + CCL_TH - 1) / CCL_TH;  // tile rows per slice
+  const int tys = (Hs + cth - 1) / cth;  // tile rows per slice
   const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
   const int z = ty / tys, tyz = ty - z * tys;
-  g.r0 = z * Hs + tyz * CCL_TH;
+  g.r0 = z * Hs + tyz * cth;
   g.w0 = tx * CCL_TWW;
-  g.th = min(CCL_TH, Hs - tyz * CCL_TH);
+  g.th = min(cth, Hs - tyz * cth);
   g.tww = min(CCL_TWW, Wp - g.w0);
   return g;
 }
@@ -554,7 +556,7 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
 // union-find state (non-roots: their root; roots: -(representative + 2))
 // and the component flags.  The final pass rebuilds the strips from the mask
 // and reloads this instead of labelling the tile again.
-VL_DEV int ccl_tile_cap(int Wp) { return CCL_NS * min(CCL_TWW, Wp) * 32; }
+VL_DEV int ccl_tile_cap(int Wp, int cth = CCL_TH) { return (cth / 2) * min(CCL_TWW, Wp) * 32; }
 
 VL_DEV void ccl_tile_save(const CclSmem& s, int32_t* tpar, uint8_t* tflag) {
   for (int i = threadIdx.x; i < s.nruns; i += blockDim.x) {
@@ -739,8 +741,8 @@ VL_DEV void ccl_write_select(const CclSmem& s, const CclGeom& g, uint32_t* Z) {
 // instead of one after another.
 // (Hs: slice rows of a volume, H for an image; horizontal borders are those
 // between the tile rows of one slice.)
-VL_DEV int merge_units(int H, int Wp, int tiles_x, int Hs) {
-  const int tys = (Hs + CCL_TH - 1) / CCL_TH;
+VL_DEV int merge_units(int H, int Wp, int tiles_x, int Hs, int cth = CCL_TH) {
+  const int tys = (Hs + cth - 1) / cth;
   return (H / Hs) * (tys - 1) * Wp + (tiles_x - 1) * ((H + 31) >> 5);
 }
 
@@ -813,14 +815,14 @@ VL_DEV void ccl_merge_rows(const uint32_t* m, int W, int Wp, int yu, int yd, int
 }
 
 VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int unit, int conn,
-                           int32_t* G, int glen, int32_t* status, int Hs) {
+                           int32_t* G, int glen, int32_t* status, int Hs, int cth = CCL_TH) {
   const int lane = threadIdx.x & 31;
-  const int tys = (Hs + CCL_TH - 1) / CCL_TH;
+  const int tys = (Hs + cth - 1) / cth;
   const int nh = (H / Hs) * (tys - 1) * Wp;
   if (unit < nh) {
     const int border = unit / Wp, w = unit - border * Wp;  // border: over all slices
     const int z = border / (tys - 1), k = border - z * (tys - 1) + 1;
-    const int yd = z * Hs + k * CCL_TH, yu = yd - 1;
+    const int yd = z * Hs + k * cth, yu = yd - 1;
     ccl_merge_rows(m, W, Wp, yu, yd, w, conn, G, glen, status);
   } else {
     const int nv = (H + 31) >> 5;

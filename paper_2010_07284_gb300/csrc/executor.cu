@@ -165,7 +165,7 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       const int j = sub / per_rz, tile = sub - j * per_rz;
       const RzDesc r = J.rz[S.rz_off + j];
       const int k = r.scratch;
-      const CclGeom geo = ccl_geom(J.H, J.W, J.Wp, tile, J.c_tiles_x, J.H);
+      const CclGeom geo = ccl_geom(J.H, J.W, J.Wp, tile, J.c_tiles_x, J.H, J.c_th);
       const uint32_t* phi1 = J.slots[r.phi1_slot];
       const uint32_t* phi2 = J.slots[r.phi2_slot];
       int32_t* tpar = rz_tpar(J, k) + (size_t)tile * J.tile_cap;
@@ -185,11 +185,11 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
     case SK_RZ_MERGE: {
       const int j = sub / per_rz, chunk = sub - j * per_rz;
       const RzDesc r = J.rz[S.rz_off + j];
-      const int n = merge_units(J.H, J.Wp, J.c_tiles_x, J.H);
+      const int n = merge_units(J.H, J.Wp, J.c_tiles_x, J.H, J.c_th);
       const int nw = blockDim.x >> 5;
       for (int u = chunk * nw + (threadIdx.x >> 5); u < n; u += per_rz * nw)
         ccl_merge_unit(J.slots[r.phi2_slot], J.H, J.W, J.Wp, u, J.conn, rz_G(J, r.scratch),
-                       2 * npx, J.status, J.H);
+                       2 * npx, J.status, J.H, J.c_th);
       break;
     }
     default:

@@ -106,6 +106,80 @@ __global__ void __launch_bounds__(EXEC_THREADS) k_select(const void* plane, int 
   if (threadIdx.x == 0) *out = v;
 }
 
+// Grid-wide radix select for large channels (a volume's 9 M voxels would
+// keep the one-CTA select on a single SM for milliseconds): the same digits
+// (8, 12, 12 bits of the order-preserving key), each pass one histogram
+// kernel over the whole grid (shared-memory bins, then global atomics) and
+// one warp that finds the digit holding the rank.
+struct WideSel {
+  uint32_t prefix, pmask;
+  unsigned long long rank;
+};
+
+__global__ void k_sel_init(WideSel* st, long long rank) {
+  st->prefix = 0;
+  st->pmask = 0;
+  st->rank = (unsigned long long)rank;
+}
+
+__global__ void __launch_bounds__(256) k_sel_hist(const void* plane, int format, int pitch, int H,
+                                                  int W, const WideSel* st, int sh, int nb,
+                                                  uint32_t* hist) {
+  __shared__ uint32_t h[4096];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const uint32_t prefix = st->prefix, pmask = st->pmask;
+  const int lane = threadIdx.x & 31;
+  const long long n = (long long)H * W;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;  // warp-uniform loop: every lane runs the match
+    const bool in = i < n;
+    uint32_t key = 0;
+    if (in) {
+      const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+      key = f2key(ld_px(plane, format, true, (size_t)y * pitch + x));
+    }
+    const bool ok = in && (key & pmask) == prefix;
+    const uint32_t bin = (key >> sh) & (uint32_t)(nb - 1);
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, ok ? bin : 0xFFFFFFFFu);
+    if (ok && lane == __ffs(grp) - 1) atomicAdd(&h[bin], (uint32_t)__popc(grp));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// One warp: lane l sums bins [l * per, (l + 1) * per); a scan finds the lane
+// whose bins hold the rank, which walks them.  The last pass writes the value.
+__global__ void k_sel_pick(const uint32_t* hist, int sh, int nb, WideSel* st, float* out) {
+  const int lane = threadIdx.x;
+  const int per = nb / 32;
+  unsigned long long sum = 0;
+  for (int q = 0; q < per; ++q) sum += hist[lane * per + q];
+  unsigned long long incl = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const unsigned long long rank = st->rank, excl = incl - sum;
+  __syncwarp();
+  if (sum > 0 && excl <= rank && rank < incl) {  // exactly one lane
+    unsigned long long acc = excl;
+    for (int q = 0; q < per; ++q) {
+      const int b = lane * per + q;
+      if (acc + hist[b] > rank) {
+        st->prefix |= (uint32_t)b << sh;
+        st->pmask |= (uint32_t)(nb - 1) << sh;
+        st->rank = rank - acc;
+        if (out) *out = key2f(st->prefix);
+        break;
+      }
+      acc += hist[b];
+    }
+  }
+}
+
 // ----------------------------------------------------------- arithmetic --
 
 // out = a (op) b pixel by pixel over H x W (row pitch `pitch` elements); b
@@ -273,6 +347,28 @@ cudaError_t launch_select(const void* plane, int format, int pitch, int H, int W
   return cudaGetLastError();
 }
 
+size_t select_wide_scratch_bytes() { return 4096 * sizeof(uint32_t) + 256; }
+
+cudaError_t launch_select_wide(const void* plane, int format, int pitch, int H, int W,
+                               long long rank, float* out, void* scratch, cudaStream_t st) {
+  uint32_t* hist = static_cast<uint32_t*>(scratch);
+  WideSel* ws = reinterpret_cast<WideSel*>(static_cast<char*>(scratch) + 4096 * sizeof(uint32_t));
+  k_sel_init<<<1, 1, 0, st>>>(ws, rank);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  const int shifts[3] = {24, 12, 0}, widths[3] = {8, 12, 12};
+  for (int pass = 0; pass < 3; ++pass) {
+    const int nb = 1 << widths[pass];
+    if ((e = cudaMemsetAsync(hist, 0, nb * sizeof(uint32_t), st))) return e;
+    k_sel_hist<<<grid_for((long long)H * W, 256 * 8), 256, 0, st>>>(plane, format, pitch, H, W, ws,
+                                                                   shifts[pass], nb, hist);
+    if ((e = cudaGetLastError())) return e;
+    k_sel_pick<<<1, 32, 0, st>>>(hist, shifts[pass], nb, ws, pass == 2 ? out : nullptr);
+    if ((e = cudaGetLastError())) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_arith(int op, const void* a, int a_format, const void* b, int b_format, float c,
                          float* out, int H, int W, int pitch, cudaStream_t st) {
   k_arith<<<grid_for((long long)H * W, kThreads), kThreads, 0, st>>>(op, a, a_format, b, b_format,
@@ -280,9 +376,9 @@ cudaError_t launch_arith(int op, const void* a, int a_format, const void* b, int
   return cudaGetLastError();
 }
 
-int ccl_tiles_y(int H, int Hs) {
+int ccl_tiles_y(int H, int Hs, int cth) {
   if (Hs <= 0) Hs = H;
-  return (H / Hs) * ((Hs + CCL_TH - 1) / CCL_TH);
+  return (H / Hs) * ((Hs + cth - 1) / cth);
 }
 int ccl_tiles_x(int Wp) { return (Wp + CCL_TWW - 1) / CCL_TWW; }
 size_t ccl_smem_bytes() { return sizeof(CclSmem); }
@@ -295,6 +391,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_attr_mu;
 bool g_attr_done[kMaxDevices] = {};
 }  // namespace
+
+static cudaError_t ccl_set_attrs();
+cudaError_t ccl_configure() { return ccl_set_attrs(); }
 
 static cudaError_t ccl_set_attrs() {
   int dev = 0;
@@ -315,12 +414,12 @@ static cudaError_t ccl_set_attrs() {
   return cudaSuccess;
 }
 
-long long ccl_merge_units(int H, int Wp, int Hs) {
+long long ccl_merge_units(int H, int Wp, int Hs, int cth) {
   if (Hs <= 0) Hs = H;
-  return (long long)(H / Hs) * ((Hs + CCL_TH - 1) / CCL_TH - 1) * Wp +
+  return (long long)(H / Hs) * ((Hs + cth - 1) / cth - 1) * Wp +
          (long long)(ccl_tiles_x(Wp) - 1) * ((H + 31) / 32);
 }
-int ccl_tile_cap_host(int Wp) { return CCL_NS * std::min(CCL_TWW, Wp) * 32; }
+int ccl_tile_cap_host(int Wp, int cth) { return (cth / 2) * std::min(CCL_TWW, Wp) * 32; }
 
 cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScratch sc,
                               int32_t* status, cudaStream_t st) {

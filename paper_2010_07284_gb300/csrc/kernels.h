@@ -31,6 +31,11 @@ cudaError_t launch_near(const uint32_t* a, MaskGeom g, int conn, uint32_t* out,
                         cudaStream_t st);
 cudaError_t launch_select(const void* plane, int format, int pitch, int H, int W, long long rank,
                           float* out, cudaStream_t st);
+// The same over the whole grid, for large channels; scratch: device memory
+// of select_wide_scratch_bytes() (reused call after call on one stream).
+size_t select_wide_scratch_bytes();
+cudaError_t launch_select_wide(const void* plane, int format, int pitch, int H, int W,
+                               long long rank, float* out, void* scratch, cudaStream_t st);
 // out = a (op) b per pixel (op an ArithOp, A_ADD .. A_DIV); b null: the
 // constant c.
 cudaError_t launch_arith(int op, const void* a, int a_format, const void* b, int b_format, float c,
@@ -45,13 +50,18 @@ struct CclScratch {
   int32_t* tpar;    // tiles * tile_cap int32: saved tile union-find state
   uint8_t* tflag;   // tiles * tile_cap bytes: saved tile flags
 };
-int ccl_tiles_y(int H, int Hs = 0);  // tile rows over all slices (Hs 0: an image)
+// Labelling tiles: rows over all slices (Hs 0: an image; cth: rows per
+// tile, even, at most CCL_TH), columns, per-tile saved-state capacity.
+int ccl_tiles_y(int H, int Hs = 0, int cth = CCL_TH);
 int ccl_tiles_x(int Wp);
-int ccl_tile_cap_host(int Wp);
+int ccl_tile_cap_host(int Wp, int cth = CCL_TH);
 // Border merge units (one warp each): words of horizontal tile borders and
 // 32-row pieces of vertical ones.
-long long ccl_merge_units(int H, int Wp, int Hs = 0);
+long long ccl_merge_units(int H, int Wp, int Hs = 0, int cth = CCL_TH);
 size_t ccl_smem_bytes();
+// Set the labelling kernels' shared-memory attribute on the current device
+// (done by every labelling launch; call it before a stream capture).
+cudaError_t ccl_configure();
 
 // Labels: sc.G is the labels array itself (it doubles as the union-find).
 cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScratch sc,

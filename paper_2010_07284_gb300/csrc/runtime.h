@@ -120,8 +120,17 @@ cudaError_t wait_images(vl_image* const* imgs, int n, cudaStream_t st);
 
 // Build a batch (plans, tables, buffers, results) for `jobs`, with the tile
 // shape `force` if given, else the one pick_tile_shape chooses.
+// `persistent`: always the persistent executor (an explicit request for the
+// fused form, and the autotuner's trials); otherwise a lone job with a tiny
+// plan takes the per-operator form captured in the batch's graph.
 vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStream_t st,
-                      vl_batch** out, const TileShape* force = nullptr);
+                      vl_batch** out, const TileShape* force = nullptr, bool persistent = false);
+// The per-operator form of a plan (one launch per primitive), enqueued on
+// `st` without synchronisation or events: roots written at `roots` (root
+// slot s at roots + H*Wp*4 * (s - n_inter_slots)), device errors to
+// *status; capturable into a CUDA graph.
+vl_status plain_enqueue(vl_context* ctx, const Plan& P, vl_image* const* imgs, int H, int W, int D,
+                        char* roots, int32_t* status, cudaStream_t st);
 // Autotuner (autotune.cpp): the tile shape for a batch -- the fixed shape of
 // the context's configuration, else the measured best for the batch's
 // signature, else a heuristic.  *tuned is set to 1 when a measurement chose it.

@@ -202,7 +202,7 @@ struct DevJob {
   int64_t set_bytes;
   int64_t off_tpar, off_tflag;
   int32_t tile_cap;
-  int32_t pad0_;
+  int32_t c_th;                 // rows of a labelling tile (16 or 32)
   int32_t* status;              // device status word of this job
   const RankTab* rtab;          // rank tables of the formula
   const float* rvals;           //   their sorted threshold values

@@ -112,12 +112,16 @@ __global__ void k_relabel(const uint32_t* m, MaskGeom g, int32_t* L, int32_t* st
 }
 
 // F[label] = 1 for every seed voxel (benign races: every writer writes 1).
+// Seeds lie in phi2, so the voxels of a run of seeds in a row share one
+// component: only the first voxel of every run is looked up.
 __global__ void k_seed_flags(const uint32_t* seed, MaskGeom g, const int32_t* L, uint8_t* F) {
   const long long nwords = (long long)g.H * g.Wp;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
        i += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
-    uint32_t bits = __ldg(seed + i) & vmask(w, g.W);
+    const uint32_t cur = __ldg(seed + i) & vmask(w, g.W);
+    const uint32_t prev = w > 0 ? __ldg(seed + i - 1) : 0u;
+    uint32_t bits = cur & ~((cur << 1) | (prev >> 31));
     while (bits) {
       const int b = __ffs(bits) - 1;
       bits &= bits - 1;
@@ -127,19 +131,24 @@ __global__ void k_seed_flags(const uint32_t* seed, MaskGeom g, const int32_t* L,
   }
 }
 
-// Z = the voxels of phi2 whose component is flagged.
+// Z = the voxels of phi2 whose component is flagged: one lookup per run of
+// phi2 inside the word (a run is one component), the run's bits taken whole.
 __global__ void k_select_flagged(const uint32_t* phi2, MaskGeom g, const int32_t* L,
                                  const uint8_t* F, uint32_t* Z) {
   const long long nwords = (long long)g.H * g.Wp;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
        i += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
-    uint32_t bits = __ldg(phi2 + i) & vmask(w, g.W), sel = 0;
-    while (bits) {
-      const int b = __ffs(bits) - 1;
-      bits &= bits - 1;
+    const uint32_t bits = __ldg(phi2 + i) & vmask(w, g.W);
+    uint32_t starts = bits & ~(bits << 1), sel = 0;  // run starts inside this word
+    while (starts) {
+      const int b = __ffs(starts) - 1;
+      starts &= starts - 1;
+      // the run: bits b.. up to the first clear bit
+      const uint32_t from = bits >> b;
+      const uint32_t len_mask = ~from ? ((~from & (0u - ~from)) - 1u) : 0xFFFFFFFFu;
       const int lab = __ldg(L + (size_t)y * g.W + 32 * w + b);
-      if ((unsigned)lab < (unsigned)(g.H * g.W) && F[lab]) sel |= 1u << b;
+      if ((unsigned)lab < (unsigned)(g.H * g.W) && F[lab]) sel |= len_mask << b;
     }
     Z[i] = sel;
   }

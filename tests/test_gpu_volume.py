@@ -116,3 +116,36 @@ def test_volumes_are_refused_by_the_batched_form():
     vol = ctx.volume(wl.mri_phantom_volume(3, 20, 30, seed=0))
     with pytest.raises(Exception):
         ctx.batch([(F, [vol])])
+
+
+@pytest.mark.parametrize("conn", (26, 6))
+def test_large_volume_percentiles_take_the_grid_wide_select(conn):
+    """Above a million voxels the percentile select runs over the whole grid:
+    ties, NaN voxels (sorted last) and ranks at both ends, float32 and
+    uint16, against the oracle's sort."""
+    rng = np.random.default_rng(conn)
+    vol = wl.mri_phantom_volume(20, 70, 1100, seed=4)
+    vol[0, 3, 5, :40] = np.nan
+    vol[1] = np.round(vol[1] * 50) / 50          # many ties
+    recs = [_f("PCT_GT", q=0.0), _f("PCT_GT", q=0.95, channel=1), _f("PCT_LT", q=0.5, channel=0),
+            _f("PCT_LT", q=1.0, channel=1), _f("PCT_GT", q=0.999, channel=2),
+            _f("AND", 1, 2), _f("NEAR", 5)]
+    roots = [0, 1, 2, 3, 4, 6]
+    got = _run(recs, roots, volumes=[vol], conn=conn)
+    exp = oracle.evaluate3(recs, roots, volumes=[vol], conn=conn).masks
+    assert_same(got, exp, f"float32 conn={conn}")
+    v16 = rng.integers(0, 700, size=(2, 12, 300, 400)).astype(np.uint16)
+    got = _run(recs[:2] + [_f("PCT_LT", q=0.3, channel=1)], [0, 1, 2], volumes=[v16], conn=conn)
+    exp = oracle.evaluate3(recs[:2] + [_f("PCT_LT", q=0.3, channel=1)], [0, 1, 2],
+                           volumes=[v16], conn=conn).masks
+    assert_same(got, exp, f"uint16 conn={conn}")
+
+
+def test_large_image_percentiles_in_the_per_operator_form():
+    torch_cuda()
+    img = wl.uniform_image(1100, 1000, channels=2, seed=8)
+    img[1] = np.round(img[1] * 30) / 30
+    img[0, 7, :100] = np.nan
+    recs = [_f("PCT_GT", q=0.25), _f("PCT_LT", q=0.75, channel=1), _f("PCT_GT", q=1.0, channel=1)]
+    from gpu_util import check_formula
+    check_formula(recs, [0, 1, 2], [img], conn=8, modes=("plain", "fused"))
