@@ -363,8 +363,10 @@ def leg_formula_scaling(ctx, stream, flush, image, sizes=(10, 100, 500, 1000, 20
                         runs: int = 3) -> dict:
     """Time against formula size (Sec. 4.1): sequential formulas f(g(...(x)))
     and random DAGs of growing size on the same resident 2048 x 2048 image,
-    the fused persistent form beside the plain per-operator form; at 2000
-    nodes also the deep-N and the reachability chains."""
+    the batched form (tuned per formula: the persistent executor, or the
+    per-operator kernels captured in a graph) beside the plain per-operator
+    form launched one kernel at a time; at 2000 nodes also the deep-N and
+    the reachability chains."""
     import torch
     import workloads as wl
     P = H * W
@@ -372,7 +374,7 @@ def leg_formula_scaling(ctx, stream, flush, image, sizes=(10, 100, 500, 1000, 20
     def timed(F, mode, n):
         ms = []
         with torch.cuda.stream(stream):
-            b = ctx.batch([(F, [image])], stream) if mode == "fused" else None
+            b = ctx.batch([(F, [image])], stream) if mode == "batched" else None
             for k in range(n + 1):
                 flush.zero_()
                 a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -404,10 +406,17 @@ def leg_formula_scaling(ctx, stream, flush, image, sizes=(10, 100, 500, 1000, 20
         f = make(n)
         F = ctx.compile(wl.formula_to_records(f), f.roots, CONN)
         info = F.info()
-        fused = timed(F, "fused", runs)
+        # the batched form as the autotuner leaves it for this job: a tile
+        # shape of the persistent executor, or the per-operator kernels in
+        # a graph (0 x 0)
+        with torch.cuda.stream(stream):
+            best = ctx.autotune([(F, [image])], stream=stream, reps=2)["best"]
+        form = ("per-operator graph" if best["tile_rows"] == 0 else
+                f"executor {best['tile_rows']}x{best['tile_words']}")
+        fused = timed(F, "batched", runs)
         plain = timed(F, "plain", max(2, runs - 1))
         rows.append({"kind": kind, "nodes": n, "n_primitive": info["n_primitive"],
-                     "n_reach": info["n_reach"], "fused_ms": fused, "plain_ms": plain,
+                     "n_reach": info["n_reach"], "form": form, "fused_ms": fused, "plain_ms": plain,
                      "fused_gpixel_ops_s": info["n_primitive"] * P / (fused / 1e3) / 1e9,
                      "fused_over_plain": plain / fused})
         F.close()
@@ -888,8 +897,8 @@ def main():
         rows = scaling["rows"]
         line["formula_scaling"] = {
             "min_fused_over_plain": min(r["fused_over_plain"] for r in rows),
-            "fused_plain_ms": [[r["kind"][:12], r["nodes"], r["fused_ms"], r["plain_ms"]]
-                               for r in rows]}
+            "fused_plain_ms": [[r["kind"][:12], r["nodes"], r["fused_ms"], r["plain_ms"],
+                                "g" if r["form"].startswith("per") else "x"] for r in rows]}
         # ---- CPU oracle on a bounded sample (rank 0 only)
         if rank == 0:
             v, dt, _ = oracle_sample(CPU_ROWS_BASE)

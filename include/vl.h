@@ -414,10 +414,11 @@ typedef struct {
  * one persistent launch; outs[i] receives job i's result.  When the
  * context's use_graphs is set, the launch sequence is captured into a CUDA
  * graph cached by the batch's structure and replayed.  A batch of a single
- * job whose formula has at most 24 primitives (after expansion and
- * sharing) runs the per-operator kernels instead, captured the same way: a
- * handful of kernels beats a chain of executor steps (vl_eval_mode with
- * VL_EXEC_FUSED always takes the persistent launch).  Enqueue only. */
+ * job may run its per-operator kernels instead, captured the same way, when
+ * the tile table (vl_autotune) measured that faster or the formula has at
+ * most 24 primitives (after expansion and sharing): a handful of kernels
+ * beats a chain of executor steps (vl_eval_mode with VL_EXEC_FUSED always
+ * takes the persistent launch).  Enqueue only. */
 VL_API vl_status vl_eval_batch(vl_context* ctx, const vl_job* jobs,
                                int32_t n_jobs, void* stream, vl_result** outs);
 
@@ -453,8 +454,12 @@ VL_API vl_status vl_batch_info(const vl_batch* b, int64_t* n_items, int32_t* gri
  * tiles, thousands of small ones large tiles).  With tile_rows = tile_words
  * = 0 in vl_config, every batch takes the shape this table gives for its
  * signature (the set of formulas, and the number, total and largest sizes
- * of its images, in powers of two), else a heuristic (the largest shape
- * whose tiles per step reach the persistent grid). */
+ * of its images, in powers of two), else a heuristic (for a batch of one
+ * job with at most 24 primitives the per-operator form, else the largest
+ * shape whose tiles per step reach three quarters of the persistent grid).
+ * A choice of 0 x 0 tiles with 0 CTAs per SM stands for the per-operator
+ * form: the batch's single job runs one kernel per primitive, captured in
+ * the batch's graph (the autotuner tries it for batches of one job). */
 typedef struct {
   int32_t tile_rows;    /* rows per fused-group tile */
   int32_t tile_words;   /* 32-px words per fused-group tile */

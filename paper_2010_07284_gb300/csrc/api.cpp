@@ -182,6 +182,9 @@ namespace vl {
 
 int64_t batch_bytes(const vl_batch* b) { return b ? b->bytes : 0; }
 
+vl_status batch_build_per_op(vl_context* ctx, const vl_job& job, int H, int W, cudaStream_t st,
+                             vl_batch** out);
+
 vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStream_t st,
                       vl_batch** out, const TileShape* force, bool persistent) {
   if (n_jobs < 1 || !jobs) return set_err(ctx, VL_ERR_ARG, "empty batch");
@@ -236,7 +239,12 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     f_deps[k] = take(sizeof(int32_t) * std::max<size_t>(1, P->deps.size()));
     f_arith[k] = take(sizeof(ArithInsn) * std::max<size_t>(1, P->arith.size()));
   }
-  const TileShape ts = force ? *force : pick_tile_shape(ctx, jobs, n_jobs);
+  const TileShape ts = force ? *force : pick_tile_shape(ctx, jobs, n_jobs, nullptr, !persistent);
+  if (ts.per_op) {
+    if (n_jobs != 1 || persistent)
+      return set_err(ctx, VL_ERR_ARG, "the per-operator form takes a batch of one job");
+    return batch_build_per_op(ctx, jobs[0], J[0].H, J[0].W, st, out);
+  }
   if (!tile_shape_fits(ctx, ts)) return set_err(ctx, VL_ERR_ARG, "tile shape does not fit shared memory");
   const int cps = ts.ctas_per_sm > 0 ? std::min(ts.ctas_per_sm, ctx->ctas_per_sm) : ctx->ctas_per_sm;
   int total_steps = 0;
@@ -269,7 +277,12 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
         case SK_PCT: n = s.pct_cnt; break;
         case SK_GROUP: n = I.gty * I.gtx; break;
         case SK_RZ_LOCAL: case SK_RZ_FINAL: n = s.rz_cnt * I.ctiles; break;
-        case SK_RZ_MERGE: n = s.rz_cnt * ccl_merge_chunks(I.H, I.Wp, I.cth); break;
+        case SK_RZ_MERGE:
+          // at most one wave of items per step: the merge is latency-bound,
+          // and a second wave would wait for the first
+          n = s.rz_cnt * std::min(ccl_merge_chunks(I.H, I.Wp, I.cth),
+                                  std::max(1, (grid + s.rz_cnt - 1) / s.rz_cnt));
+          break;
         case SK_RANK: n = (int)P.rtab.size() * ((I.H + RANK_ROWS - 1) / RANK_ROWS); break;
         case SK_ARITH: n = (I.H + ARITH_ROWS - 1) / ARITH_ROWS; break;
       }
@@ -519,14 +532,51 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     r->keep.push_back(b->persist);
     b->results.push_back(r);
   }
-  if (!persistent && n_jobs == 1 && J[0].P->n_primitive <= kTinyPlanPrimitives && !ctx->cfg.trace) {
-    b->plain_form = true;
-    b->plain_plan = std::make_shared<Plan>(*J[0].P);
-    b->plain_imgs.assign(jobs[0].images, jobs[0].images + jobs[0].n_images);
-    b->plain_H = J[0].H;
-    b->plain_W = J[0].W;
-    b->plain_roots = pb + J[0].off_roots;
-  }
+  *out = b.release();
+  return VL_OK;
+}
+
+// A batch of one job in the per-operator form: result buffers and status
+// word only; batch_run captures the kernels into the batch's graph.
+vl_status batch_build_per_op(vl_context* ctx, const vl_job& job, int H, int W, cudaStream_t st,
+                             vl_batch** out) {
+  const Plan& P = job.formula->plan;
+  const int Wp = words_per_row(W);
+  const size_t mask_bytes = (size_t)H * Wp * 4;
+  auto b = std::make_unique<vl_batch>();
+  b->ctx = ctx;
+  b->n_jobs = 1;
+  b->images.assign(job.images, job.images + job.n_images);
+  std::sort(b->images.begin(), b->images.end());
+  b->images.erase(std::unique(b->images.begin(), b->images.end()), b->images.end());
+  cudaError_t e = dev_alloc(ctx, 256 + mask_bytes * P.n_root_slots, st, &b->persist);
+  if (e) return cuda_err(ctx, e, "allocating result buffers");
+  b->bytes = (int64_t)(256 + mask_bytes * P.n_root_slots);
+  char* pb = static_cast<char*>(b->persist->ptr);
+  b->status_base = reinterpret_cast<int32_t*>(pb);
+  b->n_status = 1;
+  b->plain_form = true;
+  b->plain_plan = std::make_shared<Plan>(P);
+  b->plain_imgs.assign(job.images, job.images + job.n_images);
+  b->plain_H = H;
+  b->plain_W = W;
+  b->plain_roots = pb + 256;
+  b->done = std::make_shared<EventHolder>();
+  e = cudaEventCreateWithFlags(&b->done->ev, cudaEventDisableTiming);
+  if (e) return cuda_err(ctx, e, "creating an event");
+  auto* r = new vl_result();
+  r->ctx = ctx;
+  r->H = H; r->W = W; r->Wp = Wp;
+  r->n_roots = P.n_roots;
+  for (int q = 0; q < P.n_roots; ++q)
+    r->roots.push_back(reinterpret_cast<uint32_t*>(b->plain_roots +
+                                                   mask_bytes * (P.root_slot[q] - P.n_inter_slots)));
+  r->status = b->status_base;
+  r->stream = st;
+  r->done = b->done;
+  r->borrowed = true;
+  r->keep.push_back(b->persist);
+  b->results.push_back(r);
   *out = b.release();
   return VL_OK;
 }
@@ -534,7 +584,6 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
 vl_status batch_run(vl_batch* b, cudaStream_t st) {
   vl_context* ctx = b->ctx;
   cudaError_t e;
-  char* tb = static_cast<char*>(b->trans->ptr);
   const bool graphs = ctx->cfg.use_graphs && st != nullptr && st != cudaStreamLegacy &&
                       st != cudaStreamPerThread;
   if ((e = wait_images(b->images.data(), (int)b->images.size(), st)))
@@ -575,6 +624,7 @@ vl_status batch_run(vl_batch* b, cudaStream_t st) {
     for (vl_result* r : b->results) r->stream = st;
     return VL_OK;
   }
+  char* tb = static_cast<char*>(b->trans->ptr);
   if (graphs && !b->gexec) {
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e) return cuda_err(ctx, e, "beginning graph capture");
@@ -658,6 +708,8 @@ vl_status plain_enqueue(vl_context* ctx, const Plan& P, vl_image* const* imgs, i
   const bool vol = volume_plan(P);
   MaskGeom g{H, W, Wp};
   if (vol) g.Hs = H / D;
+  // labelling tiles of 16 rows when an image has fewer 32-row tiles than SMs
+  if (!vol && (long long)ccl_tiles_y(H) * ccl_tiles_x(Wp) < ctx->sm_count) g.cth = 16;
   const size_t mask_bytes = (size_t)H * Wp * 4;
   cudaError_t e;
   auto root_buf = [&](int slot) {
@@ -747,8 +799,8 @@ vl_status plain_enqueue(vl_context* ctx, const Plan& P, vl_image* const* imgs, i
     sc3.seed = reinterpret_cast<uint32_t*>(p + oS);
   } else if (!P.rz.empty()) {
     const size_t px = (size_t)H * W;
-    const size_t tiles = (size_t)ccl_tiles_y(H) * ccl_tiles_x(Wp);
-    const int tcap = ccl_tile_cap_host(Wp);
+    const size_t tiles = (size_t)ccl_tiles_y(H, 0, ccl_rows(g)) * ccl_tiles_x(Wp);
+    const int tcap = ccl_tile_cap_host(Wp, ccl_rows(g));
     size_t off = 0;
     auto take = [&](size_t b) { off = align_up(off, 256); size_t o = off; off += b; return o; };
     const size_t oG = take(2 * px * 4), oP = take(tiles * tcap * 4), oT = take(tiles * tcap);

@@ -73,11 +73,13 @@ int64_t group_tiles(const vl_job* jobs, int n, const TileShape& t) {
   return tiles;
 }
 
+// The per-operator form is reported as a 0 x 0 tile with 0 CTAs per SM.
 vl_tile_choice to_choice(const vl_context* ctx, const TileShape& t, int status, double ms) {
   vl_tile_choice c{};
-  c.tile_rows = t.rows;
-  c.tile_words = t.words;
-  c.ctas_per_sm = t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, ctx->ctas_per_sm) : ctx->ctas_per_sm;
+  c.tile_rows = t.per_op ? 0 : t.rows;
+  c.tile_words = t.per_op ? 0 : t.words;
+  c.ctas_per_sm = t.per_op ? 0
+                  : t.ctas_per_sm > 0 ? std::min(t.ctas_per_sm, ctx->ctas_per_sm) : ctx->ctas_per_sm;
   c.status = status;
   c.ms = ms;
   return c;
@@ -101,7 +103,8 @@ bool tile_shape_fits(const vl_context* ctx, const TileShape& t) {
   return bytes <= ctx->exec_smem;
 }
 
-TileShape pick_tile_shape(vl_context* ctx, const vl_job* jobs, int n_jobs, int* tuned) {
+TileShape pick_tile_shape(vl_context* ctx, const vl_job* jobs, int n_jobs, int* tuned,
+                          bool allow_per_op) {
   if (tuned) *tuned = 0;
   if (ctx->cfg.tile_rows > 0 && ctx->cfg.tile_words > 0)
     return TileShape{ctx->cfg.tile_rows, ctx->cfg.tile_words, 0};
@@ -109,20 +112,31 @@ TileShape pick_tile_shape(vl_context* ctx, const vl_job* jobs, int n_jobs, int* 
   if (batch_signature(ctx, jobs, n_jobs, &key)) {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     auto it = ctx->tuned.find(key);
-    if (it != ctx->tuned.end() && tile_shape_fits(ctx, it->second)) {
+    if (it != ctx->tuned.end() && tile_shape_fits(ctx, it->second) &&
+        (allow_per_op || !it->second.per_op)) {
       if (tuned) *tuned = 1;
       return it->second;
     }
   } else {
     return TileShape{};  // batch_build reports the bad handle
   }
-  // heuristic: the largest shape whose tiles per step fill the grid
+  // a lone job with a tiny plan: its per-operator kernels (a handful of
+  // launches beats a chain of executor steps)
+  if (allow_per_op && n_jobs == 1 && jobs[0].formula->plan.n_primitive <= kTinyPlanPrimitives &&
+      !ctx->cfg.trace) {
+    TileShape t{};
+    t.per_op = true;
+    return t;
+  }
+  // heuristic: the largest shape whose tiles per step fill three quarters
+  // of the grid (smaller tiles pay more halo than the last CTAs bring: on
+  // a 2048 x 2048 image 32 x 16 tiles, 256 of them, beat 16 x 16 by a fifth)
   const int64_t grid = (int64_t)ctx->sm_count * ctx->ctas_per_sm;
   TileShape last{};
   for (const TileShape& t : kShapes) {
     if (!tile_shape_fits(ctx, t)) continue;
     last = t;
-    if (group_tiles(jobs, n_jobs, t) >= grid) return t;
+    if (4 * group_tiles(jobs, n_jobs, t) >= 3 * grid) return t;
   }
   return last;
 }
@@ -154,14 +168,27 @@ extern "C" VL_API vl_status vl_autotune(vl_context* ctx, const vl_job* jobs, int
   if (ce) rc = cuda_err(ctx, ce, "creating timing events");
   std::vector<int> cps_list{ctx->ctas_per_sm};
   if (ctx->ctas_per_sm > 1) cps_list.push_back(1);
+  // candidates: every tile shape and CTA count of the persistent executor,
+  // and for a batch of one job its per-operator kernels in a graph
+  std::vector<TileShape> cands;
   for (const TileShape& base : kShapes) {
-    if (rc != VL_OK) break;
     if (!tile_shape_fits(ctx, base)) continue;
     for (int cps : cps_list) {
       TileShape t = base;
       t.ctas_per_sm = cps;
+      cands.push_back(t);
+    }
+  }
+  if (n_jobs == 1) {
+    TileShape t{};
+    t.per_op = true;
+    cands.push_back(t);
+  }
+  for (const TileShape& t : cands) {
+    if (rc != VL_OK) break;
+    {
       vl_batch* b = nullptr;
-      vl_status s = batch_build(ctx, jobs, n_jobs, st, &b, &t, true);
+      vl_status s = batch_build(ctx, jobs, n_jobs, st, &b, &t, !t.per_op);
       double ms = -1;
       if (s == VL_OK) s = batch_run(b, st);  // untimed: builds the graph, warms up
       int32_t word = 0;
@@ -223,9 +250,10 @@ extern "C" VL_API vl_status vl_tune_save(vl_context* ctx, const char* path) {
   if (!fh) return set_err(ctx, VL_ERR_ARG, std::string("cannot write ") + path);
   std::lock_guard<std::mutex> g(ctx->tune_mu);
   std::fprintf(fh, "vl-tile-table 1 sm_count %d\n", ctx->sm_count);
-  for (const auto& kv : ctx->tuned)
-    std::fprintf(fh, "%016llx %d %d %d\n", (unsigned long long)kv.first, kv.second.rows,
-                 kv.second.words, kv.second.ctas_per_sm);
+  for (const auto& kv : ctx->tuned)  // the per-operator form as 0 0 0
+    std::fprintf(fh, "%016llx %d %d %d\n", (unsigned long long)kv.first,
+                 kv.second.per_op ? 0 : kv.second.rows, kv.second.per_op ? 0 : kv.second.words,
+                 kv.second.per_op ? 0 : kv.second.ctas_per_sm);
   const bool ok = std::fclose(fh) == 0;
   return ok ? VL_OK : set_err(ctx, VL_ERR_ARG, std::string("cannot write ") + path);
 }
@@ -248,7 +276,10 @@ extern "C" VL_API vl_status vl_tune_load(vl_context* ctx, const char* path) {
   int r = 0, w = 0, c = 0;
   while (std::fscanf(fh, "%llx %d %d %d", &key, &r, &w, &c) == 4) {
     TileShape t{r, w, c};
-    if (r < 1 || w < 1 || c < 0 || !tile_shape_fits(ctx, t)) {
+    if (r == 0 && w == 0 && c == 0) {
+      t = TileShape{};
+      t.per_op = true;
+    } else if (r < 1 || w < 1 || c < 0 || !tile_shape_fits(ctx, t)) {
       std::fclose(fh);
       return set_err(ctx, VL_ERR_ARG, "tile table entry does not fit this context");
     }

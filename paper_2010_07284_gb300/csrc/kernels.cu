@@ -211,7 +211,7 @@ k_ccl_local(const uint32_t* mask, const uint32_t* phi1, MaskGeom g, int tiles_x,
             CclScratch sc, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
-  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x, slice_rows(g));
+  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x, slice_rows(g), ccl_rows(g));
   const int npx = g.H * g.W;
   const bool labels = phi1 == nullptr;  // full labelling: canonical minimum pixel
   if (!ccl_tile_label(s, mask, phi1, geo, conn, labels, status)) return;
@@ -226,10 +226,10 @@ k_ccl_local(const uint32_t* mask, const uint32_t* phi1, MaskGeom g, int tiles_x,
 __global__ void k_ccl_merge(const uint32_t* mask, MaskGeom g, int tiles_x, int conn, int32_t* G,
                             int glen, int32_t* status) {
   const int Hs = slice_rows(g);
-  const int n = merge_units(g.H, g.Wp, tiles_x, Hs);
+  const int n = merge_units(g.H, g.Wp, tiles_x, Hs, ccl_rows(g));
   const int wpb = blockDim.x >> 5;
   for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < n; u += gridDim.x * wpb)
-    ccl_merge_unit(mask, g.H, g.W, g.Wp, u, conn, G, glen, status, Hs);
+    ccl_merge_unit(mask, g.H, g.W, g.Wp, u, conn, G, glen, status, Hs, ccl_rows(g));
 }
 
 __global__ void __launch_bounds__(EXEC_THREADS, 2)
@@ -237,7 +237,7 @@ k_ccl_final_labels(const uint32_t* mask, MaskGeom g, int tiles_x, int conn, CclS
                    int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
-  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x, slice_rows(g));
+  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x, slice_rows(g), ccl_rows(g));
   const int npx = g.H * g.W;
   if (!ccl_tile_load(s, mask, geo, conn, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
                      sc.tflag + (size_t)blockIdx.x * sc.tile_cap, status))
@@ -251,7 +251,7 @@ k_rz_final(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, int tiles_x, 
            CclScratch sc, uint32_t* Z, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CclSmem& s = *reinterpret_cast<CclSmem*>(smem_raw);
-  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x, slice_rows(g));
+  const CclGeom geo = ccl_geom(g.H, g.W, g.Wp, blockIdx.x, tiles_x, slice_rows(g), ccl_rows(g));
   const int npx = g.H * g.W;
   if (!ccl_tile_load(s, phi2, geo, conn, sc.tpar + (size_t)blockIdx.x * sc.tile_cap,
                      sc.tflag + (size_t)blockIdx.x * sc.tile_cap, status))
@@ -425,12 +425,12 @@ cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScr
                               int32_t* status, cudaStream_t st) {
   cudaError_t e = ccl_set_attrs();
   if (e) return e;
-  const int ty = ccl_tiles_y(g.H, g.Hs), tx = ccl_tiles_x(g.Wp);
+  const int ty = ccl_tiles_y(g.H, g.Hs, ccl_rows(g)), tx = ccl_tiles_x(g.Wp);
   const size_t sm = sizeof(CclSmem);
   int32_t* labels = sc.G;
   k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(mask, nullptr, g, tx, conn, sc, status);
   if ((e = cudaGetLastError())) return e;
-  const long long nm = ccl_merge_units(g.H, g.Wp, g.Hs) * 32LL;
+  const long long nm = ccl_merge_units(g.H, g.Wp, g.Hs, ccl_rows(g)) * 32LL;
   if (nm > 0) {
     k_ccl_merge<<<grid_for(nm, kThreads), kThreads, 0, st>>>(mask, g, tx, conn, labels,
                                                              g.H * g.W, status);
@@ -444,11 +444,11 @@ cudaError_t launch_rz(const uint32_t* phi1, const uint32_t* phi2, MaskGeom g, in
                       CclScratch sc, uint32_t* Z, int32_t* status, cudaStream_t st) {
   cudaError_t e = ccl_set_attrs();
   if (e) return e;
-  const int ty = ccl_tiles_y(g.H, g.Hs), tx = ccl_tiles_x(g.Wp);
+  const int ty = ccl_tiles_y(g.H, g.Hs, ccl_rows(g)), tx = ccl_tiles_x(g.Wp);
   const size_t sm = sizeof(CclSmem);
   k_ccl_local<<<ty * tx, EXEC_THREADS, sm, st>>>(phi2, phi1, g, tx, conn, sc, status);
   if ((e = cudaGetLastError())) return e;
-  const long long nm = ccl_merge_units(g.H, g.Wp, g.Hs) * 32LL;
+  const long long nm = ccl_merge_units(g.H, g.Wp, g.Hs, ccl_rows(g)) * 32LL;
   if (nm > 0) {
     k_ccl_merge<<<grid_for(nm, kThreads), kThreads, 0, st>>>(phi2, g, tx, conn, sc.G,
                                                              2 * g.H * g.W, status);

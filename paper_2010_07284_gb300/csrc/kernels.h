@@ -12,8 +12,10 @@ struct MaskGeom {
   int H, W, Wp;
   int Hs = 0;  // a volume stored as its slices stacked: rows per slice (H =
                // depth * Hs); 0 for an image
+  int cth = 0; // rows of a labelling tile (even, at most CCL_TH); 0: CCL_TH
 };
 inline __host__ __device__ int slice_rows(const MaskGeom& g) { return g.Hs > 0 ? g.Hs : g.H; }
+inline __host__ __device__ int ccl_rows(const MaskGeom& g) { return g.cth > 0 ? g.cth : CCL_TH; }
 
 // ---- plain per-operator kernels (one launch per primitive) ----
 // `plane`: one channel of H x pitch elements, float or uint16 by `format`.
@@ -64,6 +66,9 @@ size_t ccl_smem_bytes();
 cudaError_t ccl_configure();
 
 // Labels: sc.G is the labels array itself (it doubles as the union-find).
+// Tiles of ccl_rows(g) rows: sc.tpar / sc.tflag hold ccl_tiles_y(H, Hs,
+// ccl_rows(g)) * ccl_tiles_x(Wp) tiles of ccl_tile_cap_host(Wp, ccl_rows(g)).
+// The same for launch_rz.
 cudaError_t launch_ccl_labels(const uint32_t* mask, MaskGeom g, int conn, CclScratch sc,
                               int32_t* status, cudaStream_t st);
 // Component select Z (rho core): Z = phi2-components meeting N phi1.

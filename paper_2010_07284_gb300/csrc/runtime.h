@@ -41,6 +41,9 @@ using DevBlockPtr = std::shared_ptr<DevBlock>;
 // rows x words (32-px words) per tile, CTAs per SM (0 = as many as fit).
 struct TileShape {
   int rows = 32, words = 32, ctas_per_sm = 0;
+  // a batch of one job: its per-operator kernels captured in the batch's
+  // graph instead of the persistent executor (tiles then unused)
+  bool per_op = false;
 };
 
 }  // namespace vl
@@ -134,7 +137,9 @@ vl_status plain_enqueue(vl_context* ctx, const Plan& P, vl_image* const* imgs, i
 // Autotuner (autotune.cpp): the tile shape for a batch -- the fixed shape of
 // the context's configuration, else the measured best for the batch's
 // signature, else a heuristic.  *tuned is set to 1 when a measurement chose it.
-TileShape pick_tile_shape(vl_context* ctx, const vl_job* jobs, int n_jobs, int* tuned = nullptr);
+// allow_per_op = false: only shapes of the persistent executor.
+TileShape pick_tile_shape(vl_context* ctx, const vl_job* jobs, int n_jobs, int* tuned = nullptr,
+                          bool allow_per_op = true);
 // Whether the group buffers of this shape fit the executor's shared memory.
 bool tile_shape_fits(const vl_context* ctx, const TileShape& t);
 uint64_t plan_hash(const Plan& P);

@@ -88,3 +88,51 @@ def test_fixed_shape_context_refuses_autotune_and_bad_tables(tmp_path):
         ctx.load_tuning(bad)
     with pytest.raises(vg.VlError):
         vg.Context(tile_rows=32, tile_words=0)
+
+
+def test_one_job_batches_can_take_the_per_operator_form(tmp_path):
+    """A batch of one job whose formula is tiny takes the per-operator form
+    (reported as a 0 x 0 tile); the autotuner tries that form for every
+    batch of one job; both forms, replayed, give the oracle's masks; a
+    saved table keeps the per-operator choice."""
+    torch = torch_cuda()
+    import paper_2010_07284_gb300 as vg
+    ctx = vg.Context()
+    img = wl.gaussian_field_image(300, 700, seed=2)
+    h = ctx.image(img)
+    tiny = wl.config1_formula()
+    F = ctx.compile(wl.formula_to_records(tiny), tiny.roots, 8)
+    assert ctx.tile_shape([(F, [h])])["tile_rows"] == 0
+    exp = oracle.evaluate(wl.formula_to_records(tiny), tiny.roots, [img], conn=8).masks
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = ctx.batch([(F, [h])], stream)
+        for _ in range(3):
+            b.run(stream)
+        stream.synchronize()
+        r = b.result(0)
+        assert r.sync() == 0
+        assert_same([r.mask(k) for k in range(len(tiny.roots))], exp, "per-operator batch")
+        b.close()
+    big = wl.sequential_dag(200, seed=4, mix="reach")
+    G = ctx.compile(wl.formula_to_records(big), big.roots, 8)
+    with torch.cuda.stream(stream):
+        tune = ctx.autotune([(G, [h])], stream=stream, reps=1)
+        assert any(t["tile_rows"] == 0 and t["status"] == 0 for t in tune["trials"])
+        b = ctx.batch([(G, [h])], stream)
+        for _ in range(2):
+            b.run(stream)
+        stream.synchronize()
+        r = b.result(0)
+        assert r.sync() == 0
+        got = [r.mask(k) for k in range(len(big.roots))]
+        b.close()
+    exp = oracle.evaluate(wl.formula_to_records(big), big.roots, [img], conn=8).masks
+    assert_same(got, exp, f"tuned batch ({tune['best']})")
+    path = str(tmp_path / "tiles.txt")
+    ctx.save_tuning(path)
+    ctx2 = vg.Context()
+    ctx2.load_tuning(path)
+    G2 = ctx2.compile(wl.formula_to_records(big), big.roots, 8)
+    h2 = ctx2.image(img)
+    assert ctx2.tile_shape([(G2, [h2])])["tile_rows"] == tune["best"]["tile_rows"]
