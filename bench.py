@@ -554,14 +554,25 @@ def leg_mri_batch(ctx, stream, flush, peak: float, n_images: int = 4096, reps: i
                                      "unit": "Gpixel-ops/s"}}
 
 
-def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formulas: int = 48,
-                load: float = 0.8) -> dict:
-    """Query stream: square U[0,1) images with sides log-uniform over
-    [128, 4096] resident in HBM, formulas of 10-2000 nodes drawn like the
-    random formula; first all queries at once (saturated throughput), then
-    Poisson arrivals at `load` x that rate (latency; also at 0.5 and 0.95 of
-    it), then the plain form one
-    query at a time on a sample."""
+def device_uniform(side: int, seed: int):
+    """A side x side U[0,1) float32 image drawn on the GPU from a seeded
+    generator (the serving pool is too large to draw on the host); the same
+    call gives the same image again (for the oracle's sample)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    return torch.rand((1, side, side), generator=g, device="cuda", dtype=torch.float32)
+
+
+def leg_serving(ctx, stream, n_queries: int = 20000, n_images: int = 512, n_formulas: int = 96,
+                load: float = 0.8, n_other: int = 3000) -> dict:
+    """Query stream: a pool of 512 square U[0,1) images with sides
+    log-uniform over [128, 4096] resident in HBM, a pool of formulas of
+    10-2000 nodes drawn like the random formula (depth cap min(500, n));
+    20000 queries (image and formula drawn uniformly from the pools): first
+    all at once (saturated throughput), then Poisson arrivals at `load` x
+    that rate (p50 / p99 latency); the other arrival rates (0.5 and 0.95 x)
+    on the first `n_other` queries; the plain form one query at a time on a
+    sample; the oracle on every host core on a bounded sample."""
     import torch
     import paper_2010_07284_gb300 as vg
     import workloads as wl
@@ -569,9 +580,12 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
     rng = np.random.default_rng(5)
     sides = pool_sides(n_images, seed=1)
     with torch.cuda.stream(stream):
-        pool = [ctx.image(wl.uniform_image(int(sd), int(sd), seed=100 + k), stream)
-                for k, sd in enumerate(sides)]
-        stream.synchronize()
+        pool = []
+        for k, sd in enumerate(sides):
+            t = device_uniform(int(sd), 100 + k)
+            pool.append(ctx.image(t, stream))
+            stream.synchronize()
+            del t
     sizes = np.rint(np.exp(np.log(10) + rng.random(n_formulas) * (np.log(2000) - np.log(10)))).astype(int)
     forms = []
     for k, n in enumerate(sizes):
@@ -582,42 +596,58 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
     qf = rng.integers(0, n_formulas, size=n_queries)
     work = float(sum(prims[f] * int(sides[i]) ** 2 for i, f in zip(qi, qf)))
 
-    def run(arrivals):
+    def run(arrivals, nq):
+        """Submit nq queries (at the arrival times, or all at once) while a
+        client thread takes the results in submission order and frees them
+        (a result holds its root masks on the device until it is freed)."""
+        import queue
         srv = vg.Server(ctx, max_inflight_batches=3, max_batch_jobs=64, batch_window_us=200)
+        tickets = queue.Queue()
+        failure = []
+
+        def drain():
+            for k in range(nq):
+                t = tickets.get()
+                st, res = srv.wait(t, timeout_us=300_000_000)
+                if st != 0:
+                    failure.append(f"serving: query {k} (side {int(sides[qi[k]])}, "
+                                   f"{int(sizes[qf[k]])} nodes) status {st}: {ctx.last_error()}; "
+                                   f"server {json.dumps(srv.stats())}")
+                    return
+                res.close()
+
+        client = threading.Thread(target=drain)
         t0 = time.perf_counter()
-        tickets = []
-        for k in range(n_queries):
+        client.start()
+        for k in range(nq):
             if arrivals is not None:
                 dt = arrivals[k] - (time.perf_counter() - t0)
                 if dt > 0:
                     time.sleep(dt)
-            tickets.append(srv.submit(forms[qf[k]], [pool[qi[k]]]))
-        for t in tickets:
-            st, res = srv.wait(t, timeout_us=120_000_000)
-            if st != 0:
-                raise SystemExit(f"serving: query status {st}")
-            res.close()
+            tickets.put(srv.submit(forms[qf[k]], [pool[qi[k]]]))
+        client.join()
         wall = time.perf_counter() - t0
+        if failure:
+            raise SystemExit(failure[0])
         stats = srv.stats()
         srv.close()
         return wall, stats
 
-    wall_sat, st_sat = run(None)
+    wall_sat, st_sat = run(None, n_queries)
     rate = n_queries / wall_sat
 
-    def poisson(ld):
-        gaps = rng.exponential(1.0 / (ld * rate), size=n_queries)
+    def poisson(ld, nq):
+        gaps = rng.exponential(1.0 / (ld * rate), size=nq)
         arrivals = np.cumsum(gaps) - gaps[0]
-        wall, st = run(arrivals)
-        return wall, st
+        return run(arrivals, nq)
 
-    wall_p, st_p = poisson(load)
-    # the other arrival rates the workload names (0.5 and 0.95 of saturation)
+    wall_p, st_p = poisson(load, n_queries)
     others = []
     for ld in (0.5, 0.95):
-        w, st = poisson(ld)
-        others.append({"load": ld, "rate_per_s": ld * rate, "queries_per_s": n_queries / w,
-                       "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "batches": st["batches"]})
+        w, st = poisson(ld, n_other)
+        others.append({"load": ld, "queries": n_other, "rate_per_s": ld * rate,
+                       "queries_per_s": n_other / w, "p50_ms": st["p50_ms"],
+                       "p99_ms": st["p99_ms"], "batches": st["batches"]})
     # plain form, one query at a time, on a sample
     sample = range(0, n_queries, max(1, n_queries // 100))
     swork = float(sum(prims[qf[k]] * int(sides[qi[k]]) ** 2 for k in sample))
@@ -631,21 +661,21 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
     plain_s = time.perf_counter() - t0
     for im in pool:
         im.close()
-    # the oracle on every host core over a seeded 1 % sample of the queries,
-    # restricted to images of at most 1024^2 (a 4096^2 query with a
+    # the oracle on every host core over a seeded draw of at most 64 of the
+    # queries whose images are at most 1024^2 (a 4096^2 query with a
     # 2000-node formula takes the oracle minutes; the whole stream would take
-    # core-hours)
+    # core-days)
     order = np.random.default_rng(9).permutation(n_queries)
-    pick = [int(k) for k in order if int(sides[qi[k]]) <= 1024][: max(1, n_queries // 100)]
+    pick = [int(k) for k in order if int(sides[qi[k]]) <= 1024][:64]
     tasks = []
     for k in pick:
         fd = wl.random_dag(int(sizes[qf[k]]), seed=1000 + int(qf[k]), max_depth=min(500, int(sizes[qf[k]])))
-        sd = int(sides[qi[k]])
-        tasks.append((wl.formula_to_records(fd), fd.roots, wl.uniform_image(sd, sd, seed=100 + int(qi[k]))))
+        img = device_uniform(int(sides[qi[k]]), 100 + int(qi[k])).cpu().numpy()
+        tasks.append((wl.formula_to_records(fd), fd.roots, img))
     cpu = oracle_all_cores(tasks)
-    return {"queries": n_queries, "pool_images": n_images,
+    return {"queries": n_queries, "pool_images": n_images, "pool_formulas": n_formulas,
             "workload": f"{n_queries} queries over {n_images} resident images (sides log-uniform "
-                        f"128-4096), {n_formulas} formulas of 10-2000 nodes, 8-adjacency",
+                        f"128-4096) and {n_formulas} formulas of 10-2000 nodes, 8-adjacency",
             "saturated": {"queries_per_s": rate, "value": work / wall_sat / 1e9,
                           "unit": "Gpixel-ops/s", "p50_ms": st_sat["p50_ms"], "p99_ms": st_sat["p99_ms"],
                           "batches": st_sat["batches"]},
@@ -656,7 +686,7 @@ def leg_serving(ctx, stream, n_queries: int = 1500, n_images: int = 64, n_formul
             "plain_one_at_a_time": {"queries": len(sample), "queries_per_s": len(sample) / plain_s,
                                     "value": swork / plain_s / 1e9, "unit": "Gpixel-ops/s"},
             "cpu_oracle_all_cores": {"kind": "oracle", "cores": cpu["cores"],
-                                     "sample": f"{cpu['tasks']} queries (seeded 1 % draw, sides <= 1024)",
+                                     "sample": f"{cpu['tasks']} queries (seeded draw, sides <= 1024)",
                                      "cpu_s_per_query": cpu["task_s"] / max(1, cpu["tasks"]),
                                      "queries_per_s": cpu["tasks"] / cpu["wall_s"],
                                      "value": cpu["pixel_ops"] / cpu["wall_s"] / 1e9,
@@ -698,7 +728,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain/ccl/e2e/cpu legs")
-    ap.add_argument("--leg", default="", choices=["", "ccl", "scaling", "volume"],
+    ap.add_argument("--leg", default="", choices=["", "ccl", "scaling", "volume", "serving"],
                     help="run only this leg and print its figures (for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -728,6 +758,10 @@ def main():
         stream = torch.cuda.Stream()
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         print(json.dumps({"leg": "ccl", **leg_ccl(ctx, stream, flush, measured_peaks()[0])}), flush=True)
+        return
+    if args.leg == "serving":
+        stream = torch.cuda.Stream()
+        print(json.dumps({"leg": "serving", **leg_serving(ctx, stream)}), flush=True)
         return
     if args.leg == "volume":
         stream = torch.cuda.Stream()

@@ -617,7 +617,12 @@ typedef struct {
 /* Start a serving loop on its own host thread.  Queries are admitted while
  * their device memory fits the budget and a batch slot is free; admitted
  * queries are packed into persistent launches on rotating streams, so new
- * arrivals run while earlier batches are still on the GPU. */
+ * arrivals run while earlier batches are still on the GPU.  The budget
+ * (memory_budget, else the free device memory at creation, after the
+ * stream-ordered pool has handed back what it held free, minus a reserve)
+ * covers the work in flight; a finished query's result keeps its root
+ * masks on the device until the caller frees it, so a client should take
+ * and free results as they complete. */
 VL_API vl_status vl_server_create(vl_context* ctx, const vl_server_config* cfg,
                                   vl_server** out);
 

@@ -47,6 +47,15 @@ cudaError_t dev_alloc(vl_context* ctx, size_t bytes, cudaStream_t st, DevBlockPt
   b->device = ctx->device;
   if (bytes) {
     cudaError_t e = cudaMallocAsync(&b->ptr, bytes, st);
+    if (e == cudaErrorMemoryAllocation) {
+      // the pool keeps freed memory (its release threshold is unlimited, so
+      // graph replays never give memory back); blocks of other sizes can
+      // fill the device: hand the free ones back and try once more
+      cudaGetLastError();
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+      e = cudaMallocAsync(&b->ptr, bytes, st);
+    }
     if (e != cudaSuccess) {
       b->ptr = nullptr;
       return e;
@@ -172,6 +181,7 @@ struct vl_batch {
   // the graph instead (the persistent launch's step latencies would
   // dominate it): its plan, images and shape.
   bool plain_form = false;
+  int plain_runs = 0;                   // the graph is captured on the second run
   std::shared_ptr<vl::Plan> plain_plan;
   std::vector<vl_image*> plain_imgs;
   int plain_H = 0, plain_W = 0;
@@ -602,7 +612,10 @@ vl_status batch_run(vl_batch* b, cudaStream_t st) {
       return plain_enqueue(ctx, *b->plain_plan, b->plain_imgs.data(), b->plain_H, b->plain_W, 1,
                            b->plain_roots, b->status_base, st);
     };
-    if (graphs && !b->gexec) {
+    // a batch run once (a server's) is not worth a capture, and its graph's
+    // memory nodes would keep their memory from the pool: capture on the
+    // second run
+    if (graphs && !b->gexec && b->plain_runs++ > 0) {
       if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)))
         return cuda_err(ctx, e, "beginning graph capture");
       const vl_status s1 = enqueue();
@@ -685,6 +698,9 @@ void batch_destroy(vl_batch* b) {
   }
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  // the per-operator graph allocated its intermediates through graph memory
+  // nodes: give that memory back to the device for the stream-ordered pool
+  if (b->plain_form && b->gexec) cudaDeviceGraphMemTrim(b->ctx->device);
   b->tag = TAG_DEAD;
   delete b;
 }

@@ -190,7 +190,10 @@ extern "C" VL_API vl_status vl_autotune(vl_context* ctx, const vl_job* jobs, int
       vl_batch* b = nullptr;
       vl_status s = batch_build(ctx, jobs, n_jobs, st, &b, &t, !t.per_op);
       double ms = -1;
-      if (s == VL_OK) s = batch_run(b, st);  // untimed: builds the graph, warms up
+      // untimed: builds the graph (the per-operator form captures it on its
+      // second run), warms up
+      if (s == VL_OK) s = batch_run(b, st);
+      if (s == VL_OK && t.per_op) s = batch_run(b, st);
       int32_t word = 0;
       if (s == VL_OK) s = batch_read_status(b, st, &word);
       if (s == VL_OK && word) s = (word & 0xFF) == VL_ERR_TIMEOUT ? VL_ERR_TIMEOUT : VL_ERR_INTERNAL;

@@ -255,6 +255,10 @@ VL_API vl_status vl_server_create(vl_context* ctx, const vl_server_config* cfg, 
   cudaSetDevice(ctx->device);
   int64_t budget = s->cfg.memory_budget > 0 ? s->cfg.memory_budget : ctx->cfg.memory_budget;
   if (budget <= 0) {
+    // the stream-ordered pool keeps what earlier batches freed; hand the
+    // free part back first, so that free device memory counts it
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       delete s;

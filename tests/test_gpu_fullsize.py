@@ -80,6 +80,32 @@ def test_random_formula_2048_seed1_conn4():
     assert_same([res.mask(r) for r in range(len(f.roots))], exp, "seed 1 conn 4")
 
 
+def test_random_formula_2048_seed2_batched():
+    """The third seeded 2000-node formula at full size (2048 x 2048, 8-
+    adjacency), in a prepared batch with the tuned tile shape, every root
+    against the oracle."""
+    torch = torch_cuda()
+    import paper_2010_07284_gb300 as vg
+    f = wl.random_dag(2000, seed=2)
+    rec = wl.formula_to_records(f)
+    img = wl.uniform_image(2048, 2048, seed=2)
+    exp = oracle.evaluate(rec, f.roots, [img], conn=8).masks
+    ctx = vg.Context()
+    F = ctx.compile(rec, f.roots, 8)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        im = ctx.image(img, s)
+        ctx.autotune([(F, [im])], stream=s, reps=1)
+        b = ctx.batch([(F, [im])], s)
+        b.run(s)
+        s.synchronize()
+        res = b.result(0)
+        assert res.sync() == 0, ctx.last_error()
+        got = [res.mask(r) for r in range(len(f.roots))]
+        b.close()
+    assert_same(got, exp, "seed 2 conn 8")
+
+
 def test_mri_batch_4096_autotuned():
     """4096 MRI-shaped images (sides 160..512, median 240, 4 channels), the
     fixed 40-primitive formula with percentile thresholds, one persistent

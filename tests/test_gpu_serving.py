@@ -125,3 +125,52 @@ def test_serving_mixes_number_terms_and_uint16_images():
         for r, e in enumerate(exp):
             assert np.array_equal(res.mask(r), e), f"ticket {t} root {r}"
     srv.close()
+
+
+def test_large_queries_in_the_mix_match_the_oracle():
+    """Queries at the large end of the serving stream -- 2048 x 2048 and
+    2304 x 2048 images with formulas of 1000 and more nodes -- submitted
+    while a burst of small queries is in flight, checked against the CPU
+    oracle root by root; a seeded sample of the small ones too."""
+    torch_cuda()
+    import oracle
+    import paper_2010_07284_gb300 as vg
+    ctx = context()
+    rng = np.random.default_rng(77)
+    small_imgs = [wl.uniform_image(int(s), int(s) + 40, seed=500 + k)
+                  for k, s in enumerate(rng.integers(128, 600, size=5))]
+    small_h = [ctx.image(im) for im in small_imgs]
+    big_imgs = [wl.uniform_image(2048, 2048, seed=601), wl.uniform_image(2304, 2048, seed=602)]
+    big_h = [ctx.image(im) for im in big_imgs]
+    big_f = [wl.random_dag(1000, seed=611, max_depth=500), wl.random_dag(1400, seed=612, max_depth=500)]
+    big_F = [ctx.compile(wl.formula_to_records(f), f.roots, 8) for f in big_f]
+    small = []
+    for k in range(30):
+        n = int(np.exp(rng.uniform(np.log(10), np.log(400))))
+        f = wl.random_dag(n, seed=700 + k, max_depth=min(500, n))
+        small.append((f, ctx.compile(wl.formula_to_records(f), f.roots, 8), int(rng.integers(0, 5))))
+    srv = vg.Server(ctx, max_inflight_batches=3, max_batch_jobs=16, batch_window_us=100)
+    tickets = []
+    for k, (f, F, i) in enumerate(small):
+        tickets.append(("small", k, srv.submit(F, [small_h[i]])))
+        if k == 10:
+            for j in range(2):
+                tickets.append(("big", j, srv.submit(big_F[j], [big_h[j]])))
+    got = {}
+    for kind, k, t in tickets:
+        st, res = srv.wait(t, timeout_us=120_000_000)
+        assert st == 0, f"{kind} {k}: status {st}"
+        nr = len((big_f[k] if kind == "big" else small[k][0]).roots)
+        got[(kind, k)] = [res.mask(q) for q in range(nr)]
+        res.close()
+    srv.close()
+    for j in range(2):
+        f = big_f[j]
+        exp = oracle.evaluate(wl.formula_to_records(f), f.roots, [big_imgs[j]], conn=8).masks
+        for r, (g, e) in enumerate(zip(got[("big", j)], exp)):
+            assert np.array_equal(g, e), f"large query {j} root {r}"
+    for k in np.random.default_rng(5).choice(len(small), size=8, replace=False):
+        f, _, i = small[int(k)]
+        exp = oracle.evaluate(wl.formula_to_records(f), f.roots, [small_imgs[i]], conn=8).masks
+        for r, (g, e) in enumerate(zip(got[("small", int(k))], exp)):
+            assert np.array_equal(g, e), f"small query {k} root {r}"
