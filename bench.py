@@ -375,6 +375,9 @@ def leg_formula_scaling(ctx, stream, flush, image, sizes=(10, 100, 500, 1000, 20
         ms = []
         with torch.cuda.stream(stream):
             b = ctx.batch([(F, [image])], stream) if mode == "batched" else None
+            if b is not None:  # (a per-operator batch captures its graph on run 2)
+                for _ in range(2):
+                    b.run(stream)
             for k in range(n + 1):
                 flush.zero_()
                 a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -469,8 +469,10 @@ typedef struct {
 } vl_tile_choice;
 
 /* Time `jobs` under every candidate tile shape and CTAs-per-SM count that
- * fits (reps timed launches each, after one untimed launch whose device
- * status must be VL_OK), keep the fastest in the context's table for the
+ * fits, and for a batch of one job its per-operator form (reps timed
+ * launches each, every one after a 192 MB write that clears the L2, after
+ * untimed launches whose device status must be VL_OK; the library holds
+ * that scratch while tuning), keep the fastest in the context's table for the
  * batch's signature and return it in *best.  trials (host, max_trials
  * entries, may be NULL) receives every candidate; *n_trials their count.
  * Runs on `stream` and synchronises it; the jobs' results are computed and
