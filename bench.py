@@ -731,7 +731,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain/ccl/e2e/cpu legs")
-    ap.add_argument("--leg", default="", choices=["", "ccl", "scaling", "volume", "serving"],
+    ap.add_argument("--leg", default="", choices=["", "ccl", "scaling", "volume", "serving", "kexec"],
                     help="run only this leg and print its figures (for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -761,6 +761,24 @@ def main():
         stream = torch.cuda.Stream()
         flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         print(json.dumps({"leg": "ccl", **leg_ccl(ctx, stream, flush, measured_peaks()[0])}), flush=True)
+        return
+    if args.leg == "kexec":
+        # the bench's step with the bench's tuned tile shape (16 x 32) and
+        # no autotuning: three launches, for an ncu capture that holds
+        # little device memory
+        kctx = vg.Context(device=local, tile_rows=16, tile_words=32)
+        fk = wl.random_dag(N_NODES, seed=DAG_SEED)
+        Fk = kctx.compile(wl.formula_to_records(fk), fk.roots, CONN)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            im = kctx.image(wl.uniform_image(H, W, seed=0), stream)
+            b = kctx.batch([(Fk, [im])], stream)
+            for _ in range(3):
+                b.run(stream)
+            stream.synchronize()
+            if b.result(0).sync() != 0:
+                raise SystemExit("kexec leg failed: " + kctx.last_error())
+        print(json.dumps({"leg": "kexec", "launches": 3, "tiles": [16, 32]}), flush=True)
         return
     if args.leg == "serving":
         stream = torch.cuda.Stream()
