@@ -152,6 +152,44 @@ VL_DEV int g_find(int32_t* G, int x, int npx, int32_t* status, bool compress = t
   return root;
 }
 
+// Roots of a and b in G, both chains walked side by side, with path halving:
+// each node passed is pointed at its grandparent.  Like the compression in
+// g_find this only ever moves a node to one of its ancestors, and it costs no
+// second walk.  On return a == b (same set; they need not be roots) or both
+// are roots.  Only while the union-find is being built: in the final pass a
+// node of a finished tile holds its final label, which a halving write would
+// replace by an inner node.
+VL_DEV void g_find2(int32_t* G, int& a, int& b, int npx, int32_t* status) {
+  const int cap = min(npx + 64, 1 << 22);
+  for (int it = 0; it < cap; ++it) {
+    if (a == b) return;
+    if ((unsigned)a >= (unsigned)npx || (unsigned)b >= (unsigned)npx) {
+      set_status(status, ST_INTERNAL | RS_GRANGE);
+      a = b = 0;
+      return;
+    }
+    const int pa = ldcg(&G[a]), pb = ldcg(&G[b]);
+    const bool ra = pa == a, rb = pb == b;
+    if (ra && rb) return;
+    if ((unsigned)pa >= (unsigned)npx || (unsigned)pb >= (unsigned)npx) {
+      set_status(status, ST_INTERNAL | RS_GRANGE);
+      a = b = 0;
+      return;
+    }
+    const int ga = ra ? pa : ldcg(&G[pa]), gb = rb ? pb : ldcg(&G[pb]);
+    if (!ra) {
+      if (ga != pa) G[a] = ga;
+      a = ga;
+    }
+    if (!rb) {
+      if (gb != pb) G[b] = gb;
+      b = gb;
+    }
+  }
+  set_status(status, ST_INTERNAL | RS_GFIND);
+  a = b = 0;
+}
+
 // Unite the sets of a and b: the larger root is linked under the smaller,
 // by compare-and-swap so that only a node that is still a root is ever
 // re-pointed.  (An atomicMin on a root that was linked meanwhile would move
@@ -162,8 +200,7 @@ VL_DEV int g_find(int32_t* G, int x, int npx, int32_t* status, bool compress = t
 VL_DEV void g_union(int32_t* G, int a, int b, int npx, int32_t* status) {
   const int cap = min(npx + 64, 1 << 22);
   for (int it = 0; it < cap; ++it) {
-    a = g_find(G, a, npx, status);
-    b = g_find(G, b, npx, status);
+    g_find2(G, a, b, npx, status);
     if (a == b) return;
     if (a < b) { int t = a; a = b; b = t; }
     if (atomicCAS(&G[a], a, b) == a) return;
@@ -610,8 +647,10 @@ constexpr int ENC_SELECT = 3;      // flag bit2 = component selected (rho)
 // flag travels with the union itself and no separate pass has to gather it.
 VL_DEV int rz_key(int v, bool seeded, int npx) { return seeded ? v : v + npx; }
 
-// Visit every local root once (at its start pixel) and replace parent[root]
-// by -(value + 2).  Block barrier at the end.
+// Give every local root its value.  The publishing modes visit each root
+// once, at its start pixel, and replace parent[root] by -(value + 2); the
+// resolving modes (ENC_LABEL, ENC_SELECT) start from the saved values and
+// walk G for the roots of border components only.  Block barrier at the end.
 //   ENC_PUBLISH     value = the component's minimum pixel (computed by the
 //                   labelling); border components publish G[value] = value
 //   ENC_PUBLISH_RZ  value = rz_key of the first pixel of the root strip run;
@@ -628,6 +667,25 @@ VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, int32_t* G,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int ns = (g.th + 1) >> 1;
+  if (mode == ENC_LABEL || mode == ENC_SELECT) {
+    // the saved roots already hold their value: only the components on the
+    // tile border have work, a walk in G.  The strip runs are dealt out over
+    // every thread of the block, so the walks of one tile run side by side
+    // (the border components' roots sit in the first and last strips).
+    for (int i = threadIdx.x; i < s.nruns; i += blockDim.x) {
+      const int p = s.parent[i];
+      if (p >= 0) continue;  // not a root
+      const uint8_t fl = s.flag[i];
+      if (mode == ENC_LABEL) {
+        if (fl & 2) s.parent[i] = -(g_find(G, -p - 2, glen, status) + 2);
+      } else {
+        const bool sel = (fl & 2) ? g_find(G, -p - 2, glen, status) < npx : (fl & 1) != 0;
+        if (sel) s.flag[i] = fl | 4;
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int k = warp; k < ns; k += nw) {
     if (lane >= g.tww) continue;
     uint32_t sc = s.st[k][lane];
@@ -645,15 +703,7 @@ VL_DEV void ccl_encode_roots(CclSmem& s, const CclGeom& g, int mode, int32_t* G,
       } else {
         v = -s.parent[S] - 2;
       }
-      if (mode == ENC_PUBLISH || mode == ENC_PUBLISH_RZ) {
-        if (fl & 2) G[v] = v;
-      } else if (mode == ENC_LABEL) {
-        if (fl & 2) v = g_find(G, v, glen, status);
-      } else {
-        bool sel = fl & 1;
-        if (fl & 2) sel = g_find(G, v, glen, status) < npx;
-        if (sel) s.flag[S] = fl | 4;
-      }
+      if (fl & 2) G[v] = v;
       s.parent[S] = -(v + 2);
     }
   }
@@ -735,16 +785,14 @@ VL_DEV void ccl_write_select(const CclSmem& s, const CclGeom& g, uint32_t* Z) {
 }
 
 // --------------------------------------------------------- border merge --
-// Merge units: one per word of each horizontal tile border (its 32 columns)
-// and one per 32 rows of each vertical tile border.  A warp takes a unit,
-// one lane per column (or row), so the unions of a unit run side by side
-// instead of one after another.
-// (Hs: slice rows of a volume, H for an image; horizontal borders are those
-// between the tile rows of one slice.)
-VL_DEV int merge_units(int H, int Wp, int tiles_x, int Hs, int cth = CCL_TH) {
-  const int tys = (Hs + cth - 1) / cth;
-  return (H / Hs) * (tys - 1) * Wp + (tiles_x - 1) * ((H + 31) >> 5);
-}
+// The borders between labelling tiles are merged by a pass of their own
+// after the labelling launch, in merge units: one per word of each
+// horizontal tile border (its 32 columns) and one per 32 rows of each
+// vertical tile border.  A warp takes a unit, one lane per column (or row),
+// so the unions of a unit run side by side.  (A merge inside the labelling
+// launch, by whichever tile beside a border finished last, measured slower:
+// its latency-bound walks then hold a labelling CTA instead of running at
+// full occupancy.)
 
 // Which of columns x-1, x, x+1 (8-adjacency) or x (4-adjacency) of a row is
 // set, leftmost first, as an offset -1/0/1 (2: none).  The row is given by
@@ -779,21 +827,36 @@ VL_DEV void warp_unite(int32_t* G, bool valid, int a, int b, int glen, int32_t* 
   if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) g_union(G, ka, kb, glen, status);
 }
 
-// Unite the components that touch across the tile border of merge unit
-// `unit`.  A horizontal border is covered by checking each row-run start of
-// both border rows against the 1- or 3-pixel window of the other row: two
-// runs that touch always have a start of one run inside the other's window.
-// A vertical border pairs each set pixel left of it with the pixel right of
-// it, or, for 8-adjacency when that one is clear, with its diagonal
-// neighbours (both border columns lie inside the image: a tile border is a
-// multiple of 1024 columns, below W).  Padding bits of the loaded words are
-// cleared.  Must be called by the whole warp.
+// Two pairs per lane, (a1, b1) and (a2, b2).  When the warp holds at most 32
+// valid pairs they are dealt out one per lane, so the unions run side by
+// side in one round instead of two.  Must be called by the whole warp.
+VL_DEV void warp_unite2(int32_t* G, bool v1, int a1, int b1, bool v2, int a2, int b2, int glen,
+                        int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m1 = __ballot_sync(FULL, v1), m2 = __ballot_sync(FULL, v2);
+  const int n1 = __popc(m1), n = n1 + __popc(m2);
+  if (n > 32) {
+    warp_unite(G, v1, a1, b1, glen, status);
+    warp_unite(G, v2, a2, b2, glen, status);
+    return;
+  }
+  // lane L takes the L-th valid pair: the first kind's in lane order, then
+  // the second's
+  int src = lane;
+  if (lane < n1) src = __fns(m1, 0, lane + 1);
+  else if (lane < n) src = __fns(m2, 0, lane - n1 + 1);
+  const int xa1 = __shfl_sync(FULL, a1, src), xb1 = __shfl_sync(FULL, b1, src);
+  const int xa2 = __shfl_sync(FULL, a2, src), xb2 = __shfl_sync(FULL, b2, src);
+  const bool first = lane < n1;
+  warp_unite(G, lane < n, first ? xa1 : xa2, first ? xb1 : xb2, glen, status);
+}
+
 // Unite the components of row yu and row yd (rows of the stored image) that
 // touch in word w: with conn 8 a pixel meets the three pixels at x - 1, x,
-// x + 1 of the other row, with conn 4 only the one at x.  Every row-run start
-// of either row is checked against that window of the other row: two runs
-// that touch always have a start of one run inside the other's window.  Must
-// be called by the whole warp.
+// x + 1 of the other row, with conn 4 only the one at x.  Every row-run
+// start of either row is checked against that window of the other row: two
+// runs that touch always have a start of one run inside the other's window.
+// Padding bits are cleared.  Must be called by the whole warp.
 VL_DEV void ccl_merge_rows(const uint32_t* m, int W, int Wp, int yu, int yd, int w, int conn,
                            int32_t* G, int glen, int32_t* status) {
   const int lane = threadIdx.x & 31;
@@ -808,12 +871,25 @@ VL_DEV void ccl_merge_rows(const uint32_t* m, int W, int Wp, int yu, int yd, int
   const uint32_t sd = md & ~((md << 1) | (mdl >> 31));
   const uint32_t su = mu & ~((mu << 1) | (mul >> 31));
   const int x = 32 * w + lane;
-  int dx = (sd >> lane) & 1u ? window_hit(mul, mu, mur, lane, conn) : 2;
-  warp_unite(G, dx != 2, yd * W + x, yu * W + x + dx, glen, status);
-  dx = (su >> lane) & 1u ? window_hit(mdl, md, mdr, lane, conn) : 2;
-  warp_unite(G, dx != 2, yu * W + x, yd * W + x + dx, glen, status);
+  const int dd = (sd >> lane) & 1u ? window_hit(mul, mu, mur, lane, conn) : 2;
+  const int du = (su >> lane) & 1u ? window_hit(mdl, md, mdr, lane, conn) : 2;
+  warp_unite2(G, dd != 2, yd * W + x, yu * W + x + dd, du != 2, yu * W + x, yd * W + x + du,
+              glen, status);
 }
 
+// (Hs: slice rows of a volume, H for an image; horizontal borders are those
+// between the tile rows of one slice.)
+VL_DEV int merge_units(int H, int Wp, int tiles_x, int Hs, int cth = CCL_TH) {
+  const int tys = (Hs + cth - 1) / cth;
+  return (H / Hs) * (tys - 1) * Wp + (tiles_x - 1) * ((H + 31) >> 5);
+}
+
+// Unite the components that touch across the tile border of merge unit
+// `unit`.  A horizontal border is ccl_merge_rows over the whole row.  A
+// vertical border pairs each set pixel left of it with the pixel right of it,
+// or, for 8-adjacency when that one is clear, with its diagonal neighbours
+// (both border columns lie inside the image: a tile border is a multiple of
+// 1024 columns, below W).  Must be called by the whole warp.
 VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int unit, int conn,
                            int32_t* G, int glen, int32_t* status, int Hs, int cth = CCL_TH) {
   const int lane = threadIdx.x & 31;
@@ -848,8 +924,8 @@ VL_DEV void ccl_merge_unit(const uint32_t* m, int H, int W, int Wp, int unit, in
     // (lane-dependent choices go into the arguments: every lane calls)
     const int a = y * W + x0 - 1;
     const bool straight = R || conn == 4;
-    warp_unite(G, L && (straight ? R : Ru), a, (straight ? y : y - 1) * W + x0, glen, status);
-    warp_unite(G, L && !straight && Rd, a, (y + 1) * W + x0, glen, status);
+    warp_unite2(G, L && (straight ? R : Ru), a, (straight ? y : y - 1) * W + x0,
+                L && !straight && Rd, a, (y + 1) * W + x0, glen, status);
   }
 }
 
