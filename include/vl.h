@@ -299,6 +299,7 @@ typedef struct {
   int32_t kind, insn_off, insn_cnt, halo, sel_off, sel_cnt, pct_off, pct_cnt;
   int32_t rank_mask;  /* groups: rank tables their opcode-10 instructions read */
   int32_t rank_halo;  /* groups: largest halo of those instructions */
+  int32_t n_bufs;     /* groups: tile buffers the instructions use (0 .. n_bufs-1) */
 } vl_plan_step;
 typedef struct {
   uint8_t op, dst, a, b;   /* b: direction (1 = less-than) for thresholds, value for constants */

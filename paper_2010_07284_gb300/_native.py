@@ -66,7 +66,7 @@ class VlPlanStep(C.Structure):
     _fields_ = [("kind", C.c_int32), ("insn_off", C.c_int32), ("insn_cnt", C.c_int32),
                 ("halo", C.c_int32), ("sel_off", C.c_int32), ("sel_cnt", C.c_int32),
                 ("pct_off", C.c_int32), ("pct_cnt", C.c_int32),
-                ("rank_mask", C.c_int32), ("rank_halo", C.c_int32)]
+                ("rank_mask", C.c_int32), ("rank_halo", C.c_int32), ("n_bufs", C.c_int32)]
 
 
 class VlPlanInsn(C.Structure):

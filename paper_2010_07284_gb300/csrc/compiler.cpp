@@ -823,6 +823,22 @@ int compile_formula(const vl_node* in, int n_nodes, const int32_t* roots, int n_
       P.steps.insert(P.steps.begin(), r);
     }
   }
+  // tile buffers each group uses (buffers are taken lowest first): the
+  // executor places the stage of rank planes right after them
+  for (StepDesc& s : P.steps) {
+    if (s.kind != SK_GROUP) continue;
+    int hi = 0;
+    for (int k = s.insn_off; k < s.insn_off + s.insn_cnt; ++k) {
+      const Insn& in = P.insns[k];
+      const int op = insn_op(in);
+      if (op != I_STORE) hi = std::max(hi, in.dst + 1);
+      if (op == I_NOT || op == I_NEAR || op == I_AND || op == I_OR || op == I_ANDNOT ||
+          op == I_STORE)
+        hi = std::max(hi, in.a + 1);
+      if (op == I_AND || op == I_OR || op == I_ANDNOT) hi = std::max(hi, in.b + 1);
+    }
+    s.n_bufs = hi;
+  }
   // ---- 5b. block barriers inside groups.  Every instruction but the float
   // threshold writes (and a store reads) each buffer word from the thread
   // that owns it -- one fixed owner per buffer word -- so a value read at

@@ -80,6 +80,20 @@ VL_DEV bool rank_stage_begin(const GroupCtx& c) {
 // Most code bits of a rank table (values <= 8191: codes < 2^14).
 constexpr int kRankMaxBits = 14;
 
+// The instruction stream and the slot table are read-only for the whole
+// launch: both go through the read-only data cache, so that every tile of a
+// step after the first on an SM finds them in L1 instead of L2.
+VL_DEV Insn ld_insn(const Insn* p) {
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+  Insn I;
+  memcpy(&I, &v, sizeof(Insn));
+  return I;
+}
+VL_DEV uint32_t* ld_slot(uint32_t* const* slots, int k) {
+  return reinterpret_cast<uint32_t*>(
+      __ldg(reinterpret_cast<const unsigned long long*>(slots + k)));
+}
+
 
 // Word ownership: buffer word idx (row-major, idx = row * bw + word) is
 // always read and written by thread idx mod EXEC_THREADS, by every
@@ -103,7 +117,7 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
   // 0: planes read from global memory; 1: being staged; 2: staged
   int stage = rank_stage_begin(c) ? 1 : 0;
   for (int k = 0; k < n_insn; ++k) {
-    const Insn I = insns[k];
+    const Insn I = ld_insn(insns + k);
     if (I.op & I_SYNC) __syncthreads();  // uniform: one instruction stream per CTA
     const int op = I.op & ~I_SYNC;
     const int h = I.h;
@@ -128,39 +142,34 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
         const int y = c.r0 - c.halo + i, wg = c.w0 - 1 + j;
         uint32_t word = 0;
         if (y >= 0 && y < c.H && wg >= 0 && wg < c.Wp) {
-          const uint32_t* s0 = sp + (size_t)(i - s_row0) * bw + j;
-          const uint32_t* g0 = c.planes + (size_t)I.slot * c.pstride + (size_t)y * c.Wp + wg;
-          // bit-sliced c >= K over the code planes, most significant first
-          // (K's bits are the same for every thread: the branch is uniform)
+          // bit-sliced code >= K: the subtraction code - K must not borrow.
+          // Bit b passes the borrow on as ~x_b | borrow where K_b = 1 and
+          // as ~x_b & borrow where K_b = 0, i.e. the majority of (~x_b,
+          // borrow, K_b) -- one logic op per plane.  Below K's lowest set
+          // bit no borrow starts, so the chain begins there (K = 0: code
+          // >= K everywhere).  K's bits are the same for every thread.
           // (two separate loops: a select between a shared and a global load
           // inside one loop made every word wait for global memory)
-          uint32_t gt = 0, eq = 0xFFFFFFFFu, nan = 0;
+          uint32_t borrow = 0, nan = 0;
+          const int b0 = K ? __ffs(K) - 1 : nb;
           if (stage) {
+            const uint32_t* s0 = sp + (size_t)(i - s_row0) * bw + j;
 #pragma unroll 4
-            for (int b = kRankMaxBits - 1; b >= 0; --b) {
-              if (b >= nb) continue;
-              const uint32_t pw = s0[b * per_plane];
-              if ((K >> b) & 1u) {
-                eq &= pw;
-              } else {
-                gt |= eq & pw;
-                eq &= ~pw;
-              }
+            for (int b = 0; b < kRankMaxBits; ++b) {
+              if (b < b0 || b >= nb) continue;
+              const uint32_t x = s0[b * per_plane], km = 0u - ((K >> b) & 1u);
+              borrow = (~x & borrow) | (~x & km) | (borrow & km);
             }
             if (lt) nan = s0[nb * per_plane];
           } else {
-            for (int b = nb - 1; b >= 0; --b) {
-              const uint32_t pw = ldcg(g0 + (size_t)b * c.pstride);
-              if ((K >> b) & 1u) {
-                eq &= pw;
-              } else {
-                gt |= eq & pw;
-                eq &= ~pw;
-              }
+            const uint32_t* g0 = c.planes + (size_t)I.slot * c.pstride + (size_t)y * c.Wp + wg;
+            for (int b = b0; b < nb; ++b) {
+              const uint32_t x = ldcg(g0 + (size_t)b * c.pstride), km = 0u - ((K >> b) & 1u);
+              borrow = (~x & borrow) | (~x & km) | (borrow & km);
             }
             if (lt) nan = ldcg(g0 + (size_t)nb * c.pstride);
           }
-          const uint32_t ge = gt | eq;
+          const uint32_t ge = ~borrow;
           word = lt ? (~ge & ~nan) : ge;
           word &= vmask(wg, c.W);
         }
@@ -246,17 +255,31 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
     } else if (op == I_STORE) {
       // the core words, each from the thread that owns it in the buffer
       const uint32_t* a = gbuf(I.a);
-      uint32_t* g = c.slots[I.slot];
+      uint32_t* g = ld_slot(c.slots, I.slot);
       const int s_hi = (c.halo + c.th) * bw;
       for (int idx = own_first(c.halo * bw, tid); idx < s_hi; idx += nthr) {
         const int i = idx / bw, j = idx - (idx / bw) * bw;
         if (j >= 1 && j <= c.tww) g[(size_t)(c.r0 + i - c.halo) * c.Wp + c.w0 + j - 1] = a[idx];
       }
+    } else if (op == I_AND || op == I_OR || op == I_ANDNOT) {
+      // every buffer holds 0 outside the image, and so does the result of
+      // these three: no bounds to check
+      uint32_t* d = gbuf(I.dst);
+      const uint32_t* a = gbuf(I.a);
+      const uint32_t* b = gbuf(I.b);
+      const int first = own_first(w_lo, tid);
+      if (op == I_AND) {
+        for (int idx = first; idx < w_hi; idx += nthr) d[idx] = a[idx] & b[idx];
+      } else if (op == I_OR) {
+        for (int idx = first; idx < w_hi; idx += nthr) d[idx] = a[idx] | b[idx];
+      } else {
+        for (int idx = first; idx < w_hi; idx += nthr) d[idx] = a[idx] & ~b[idx];
+      }
     } else {
       uint32_t* d = gbuf(I.dst);
       const uint32_t* a = gbuf(I.a);
       const uint32_t* b = gbuf(I.b);
-      const uint32_t* g = (op == I_LOAD) ? c.slots[I.slot] : nullptr;
+      const uint32_t* g = (op == I_LOAD) ? ld_slot(c.slots, I.slot) : nullptr;
       for (int idx = own_first(w_lo, tid); idx < w_hi; idx += nthr) {
         const int i = idx / bw, j = idx - (idx / bw) * bw;
         const int y = c.r0 - c.halo + i, wg = c.w0 - 1 + j;
@@ -266,9 +289,6 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
           switch (op) {
             case I_LOAD: word = ldcg(&g[(size_t)y * c.Wp + wg]); break;
             case I_NOT: word = ~a[o] & vmask(wg, c.W); break;
-            case I_AND: word = a[o] & b[o]; break;
-            case I_OR: word = a[o] | b[o]; break;
-            case I_ANDNOT: word = a[o] & ~b[o]; break;
             case I_CONST: word = I.b ? vmask(wg, c.W) : 0u; break;
             case I_NEAR: {
               uint32_t ul = 0, uc = a[o - bw], ur = 0, ml = 0, mc = a[o], mr = 0,

@@ -137,8 +137,10 @@ VL_DEV void run_subitem(const DevJob& J, const StepDesc& S, int sub, int per_rz,
       c.buf = reinterpret_cast<uint32_t*>(smem);
       c.images = J.images; c.slots = J.slots; c.pct_val = J.pct_val;
       c.rtab = J.rtab; c.planes = J.planes; c.pstride = (size_t)J.H * J.Wp;
-      c.stage = c.buf + (size_t)L.group_buffers * c.bh * c.bw;
-      c.stage_cap = L.smem_bytes / 4 - L.group_buffers * c.bh * c.bw;
+      // the stage of rank planes follows the buffers this group uses
+      const int nbuf = min(max(S.n_bufs, 1), L.group_buffers);
+      c.stage = c.buf + (size_t)nbuf * c.bh * c.bw;
+      c.stage_cap = L.smem_bytes / 4 - nbuf * c.bh * c.bw;
       c.rank_mask = S.rank_mask; c.rank_halo = S.rank_halo;
       group_tile(c, J.insns + S.insn_off, S.insn_cnt);
       break;

@@ -125,6 +125,8 @@ struct StepDesc {
   int32_t pct_cnt;
   int32_t rank_mask; // groups: rank tables (< 32) its I_RTHR read, one bit each
   int32_t rank_halo; // groups: largest halo of those I_RTHR
+  int32_t n_bufs;    // groups: tile buffers its instructions use (0 .. n_bufs-1);
+                     //   the shared-memory stage of rank planes follows them
 };
 
 // Rank codes of one image channel against the sorted distinct constant
