@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <queue>
 
 #include "runtime.h"
 
@@ -303,63 +304,122 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.off_images = take(sizeof(DevImage) * std::max(1, I.n_table));
     I.off_slotptrs = take(sizeof(uint32_t*) * std::max(1, P.n_inter_slots + P.n_root_slots + P.n_mask_slots));
   }
-  // work items, in list-scheduling order: every (job, step) gets the time
-  // its step could start if the job ran alone on the whole GPU (the latest
-  // estimated finish of its dependencies), and pairs are emitted in the
-  // order of those times.  A step starts after its dependencies finish
-  // (latencies are positive), so everything an item waits for comes earlier
-  // in the list;
-  // jobs of very different sizes interleave by their progress instead of
-  // step index.  Steps split into items of about a tile each, at most
-  // 4 x grid items per step.
+  // work items, in the order of a list-scheduling simulation on `grid` CTAs:
+  // a CTA that frees up takes the ready item whose step has the longest
+  // estimated path to the end of its job (its bottom level), and items are
+  // emitted in the order the simulation starts them.  An item starts only
+  // after every step it depends on has finished, so everything an item waits
+  // for comes earlier in the list.  Ordering by start times estimated as if
+  // the GPU had unlimited CTAs instead let wide steps off the critical path
+  // take every CTA just before a critical step became ready.
+  // Steps split into items of about a tile each, at most 4 x grid items per
+  // step.
   {
-    struct Pair { double t; int j, s; };
-    std::vector<Pair> pairs;
-    for (int j = 0; j < n_jobs; ++j) {
-      const Plan& P = *J[j].P;
-      std::vector<double> fin(J[j].need.size(), 0.0);
-      for (size_t s = 0; s < J[j].need.size(); ++s) {
-        double t = 0;  // earliest start: after every dependency finished
-        for (int q = P.dep_off[s]; q < P.dep_off[s + 1]; ++q) t = std::max(t, fin[P.deps[q]]);
-        pairs.push_back(Pair{t, j, (int)s});
-        const int n = J[j].need[s];
-        const double waves = std::ceil((double)n / grid);
-        double len;
-        switch (P.steps[s].kind) {
-          case SK_GROUP: len = waves * (5.0 + 1.0 * P.steps[s].insn_cnt); break;
-          case SK_RZ_LOCAL: len = waves * 50.0; break;
-          case SK_RZ_MERGE: len = 30.0; break;
-          case SK_RZ_FINAL: len = waves * 25.0; break;
-          case SK_RANK: len = 20.0 + waves * 5.0; break;
-          case SK_ARITH: len = 10.0 + waves * 2.0 * P.steps[s].insn_cnt; break;
-          default: len = 100.0; break;
-        }
-        fin[s] = t + len;
-      }
-    }
-    std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& a, const Pair& b) { return a.t < b.t; });
+    struct StepRec { int j, s, first, n; double item_us, bl; int deps_left; };
+    std::vector<StepRec> recs;
+    std::vector<int> rec_of_job(n_jobs + 1, 0);
+    long long subitems = 0;
+    for (int j = 0; j < n_jobs; ++j)
+      for (size_t s = 0; s < J[j].need.size(); ++s) subitems += J[j].need[s];
     // with work for many waves (thousands of small images), items of short
     // tiles are merged up to ~40 us so that popping stays cheap beside work
     // -- but only as far as the jobs running side by side still offer four
     // items per CTA: the steps of one job mostly wait on each other, and
     // merging the tiles of a step there only serialises them on fewer CTAs
-    long long subitems = 0;
-    for (const Pair& p : pairs) subitems += J[p.j].need[p.s];
     const bool plenty = subitems > 32LL * grid;
-    for (const Pair& p : pairs) {
-      const int n = J[p.j].need[p.s];
-      int chunk = std::max(1, (n + 4 * grid - 1) / (4 * grid));
-      if (plenty) {
-        const StepDesc& sd = J[p.j].P->steps[p.s];
-        const double tile_us = sd.kind == SK_GROUP ? 5.0 + 1.0 * sd.insn_cnt
-                               : sd.kind == SK_RZ_FINAL ? 20.0 : 40.0;
-        const long long side_by_side = std::max<long long>(1, (long long)n * n_jobs / (4LL * grid));
-        chunk = std::max<long long>(chunk, std::min<long long>(
-            {(long long)n, (long long)std::ceil(40.0 / tile_us), side_by_side}));
+    std::vector<WorkItem> pending;  // every item, step by step
+    for (int j = 0; j < n_jobs; ++j) {
+      rec_of_job[j] = (int)recs.size();
+      const Plan& P = *J[j].P;
+      const double tile_scale = (double)ts.rows * ts.words / (16.0 * 32.0);
+      for (size_t si = 0; si < J[j].need.size(); ++si) {
+        const StepDesc& sd = P.steps[si];
+        const int n = J[j].need[si];
+        // estimated microseconds per sub-item (one GB300, two CTAs per SM)
+        double sub_us;
+        switch (sd.kind) {
+          case SK_GROUP: sub_us = (5.0 + 1.3 * sd.insn_cnt) * tile_scale; break;
+          case SK_RZ_LOCAL: sub_us = 35.0 * J[j].cth / CCL_TH; break;
+          case SK_RZ_MERGE: sub_us = 15.0; break;
+          case SK_RZ_FINAL: sub_us = 10.0 * J[j].cth / CCL_TH; break;
+          case SK_RANK: sub_us = 50.0; break;
+          case SK_ARITH: sub_us = 10.0 + 2.0 * sd.insn_cnt; break;
+          default: sub_us = 100.0; break;
+        }
+        int chunk = std::max(1, (n + 4 * grid - 1) / (4 * grid));
+        if (plenty) {
+          const double tile_us = sd.kind == SK_GROUP ? 5.0 + 1.0 * sd.insn_cnt
+                                 : sd.kind == SK_RZ_FINAL ? 20.0 : 40.0;
+          const long long side_by_side = std::max<long long>(1, (long long)n * n_jobs / (4LL * grid));
+          chunk = std::max<long long>(chunk, std::min<long long>(
+              {(long long)n, (long long)std::ceil(40.0 / tile_us), side_by_side}));
+        }
+        StepRec r{j, (int)si, (int)pending.size(), 0, sub_us * chunk, 0.0, 0};
+        for (int first = 0; first < n; first += chunk, ++r.n)
+          pending.push_back(WorkItem{j, (int)si, first, std::min(chunk, n - first)});
+        r.deps_left = P.dep_off[si + 1] - P.dep_off[si];
+        recs.push_back(r);
       }
-      for (int first = 0; first < n; first += chunk)
-        items.push_back(WorkItem{p.j, p.s, first, std::min(chunk, n - first)});
     }
+    rec_of_job[n_jobs] = (int)recs.size();
+    // bottom levels: a step's estimated length plus the longest of its
+    // successors' (deps point at earlier steps, so one backward sweep)
+    std::vector<std::vector<int>> succ(recs.size());
+    for (int j = 0; j < n_jobs; ++j) {
+      const Plan& P = *J[j].P;
+      const int base = rec_of_job[j];
+      for (size_t si = 0; si < J[j].need.size(); ++si)
+        for (int q = P.dep_off[si]; q < P.dep_off[si + 1]; ++q)
+          succ[base + P.deps[q]].push_back(base + (int)si);
+    }
+    for (int r = (int)recs.size() - 1; r >= 0; --r) {
+      double tail = 0;
+      for (int x : succ[r]) tail = std::max(tail, recs[x].bl);
+      recs[r].bl = std::ceil((double)recs[r].n / grid) * recs[r].item_us + tail;
+    }
+    // the simulation: ready items by (bottom level, then list position)
+    struct Ready {
+      double bl; int idx;
+      bool operator<(const Ready& o) const { return bl != o.bl ? bl < o.bl : idx > o.idx; }
+    };
+    struct Busy {
+      double t; int rec;
+      bool operator<(const Busy& o) const { return t > o.t; }
+    };
+    std::priority_queue<Ready> ready;
+    std::priority_queue<Busy> busy;
+    std::vector<int> left(recs.size());
+    auto release = [&](int r) {
+      for (int k = 0; k < recs[r].n; ++k) ready.push(Ready{recs[r].bl, recs[r].first + k});
+    };
+    for (size_t r = 0; r < recs.size(); ++r) {
+      left[r] = recs[r].n;
+      if (recs[r].deps_left == 0) release((int)r);
+    }
+    std::vector<int> rec_index(pending.size());
+    for (size_t r = 0; r < recs.size(); ++r)
+      for (int k = 0; k < recs[r].n; ++k) rec_index[recs[r].first + k] = (int)r;
+    items.reserve(pending.size());
+    double now = 0;
+    int free_ctas = grid;
+    while (items.size() < pending.size()) {
+      while (free_ctas > 0 && !ready.empty()) {
+        const int idx = ready.top().idx;
+        ready.pop();
+        items.push_back(pending[idx]);
+        busy.push(Busy{now + recs[rec_index[idx]].item_us, rec_index[idx]});
+        --free_ctas;
+      }
+      if (busy.empty()) break;  // (cannot happen: some step is always ready)
+      const Busy b = busy.top();
+      busy.pop();
+      now = b.t;
+      ++free_ctas;
+      if (--left[b.rec] == 0)
+        for (int x : succ[b.rec])
+          if (--recs[x].deps_left == 0) release(x);
+    }
+    if (items.size() != pending.size()) return set_err(ctx, VL_ERR_INTERNAL, "internal: step order");
   }
   const size_t off_items = take(sizeof(WorkItem) * std::max<size_t>(1, items.size()));
   const size_t off_need = take(sizeof(int32_t) * std::max(1, total_steps));
