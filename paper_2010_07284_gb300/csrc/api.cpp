@@ -340,7 +340,14 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
         switch (sd.kind) {
           case SK_GROUP: sub_us = (5.0 + 1.3 * sd.insn_cnt) * tile_scale; break;
           case SK_RZ_LOCAL: sub_us = 35.0 * J[j].cth / CCL_TH; break;
-          case SK_RZ_MERGE: sub_us = 15.0; break;
+          case SK_RZ_MERGE: {
+            // a sub-item of a select's merge: its share of the merge units
+            // over the 16 warps of a CTA, ~5 us per latency-bound unit
+            const long long units = ccl_merge_units(J[j].H, J[j].Wp, 0, J[j].cth);
+            const long long per_rz = std::max(1, n / std::max(1, sd.rz_cnt));
+            sub_us = 5.0 * std::ceil((double)units / (per_rz * (EXEC_THREADS / 32)));
+            break;
+          }
           case SK_RZ_FINAL: sub_us = 10.0 * J[j].cth / CCL_TH; break;
           case SK_RANK: sub_us = 50.0; break;
           case SK_ARITH: sub_us = 10.0 + 2.0 * sd.insn_cnt; break;
