@@ -289,10 +289,11 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
         case SK_GROUP: n = I.gty * I.gtx; break;
         case SK_RZ_LOCAL: case SK_RZ_FINAL: n = s.rz_cnt * I.ctiles; break;
         case SK_RZ_MERGE:
-          // at most one wave of items per step: the merge is latency-bound,
-          // and a second wave would wait for the first
+          // at most two waves of items per step: the merge is latency-bound,
+          // and fewer, longer items tie up fewer CTAs that a critical step
+          // could use (one wave, or no cap, measured slower)
           n = s.rz_cnt * std::min(ccl_merge_chunks(I.H, I.Wp, I.cth),
-                                  std::max(1, (grid + s.rz_cnt - 1) / s.rz_cnt));
+                                  std::max(1, 2 * (grid + s.rz_cnt - 1) / s.rz_cnt));
           break;
         case SK_RANK: n = (int)P.rtab.size() * ((I.H + RANK_ROWS - 1) / RANK_ROWS); break;
         case SK_ARITH: n = (I.H + ARITH_ROWS - 1) / ARITH_ROWS; break;

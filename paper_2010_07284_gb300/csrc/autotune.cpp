@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <iterator>
 #include <set>
 
 #include "runtime.h"
@@ -175,8 +176,26 @@ extern "C" VL_API vl_status vl_autotune(vl_context* ctx, const vl_job* jobs, int
   if (ctx->ctas_per_sm > 1) cps_list.push_back(1);
   // candidates: every tile shape and CTA count of the persistent executor,
   // and for a batch of one job its per-operator kernels in a graph
+  // Besides the fixed shapes, for one job: per tile width, the lowest tile
+  // height whose tiles still fit in one wave of the grid (a 2048 x 2048
+  // image: 14 x 32 gives 294 tiles, 27 x 16 gives 304, where 16 x 32 gives
+  // 256 and leaves 48 CTAs without a tile of each group step).
+  std::vector<TileShape> bases(std::begin(kShapes), std::end(kShapes));
+  if (n_jobs == 1) {
+    const int64_t grid = (int64_t)ctx->sm_count * ctx->ctas_per_sm;
+    const vl_image* im = jobs[0].images[0];
+    for (int words : {32, 16}) {
+      const int64_t tx = (im->Wp + words - 1) / words, per_col = grid / tx;
+      if (per_col < 1) continue;
+      const int rows = (int)((im->H + per_col - 1) / per_col);
+      if (rows < 8 || rows > 64) continue;
+      bool dup = false;
+      for (const TileShape& b : bases) dup |= b.rows == rows && b.words == words;
+      if (!dup) bases.push_back(TileShape{rows, words, 0});
+    }
+  }
   std::vector<TileShape> cands;
-  for (const TileShape& base : kShapes) {
+  for (const TileShape& base : bases) {
     if (!tile_shape_fits(ctx, base)) continue;
     for (int cps : cps_list) {
       TileShape t = base;

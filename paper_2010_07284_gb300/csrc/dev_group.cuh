@@ -104,15 +104,17 @@ VL_DEV int own_first(int lo, int tid) {
   return lo <= tid ? tid : tid + ((lo - tid + EXEC_THREADS - 1) / EXEC_THREADS) * EXEC_THREADS;
 }
 
-// BH, BW > 0: the buffer shape as compile-time constants (index arithmetic
-// and divisions by the row length fold into multiplies); 0: read from c.
+// BW > 0: the buffer row length as a compile-time constant (index
+// arithmetic and divisions by the row length fold into multiplies); 0: read
+// from c.  The number of buffer rows is only a stride between buffers and
+// stays a run-time value, so that any tile height runs the fast path.
 // Launched with EXEC_THREADS threads.
-template <int BH, int BW>
+template <int BW>
 VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
   const int tid = threadIdx.x, nthr = EXEC_THREADS;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   const int bw = BW > 0 ? BW : c.bw;
-  const int bhbw = (BH > 0 ? BH : c.bh) * bw;
+  const int bhbw = c.bh * bw;
   auto gbuf = [&](int b) { return c.buf + (size_t)b * bhbw; };
   // 0: planes read from global memory; 1: being staged; 2: staged
   int stage = rank_stage_begin(c) ? 1 : 0;
@@ -308,17 +310,14 @@ VL_DEV void group_tile_t(const GroupCtx& c, const Insn* insns, int n_insn) {
   if (stage == 1) cp_async_wait_all();  // no copy may outlive the tile
 }
 
-// The group interpreter for the tile shapes the autotuner tries (buffer
-// rows = tile rows + 16, words = tile words + 2), generic otherwise.
+// The group interpreter for the tile widths the autotuner tries (buffer
+// words = tile words + 2: 32, 16 and 8-word tiles), generic otherwise.
 VL_DEV void group_tile(const GroupCtx& c, const Insn* insns, int n_insn) {
-  const int key = c.bh * 1000 + c.bw;
-  switch (key) {
-    case 32 * 1000 + 34: group_tile_t<32, 34>(c, insns, n_insn); break;  // 16 x 32
-    case 48 * 1000 + 18: group_tile_t<48, 18>(c, insns, n_insn); break;  // 32 x 16
-    case 48 * 1000 + 34: group_tile_t<48, 34>(c, insns, n_insn); break;  // 32 x 32
-    case 80 * 1000 + 18: group_tile_t<80, 18>(c, insns, n_insn); break;  // 64 x 16
-    case 80 * 1000 + 10: group_tile_t<80, 10>(c, insns, n_insn); break;  // 64 x 8
-    default: group_tile_t<0, 0>(c, insns, n_insn); break;
+  switch (c.bw) {
+    case 34: group_tile_t<34>(c, insns, n_insn); break;
+    case 18: group_tile_t<18>(c, insns, n_insn); break;
+    case 10: group_tile_t<10>(c, insns, n_insn); break;
+    default: group_tile_t<0>(c, insns, n_insn); break;
   }
 }
 
