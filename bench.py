@@ -64,13 +64,14 @@ def aggregate_throughput(total_ms: float, units_per_rank: float, world: int, dev
 
 def profiled_traffic(kernel: str, key: str):
     """DRAM bytes that an ncu capture of the current kernel sources measured
-    (profiles/traffic.json: each entry names the sources it was taken at),
-    or None when the sources changed since."""
+    (profiles/traffic.json: each entry lists the source files its kernels are
+    built from and their hash when it was taken), or None when one of those
+    files changed since."""
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         entry = json.load(open(tfile)).get(kernel, {})
         from paper_2010_07284_gb300 import buildlib
-        if entry.get("source_hash") == buildlib.source_hash():
+        if entry.get("source_hash") == buildlib.source_hash(entry.get("sources")):
             return entry.get(key)
     except Exception:
         pass

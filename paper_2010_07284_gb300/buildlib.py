@@ -40,12 +40,16 @@ def _deps():
     return files
 
 
-def source_hash() -> str:
-    """Hash of the library sources (identifies which kernels a profile saw)."""
+def source_hash(names=None) -> str:
+    """Hash of the library sources, or of the named ones (file names, e.g.
+    the files a kernel is built from): identifies which kernels a profile
+    saw."""
     import hashlib
     h = hashlib.sha256()
     for f in sorted(_deps()):
         if f.endswith("buildlib.py"):
+            continue
+        if names is not None and os.path.basename(f) not in names:
             continue
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
