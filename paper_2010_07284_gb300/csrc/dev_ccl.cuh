@@ -90,6 +90,34 @@ VL_DEV int s_find(int32_t* par, int x, int cap) {
   return -1;
 }
 
+// Roots of a and b, both chains walked side by side with path halving (each
+// node passed is pointed at its grandparent, and the walk jumps there): on
+// return a == b when the walks met (the same set; not necessarily a root),
+// else both are roots.  False if an index is out of range or a bounded loop
+// ran out (impossible unless memory is corrupted).
+VL_DEV bool s_find2(int32_t* par, int& a, int& b, int cap) {
+  volatile int32_t* p = par;
+  const unsigned lim = (unsigned)(cap - 64);
+  for (int it = 0; it < cap; ++it) {
+    if (a == b) return true;
+    if ((unsigned)a >= lim || (unsigned)b >= lim) return false;
+    const int qa = p[a], qb = p[b];
+    const bool ra = qa == a, rb = qb == b;
+    if (ra && rb) return true;
+    if ((unsigned)qa >= lim || (unsigned)qb >= lim) return false;
+    const int ga = ra ? qa : p[qa], gb = rb ? qb : p[qb];
+    if (!ra) {
+      if (ga != qa) p[a] = ga;
+      a = ga;
+    }
+    if (!rb) {
+      if (gb != qb) p[b] = gb;
+      b = gb;
+    }
+  }
+  return false;
+}
+
 // Unite the sets of a and b; the smaller root wins.  Returns false if a
 // bounded loop ran out (impossible unless memory is corrupted).
 VL_DEV bool s_union(int32_t* par, int a, int b, int cap) {
@@ -473,9 +501,9 @@ VL_DEV bool ccl_tile_label(CclSmem& s, const uint32_t* mask, const uint32_t* phi
             v = carry >= 0 ? carry : u;
           }
         }
-        ra = s_find(s.parent, u, cap);
-        rb = s_find(s.parent, v, cap);
-        if (ra < 0 || rb < 0) { ok = false; ra = rb = 0; }
+        // both roots at once; walks that meet need no link
+        ra = u; rb = v;
+        if (!s_find2(s.parent, ra, rb, cap)) { ok = false; ra = rb = 0; }
       }
       // link the larger root under the smaller; when hi was no longer a
       // root its old parent (unless already lo) still has to meet lo

@@ -36,36 +36,57 @@ VL_DEV int ld_acquire(const int32_t* p) {
 // Rank codes of rows [y0, y1) of one channel against the sorted table tv
 // (see RankTab): one warp per 32-pixel word, one lane per pixel; code bit b
 // of the word's pixels is a ballot, written to plane b (lane b writes it).
+// A warp takes RANK_UNR words at a time: their loads are in flight
+// together, and their searches (branch-free, the same number of steps for
+// every lane) interleave.
+constexpr int RANK_UNR = 4;
 VL_DEV void rank_rows(const float* tv, const RankTab& T, const void* plane, int format, bool nc,
                       int H, int W, int Wp, int pitch, int y0, int y1, uint32_t* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const size_t pstride = (size_t)H * Wp;
   const int nwords = (y1 - y0) * Wp;
-  for (int idx = warp; idx < nwords; idx += nw) {
-    const int y = y0 + idx / Wp, w = idx - (idx / Wp) * Wp;
-    const int x = 32 * w + lane;
-    const bool in = x < W;
-    float v = 0.f;
-    if (in) {
-      const size_t i = (size_t)y * pitch + x;
-      if (format == PX_U16) v = (float)static_cast<const unsigned short*>(plane)[i];
-      else v = nc ? __ldg(static_cast<const float*>(plane) + i) : __ldcg(static_cast<const float*>(plane) + i);
+  for (int base = warp * RANK_UNR; base < nwords; base += nw * RANK_UNR) {
+    float v[RANK_UNR];
+    bool in[RANK_UNR];
+#pragma unroll
+    for (int u = 0; u < RANK_UNR; ++u) {
+      const int idx = base + u;
+      const int y = y0 + idx / Wp, w = idx - (idx / Wp) * Wp;
+      const int x = 32 * w + lane;
+      in[u] = idx < nwords && x < W;
+      v[u] = 0.f;
+      if (in[u]) {
+        const size_t i = (size_t)y * pitch + x;
+        if (format == PX_U16) v[u] = (float)static_cast<const unsigned short*>(plane)[i];
+        else v[u] = nc ? __ldg(static_cast<const float*>(plane) + i) : __ldcg(static_cast<const float*>(plane) + i);
+      }
     }
-    int lo = 0, hi = T.m;  // thresholds below v (none for NaN)
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (tv[mid] < v) lo = mid + 1;
-      else hi = mid;
+    // lower bound: the number of table values below v (none for NaN)
+    int lo[RANK_UNR];
+#pragma unroll
+    for (int u = 0; u < RANK_UNR; ++u) lo[u] = 0;
+    for (int n = T.m; n > 1;) {
+      const int half = n >> 1;
+#pragma unroll
+      for (int u = 0; u < RANK_UNR; ++u) lo[u] = tv[lo[u] + half - 1] < v[u] ? lo[u] + half : lo[u];
+      n -= half;
     }
-    const unsigned code = 2u * (unsigned)lo + ((lo < T.m && tv[lo] == v) ? 1u : 0u);
-    uint32_t mine = 0;
-    for (int b = 0; b < T.nbits; ++b) {
-      const uint32_t word = __ballot_sync(FULL, in && ((code >> b) & 1u));
-      if (lane == b) mine = word;
+#pragma unroll
+    for (int u = 0; u < RANK_UNR; ++u) {
+      const int idx = base + u;
+      if (idx >= nwords) break;  // uniform: idx is the same for the warp
+      if (T.m > 0 && tv[lo[u]] < v[u]) ++lo[u];
+      const unsigned code = 2u * (unsigned)lo[u] + ((lo[u] < T.m && tv[lo[u]] == v[u]) ? 1u : 0u);
+      uint32_t mine = 0;
+      for (int b = 0; b < T.nbits; ++b) {
+        const uint32_t word = __ballot_sync(FULL, in[u] && ((code >> b) & 1u));
+        if (lane == b) mine = word;
+      }
+      const uint32_t nan = __ballot_sync(FULL, in[u] && v[u] != v[u]);
+      if (lane == T.nbits) mine = nan;
+      const int y = y0 + idx / Wp, w = idx - (idx / Wp) * Wp;
+      if (lane <= T.nbits) out[(size_t)lane * pstride + (size_t)y * Wp + w] = mine;
     }
-    const uint32_t nan = __ballot_sync(FULL, in && v != v);
-    if (lane == T.nbits) mine = nan;
-    if (lane <= T.nbits) out[(size_t)lane * pstride + (size_t)y * Wp + w] = mine;
   }
 }
 
