@@ -19,6 +19,20 @@ VL_DEV uint32_t vmask(int w, int W) {
 VL_DEV uint32_t le_mask(int b) { return b >= 31 ? 0xFFFFFFFFu : ((2u << b) - 1u); }
 
 // Loads that bypass L1: data written by other CTAs of the same launch.
+// Row and column of element i of a row-major grid of `cols` columns: a
+// 32-bit division while i < 2^32 (every word index, and every pixel index
+// of a grid under 2^32 pixels), else a 64-bit one.
+VL_DEV void split_index(long long i, int cols, int& row, int& col) {
+  if (i < (1LL << 32)) {
+    const unsigned u = (unsigned)i, c = (unsigned)cols, r = u / c;
+    row = (int)r;
+    col = (int)(u - r * c);
+  } else {
+    row = (int)(i / cols);
+    col = (int)(i - (long long)row * cols);
+  }
+}
+
 VL_DEV uint32_t ldcg(const uint32_t* p) { return __ldcg(p); }
 VL_DEV int32_t ldcg(const int32_t* p) { return __ldcg(p); }
 VL_DEV float ldcg(const float* p) { return __ldcg(p); }

@@ -38,7 +38,8 @@ __global__ void k_threshold(const void* __restrict__ plane, int format, int pitc
     for (int u = 0; u < 2; ++u) {
       const long long i = base + 4 * u + (lane >> 3);
       if (i < nwords) {
-        const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+        int y, w;
+        split_index(i, g.Wp, y, w);
         v[u] = ld_px4(plane, format, true, (size_t)y * pitch + 32 * w + 4 * sub);
       } else {
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -54,7 +55,11 @@ __global__ void k_threshold(const void* __restrict__ plane, int format, int pitc
       word |= __shfl_xor_sync(FULL, word, 2);
       word |= __shfl_xor_sync(FULL, word, 4);
       const long long i = base + 4 * u + (lane >> 3);
-      if (sub == 0 && i < nwords) out[i] = word & vmask((int)(i % g.Wp), g.W);
+      if (sub == 0 && i < nwords) {
+        int y, w;
+        split_index(i, g.Wp, y, w);
+        out[i] = word & vmask(w, g.W);
+      }
     }
   }
 }
@@ -65,7 +70,8 @@ __global__ void k_pointwise(const uint32_t* __restrict__ a, const uint32_t* __re
   const long long nwords = (long long)g.H * g.Wp;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
        i += (long long)gridDim.x * blockDim.x) {
-    const int w = (int)(i % g.Wp);
+    int y, w;
+    split_index(i, g.Wp, y, w);
     uint32_t v;
     if (OP == 0) v = ~__ldg(a + i) & vmask(w, g.W);
     else if (OP == 1) v = __ldg(a + i) & __ldg(b + i);
@@ -82,7 +88,8 @@ __global__ void k_near(const uint32_t* __restrict__ a, MaskGeom g, int conn,
   const long long nwords = (long long)g.H * g.Wp;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
        i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+    int y, w;
+    split_index(i, g.Wp, y, w);
     uint32_t r[3][3];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
@@ -122,6 +129,13 @@ __global__ void k_sel_init(WideSel* st, long long rank) {
   st->rank = (unsigned long long)rank;
 }
 
+// Each thread takes SEL_UNR elements a grid stride apart per iteration (their
+// loads in flight together); the row and column of an element are stepped
+// by the stride instead of divided out.  A warp whose elements all fall in
+// one bin (a background value) counts them with one shared atomic, else
+// each element with its own; a warp none of whose elements passes the
+// prefix skips both.
+constexpr int SEL_UNR = 4;
 __global__ void __launch_bounds__(256) k_sel_hist(const void* plane, int format, int pitch, int H,
                                                   int W, const WideSel* st, int sh, int nb,
                                                   uint32_t* hist) {
@@ -132,18 +146,35 @@ __global__ void __launch_bounds__(256) k_sel_hist(const void* plane, int format,
   const int lane = threadIdx.x & 31;
   const long long n = (long long)H * W;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long i = base + threadIdx.x;  // warp-uniform loop: every lane runs the match
-    const bool in = i < n;
-    uint32_t key = 0;
-    if (in) {
-      const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-      key = f2key(ld_px(plane, format, true, (size_t)y * pitch + x));
+  const int sy = (int)(stride / W), sx = (int)(stride - (long long)sy * W);
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int y = (int)(i / W), x = (int)(i - (long long)y * W);
+  // warp-uniform loop (every lane runs the ballots and the match)
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += SEL_UNR * stride) {
+    uint32_t key[SEL_UNR];
+    bool in[SEL_UNR];
+#pragma unroll
+    for (int u = 0; u < SEL_UNR; ++u) {
+      in[u] = i < n;
+      key[u] = in[u] ? f2key(ld_px(plane, format, true, (size_t)y * pitch + x)) : 0u;
+      i += stride;
+      y += sy;
+      x += sx;
+      if (x >= W) { x -= W; ++y; }
     }
-    const bool ok = in && (key & pmask) == prefix;
-    const uint32_t bin = (key >> sh) & (uint32_t)(nb - 1);
-    const unsigned grp = __match_any_sync(0xFFFFFFFFu, ok ? bin : 0xFFFFFFFFu);
-    if (ok && lane == __ffs(grp) - 1) atomicAdd(&h[bin], (uint32_t)__popc(grp));
+#pragma unroll
+    for (int u = 0; u < SEL_UNR; ++u) {
+      const bool ok = in[u] && (key[u] & pmask) == prefix;
+      if (!__any_sync(0xFFFFFFFFu, ok)) continue;
+      const uint32_t bin = (key[u] >> sh) & (uint32_t)(nb - 1);
+      int same = 0;
+      __match_all_sync(0xFFFFFFFFu, ok ? bin : 0xFFFFFFFFu, &same);
+      if (same) {  // the whole warp in one bin (a background value)
+        if (lane == 0) atomicAdd(&h[bin], 32u);
+      } else if (ok) {
+        atomicAdd(&h[bin], 1u);
+      }
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x)
@@ -189,7 +220,8 @@ __global__ void k_arith(int op, const void* __restrict__ a, int a_format, const 
   const long long n = (long long)H * W;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    int y, x;
+    split_index(i, W, y, x);
     const size_t off = (size_t)y * pitch + x;
     const float u = ld_px(a, a_format, false, off);
     const float w = b ? ld_px(b, b_format, false, off) : c;
@@ -268,7 +300,8 @@ __global__ void k_pack_u8(const uint8_t* __restrict__ src, MaskGeom g, uint32_t*
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nwords;
        i += nwarps) {
-    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+    int y, w;
+    split_index(i, g.Wp, y, w);
     const int x = 32 * w + lane;
     const bool p = (x < g.W) && src[(size_t)y * g.W + x] != 0;
     const uint32_t word = __ballot_sync(FULL, p);
@@ -280,7 +313,8 @@ __global__ void k_unpack_u8(const uint32_t* __restrict__ src, MaskGeom g, uint8_
   const long long n = (long long)g.H * g.W;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / g.W), x = (int)(i - (long long)y * g.W);
+    int y, x;
+    split_index(i, g.W, y, x);
     out[i] = (uint8_t)((__ldg(src + (size_t)y * g.Wp + (x >> 5)) >> (x & 31)) & 1u);
   }
 }
@@ -288,8 +322,11 @@ __global__ void k_unpack_u8(const uint32_t* __restrict__ src, MaskGeom g, uint8_
 __global__ void k_clear_padding(uint32_t* m, MaskGeom g) {
   const long long nwords = (long long)g.H * g.Wp;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
-       i += (long long)gridDim.x * blockDim.x)
-    m[i] &= vmask((int)(i % g.Wp), g.W);
+       i += (long long)gridDim.x * blockDim.x) {
+    int y, w;
+    split_index(i, g.Wp, y, w);
+    m[i] &= vmask(w, g.W);
+  }
 }
 
 }  // namespace

@@ -45,7 +45,8 @@ __global__ void k_near3(const uint32_t* __restrict__ a, MaskGeom g, int conn,
   const long long nwords = (long long)g.H * g.Wp;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
        i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+    int y, w;
+    split_index(i, g.Wp, y, w);
     const int z = y / Hs, yz = y - z * Hs;
     uint32_t res;
     if (conn == 26) {
@@ -76,25 +77,27 @@ __global__ void k_near3(const uint32_t* __restrict__ a, MaskGeom g, int conn,
   }
 }
 
-// Unite the components of slices z and z + 1: one warp per (z, y, dy, word).
+// Unite the components of slices z and z + 1: one warp per row pair (z, y)
+// -- placed by a 32-bit division -- looping over the row's words and, for
+// 26-adjacency, the rows y - 1, y, y + 1 of slice z + 1.
 // L holds, for every voxel of the mask, its component's key (after the 2D
 // pass: the minimum index of its slice component, which is a root).
 __global__ void k_zmerge(const uint32_t* m, MaskGeom g, int conn, int32_t* L, int32_t* status) {
   const int Hs = slice_rows(g), D = g.H / Hs;
   const int nd = conn == 26 ? 3 : 1;
-  const long long units = (long long)(D - 1) * Hs * nd * g.Wp;
+  const long long rows = (long long)(D - 1) * Hs;
   const int npx = g.H * g.W;
   const long long wpb = blockDim.x >> 5;
-  for (long long u = blockIdx.x * wpb + (threadIdx.x >> 5); u < units; u += gridDim.x * wpb) {
-    long long r = u;
-    const int w = (int)(r % g.Wp); r /= g.Wp;
-    const int k = (int)(r % nd); r /= nd;
-    const int yz = (int)(r % Hs);
-    const int z = (int)(r / Hs);
-    const int yb = yz + (nd == 3 ? k - 1 : 0);
-    if (yb < 0 || yb >= Hs) continue;  // uniform across the warp
-    ccl_merge_rows(m, g.W, g.Wp, z * Hs + yz, (z + 1) * Hs + yb, w, conn == 26 ? 8 : 4, L, npx,
-                   status);
+  for (long long r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += gridDim.x * wpb) {
+    int z, yz;  // uniform across the warp
+    split_index(r, Hs, z, yz);
+    for (int w = 0; w < g.Wp; ++w)
+      for (int k = 0; k < nd; ++k) {
+        const int yb = yz + (nd == 3 ? k - 1 : 0);
+        if (yb < 0 || yb >= Hs) continue;
+        ccl_merge_rows(m, g.W, g.Wp, z * Hs + yz, (z + 1) * Hs + yb, w, conn == 26 ? 8 : 4, L,
+                       npx, status);
+      }
   }
 }
 
@@ -103,11 +106,18 @@ __global__ void k_zmerge(const uint32_t* m, MaskGeom g, int conn, int32_t* L, in
 // on the way).
 __global__ void k_relabel(const uint32_t* m, MaskGeom g, int32_t* L, int32_t* status) {
   const int npx = g.H * g.W;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npx;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / g.W), x = (int)(i - (long long)y * g.W);
+  // grid-stride over the voxels, row and column stepped instead of divided
+  const int stride = gridDim.x * blockDim.x;
+  const int sy = stride / g.W, sx = stride - sy * g.W;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int y, x;
+  split_index(i, g.W, y, x);
+  for (; i < npx; i += stride) {
     if ((__ldg(m + (size_t)y * g.Wp + (x >> 5)) >> (x & 31)) & 1u)
       L[i] = g_find(L, ldcg(&L[i]), npx, status);
+    y += sy;
+    x += sx;
+    if (x >= g.W) { x -= g.W; ++y; }
   }
 }
 
@@ -118,7 +128,8 @@ __global__ void k_seed_flags(const uint32_t* seed, MaskGeom g, const int32_t* L,
   const long long nwords = (long long)g.H * g.Wp;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
        i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+    int y, w;
+    split_index(i, g.Wp, y, w);
     const uint32_t cur = __ldg(seed + i) & vmask(w, g.W);
     const uint32_t prev = w > 0 ? __ldg(seed + i - 1) : 0u;
     uint32_t bits = cur & ~((cur << 1) | (prev >> 31));
@@ -138,7 +149,8 @@ __global__ void k_select_flagged(const uint32_t* phi2, MaskGeom g, const int32_t
   const long long nwords = (long long)g.H * g.Wp;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nwords;
        i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / g.Wp), w = (int)(i - (long long)y * g.Wp);
+    int y, w;
+    split_index(i, g.Wp, y, w);
     const uint32_t bits = __ldg(phi2 + i) & vmask(w, g.W);
     uint32_t starts = bits & ~(bits << 1), sel = 0;  // run starts inside this word
     while (starts) {
@@ -168,8 +180,8 @@ cudaError_t launch_labels3(const uint32_t* mask, MaskGeom g, int conn, CclScratc
   if (e) return e;
   const int Hs = slice_rows(g), D = g.H / Hs;
   if (D < 2) return cudaSuccess;
-  const long long units = (long long)(D - 1) * Hs * (conn == 26 ? 3 : 1) * g.Wp;
-  k_zmerge<<<grid_for(units * 32, kThreads), kThreads, 0, st>>>(mask, g, conn, sc.G, status);
+  const long long rows = (long long)(D - 1) * Hs;  // one warp per row pair
+  k_zmerge<<<grid_for(rows * 32, kThreads), kThreads, 0, st>>>(mask, g, conn, sc.G, status);
   if ((e = cudaGetLastError())) return e;
   k_relabel<<<grid_for((long long)g.H * g.W, kThreads * 4), kThreads, 0, st>>>(mask, g, sc.G, status);
   return cudaGetLastError();
