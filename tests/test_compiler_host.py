@@ -390,3 +390,29 @@ def test_sequential_chains_plan_matches_oracle(mix, conn):
     img = wl.gaussian_field_image(40, 300, sigma=8.0, seed=7)
     _check_sim(f, [img], conn=conn)
     _check_sim(f, [img], conn=conn, shuffle=3)
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_group_steps_record_the_buffers_they_use(seed):
+    """Each group step's n_bufs is one past the highest tile buffer its
+    instructions touch (the executor places the shared-memory stage of rank
+    planes right after them, so a lower count would let the stage overwrite
+    a live buffer)."""
+    f = wl.random_dag(2000, seed=seed)
+    p = vg.compile_formula(_rec(f), f.roots, 8).plan()
+    ins = p["insns"]
+    groups = [s for s in p["steps"] if s["kind"] == 1]
+    assert groups
+    for s in groups:
+        hi = 0
+        for i in ins[s["insn_off"]:s["insn_off"] + s["insn_cnt"]]:
+            op = i["op"]
+            if op != 8:                      # every op but the store writes dst
+                hi = max(hi, i["dst"] + 1)
+            if op in (3, 4, 5, 6, 8, 9):     # not, and, or, N, store, and-not read a
+                hi = max(hi, i["a"] + 1)
+            if op in (4, 5, 9):              # and, or, and-not read b
+                hi = max(hi, i["b"] + 1)
+        assert s["n_bufs"] == hi, (s, hi)
+    for s in p["steps"]:
+        if s["kind"] != 1:
+            assert s["n_bufs"] == 0
