@@ -470,7 +470,11 @@ typedef struct {
 } vl_tile_choice;
 
 /* Time `jobs` under every candidate tile shape and CTAs-per-SM count that
- * fits, and for a batch of one job its per-operator form (reps timed
+ * fits -- the fixed shapes 32x32, 64x16, 32x16, 16x32, 16x16, 64x8, 32x8,
+ * 16x8 (rows x words) and, for a batch of one job, per tile width of 32 and
+ * 16 words the lowest height whose tiles fit one wave of the grid (2048 x
+ * 2048 on 152 SMs: 14x32 and 27x16) -- and for a batch of one job its
+ * per-operator form (reps timed
  * launches each, every one after a 192 MB write that clears the L2, after
  * untimed launches whose device status must be VL_OK; the library holds
  * that scratch while tuning), keep the fastest in the context's table for the
