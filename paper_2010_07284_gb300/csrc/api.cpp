@@ -4,9 +4,9 @@
 #include <cmath>
 #include <cstring>
 #include <map>
-#include <queue>
 
 #include "runtime.h"
+#include "schedule.h"
 
 using namespace vl;
 
@@ -305,23 +305,11 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     I.off_images = take(sizeof(DevImage) * std::max(1, I.n_table));
     I.off_slotptrs = take(sizeof(uint32_t*) * std::max(1, P.n_inter_slots + P.n_root_slots + P.n_mask_slots));
   }
-  // work items.  One job: in the order of a list-scheduling simulation on
-  // `grid` CTAs -- a CTA that frees up takes the ready item whose step has
-  // the longest estimated path to the end of the job (its bottom level), and
-  // items are emitted in the order the simulation starts them.  An item
-  // starts only after every step it depends on has finished, so everything
-  // an item waits for comes earlier in the list.  (Ordering by start times
-  // estimated as if the GPU had unlimited CTAs let wide steps off the
-  // critical path take every CTA just before a critical step became ready.)
-  // Several jobs: by those unbounded start times, so that jobs of very
-  // different sizes interleave by their progress and a small job finishes
-  // early (by bottom level a server's small queries waited for the large
-  // ones' critical paths: p50 latency 34 -> 128 ms).  Steps split into items
-  // of about a tile each, at most 4 x grid items per step.
+  // work items: every step split into items of about a tile each (at most
+  // 4 x grid items per step), with an estimated time per item, then put in
+  // executor order (order_work_items in schedule.cpp: a list-scheduling
+  // simulation by bottom level for one job, progress order for several).
   {
-    struct StepRec { int j, s, first, n; double item_us, bl, t0; int deps_left; };
-    std::vector<StepRec> recs;
-    std::vector<int> rec_of_job(n_jobs + 1, 0);
     long long subitems = 0;
     for (int j = 0; j < n_jobs; ++j)
       for (size_t s = 0; s < J[j].need.size(); ++s) subitems += J[j].need[s];
@@ -332,9 +320,11 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
     // merging the tiles of a step there only serialises them on fewer CTAs
     const bool plenty = subitems > 32LL * grid;
     std::vector<WorkItem> pending;  // every item, step by step
+    std::vector<SchedJob> sj(n_jobs);
     for (int j = 0; j < n_jobs; ++j) {
-      rec_of_job[j] = (int)recs.size();
       const Plan& P = *J[j].P;
+      sj[j].dep_off = P.dep_off.data();
+      sj[j].deps = P.deps.data();
       const double tile_scale = (double)ts.rows * ts.words / (16.0 * 32.0);
       for (size_t si = 0; si < J[j].need.size(); ++si) {
         const StepDesc& sd = P.steps[si];
@@ -365,94 +355,14 @@ vl_status batch_build(vl_context* ctx, const vl_job* jobs, int n_jobs, cudaStrea
           chunk = std::max<long long>(chunk, std::min<long long>(
               {(long long)n, (long long)std::ceil(40.0 / tile_us), side_by_side}));
         }
-        StepRec r{j, (int)si, (int)pending.size(), 0, sub_us * chunk, 0.0, 0.0, 0};
-        for (int first = 0; first < n; first += chunk, ++r.n)
+        SchedStep st{(int)pending.size(), 0, sub_us * chunk};
+        for (int first = 0; first < n; first += chunk, ++st.n)
           pending.push_back(WorkItem{j, (int)si, first, std::min(chunk, n - first)});
-        r.deps_left = P.dep_off[si + 1] - P.dep_off[si];
-        recs.push_back(r);
+        sj[j].steps.push_back(st);
       }
     }
-    rec_of_job[n_jobs] = (int)recs.size();
-    // bottom levels: a step's estimated length plus the longest of its
-    // successors' (deps point at earlier steps, so one backward sweep)
-    std::vector<std::vector<int>> succ(recs.size());
-    for (int j = 0; j < n_jobs; ++j) {
-      const Plan& P = *J[j].P;
-      const int base = rec_of_job[j];
-      for (size_t si = 0; si < J[j].need.size(); ++si)
-        for (int q = P.dep_off[si]; q < P.dep_off[si + 1]; ++q)
-          succ[base + P.deps[q]].push_back(base + (int)si);
-    }
-    for (int r = (int)recs.size() - 1; r >= 0; --r) {
-      double tail = 0;
-      for (int x : succ[r]) tail = std::max(tail, recs[x].bl);
-      recs[r].bl = std::ceil((double)recs[r].n / grid) * recs[r].item_us + tail;
-    }
-    if (n_jobs > 1) {
-      // each step's start if its job ran alone on the whole GPU: the latest
-      // estimated finish of its dependencies
-      for (int j = 0; j < n_jobs; ++j) {
-        const Plan& P = *J[j].P;
-        const int base = rec_of_job[j];
-        std::vector<double> fin(J[j].need.size(), 0.0);
-        for (size_t si = 0; si < J[j].need.size(); ++si) {
-          double t = 0;
-          for (int q = P.dep_off[si]; q < P.dep_off[si + 1]; ++q) t = std::max(t, fin[P.deps[q]]);
-          StepRec& r = recs[base + si];
-          r.t0 = t;
-          fin[si] = t + std::ceil((double)r.n / grid) * r.item_us;
-        }
-      }
-      std::vector<int> order(recs.size());
-      for (size_t r = 0; r < recs.size(); ++r) order[r] = (int)r;
-      std::stable_sort(order.begin(), order.end(),
-                       [&](int a, int b) { return recs[a].t0 < recs[b].t0; });
-      for (int r : order)
-        for (int k = 0; k < recs[r].n; ++k) items.push_back(pending[recs[r].first + k]);
-    }
-    // the simulation: ready items by (bottom level, then list position)
-    struct Ready {
-      double bl; int idx;
-      bool operator<(const Ready& o) const { return bl != o.bl ? bl < o.bl : idx > o.idx; }
-    };
-    struct Busy {
-      double t; int rec;
-      bool operator<(const Busy& o) const { return t > o.t; }
-    };
-    std::priority_queue<Ready> ready;
-    std::priority_queue<Busy> busy;
-    std::vector<int> left(recs.size());
-    auto release = [&](int r) {
-      for (int k = 0; k < recs[r].n; ++k) ready.push(Ready{recs[r].bl, recs[r].first + k});
-    };
-    for (size_t r = 0; r < recs.size(); ++r) {
-      left[r] = recs[r].n;
-      if (recs[r].deps_left == 0) release((int)r);
-    }
-    std::vector<int> rec_index(pending.size());
-    for (size_t r = 0; r < recs.size(); ++r)
-      for (int k = 0; k < recs[r].n; ++k) rec_index[recs[r].first + k] = (int)r;
-    items.reserve(pending.size());
-    double now = 0;
-    int free_ctas = grid;
-    while (n_jobs == 1 && items.size() < pending.size()) {
-      while (free_ctas > 0 && !ready.empty()) {
-        const int idx = ready.top().idx;
-        ready.pop();
-        items.push_back(pending[idx]);
-        busy.push(Busy{now + recs[rec_index[idx]].item_us, rec_index[idx]});
-        --free_ctas;
-      }
-      if (busy.empty()) break;  // (cannot happen: some step is always ready)
-      const Busy b = busy.top();
-      busy.pop();
-      now = b.t;
-      ++free_ctas;
-      if (--left[b.rec] == 0)
-        for (int x : succ[b.rec])
-          if (--recs[x].deps_left == 0) release(x);
-    }
-    if (items.size() != pending.size()) return set_err(ctx, VL_ERR_INTERNAL, "internal: step order");
+    if (!order_work_items(sj, pending, grid, &items))
+      return set_err(ctx, VL_ERR_INTERNAL, "internal: step order");
   }
   const size_t off_items = take(sizeof(WorkItem) * std::max<size_t>(1, items.size()));
   const size_t off_need = take(sizeof(int32_t) * std::max(1, total_steps));
