@@ -10,7 +10,10 @@ read and write their own words, N reads the 3 x 3 words around its own, a
 store reads the core words it owns, the float threshold writes its words
 from other lanes -- and reports any read after a write, write after a read,
 or write after a write of one word by two threads with no barrier between.
-It runs over the tile shapes the autotuner tries.
+It runs over the tile shapes the autotuner tries: the fixed ones, the
+one-wave shapes it adds for a single job (on a 2048 x 2048 image 14 x 32
+and 27 x 16), and short last tile rows (an image height that is not a
+multiple of the tile height).
 """
 from __future__ import annotations
 
@@ -23,7 +26,8 @@ from test_compiler_fuzz import random_formula
 
 NT = 512
 HMAX = 8
-SHAPES = [(32, 32), (64, 16), (32, 16), (16, 32), (16, 16), (64, 8), (32, 8), (16, 8)]
+SHAPES = [(32, 32), (64, 16), (32, 16), (16, 32), (16, 16), (64, 8), (32, 8), (16, 8),
+          (14, 32), (27, 16), (4, 32), (1, 16)]
 OWN_WRITE = {1: False, 2: True, 3: True, 4: True, 5: True, 6: True, 7: True, 9: True, 10: True}
 
 
