@@ -265,6 +265,48 @@ VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes,
                                     int32_t n_roots, int32_t connectivity,
                                     vl_formula** out);
 
+/* Compile a specification text in the command language of the paper's tool
+ * (Sec. 3: commands let / load / save; expressions are numbers, names,
+ * applications f(e1, ..., eN), infix applications and parenthesised
+ * expressions; macros are expanded, sharing identical sub-expressions).
+ * The paper defers the grammar to the tool's documentation; this library
+ * reads it as follows.
+ *   load x = "s"            x names the next image given at evaluation
+ *                           (images in load order; "s" only labels it)
+ *   let x = e               a constant
+ *   let f(p1, ..., pN) = e  a macro; a body sees its parameters and the
+ *                           names defined before it is applied
+ *   save "s" e              an output: the mask e (roots in save order)
+ *   import "s"              accepted and ignored (derived operators are
+ *                           built in)
+ *   // ...                  a comment, to the end of the line
+ * Expressions, loosest binding first: a | b (or), a & b (and), a >. t and
+ * a <. t (strict comparisons of a number term with a number or with
+ * percentile(a, q), not chained), + and -, * and /, prefix ! (not) and -.
+ * Functions: intensity(x) (channel 0 of image x), red, green, blue, alpha
+ * (channels 0-3), channel(x, c), mask(x) (a binary image as an atom),
+ * percentile(term, q) (q in [0, 1], only as a comparison's bound), not,
+ * and, or, near or N, interior, surrounded(a, b), grow(a, b), touch(a, b),
+ * reach or rho(a, b) (= rho a[b]); tt and ff are the constants.  Numbers
+ * combine exactly and are rounded to float32 where a node takes them;
+ * t - term is computed as (term * -1) + t, and number / term is refused.
+ * connectivity as for vl_formula_compile.  err_buf (err_len bytes, may be
+ * NULL) receives "" or the error, "line L, column C: ..." for the text.
+ * Errors: VL_ERR_FORMULA (syntax, unknown or redefined names, a value of
+ * the wrong kind, nothing saved, and the compiler's own checks), VL_ERR_ARG.
+ * ctx may be NULL as for vl_formula_compile. */
+VL_API vl_status vl_formula_compile_text(vl_context* ctx, const char* src,
+                                         int32_t connectivity, vl_formula** out,
+                                         char* err_buf, int32_t err_len);
+
+/* Names of a formula compiled from a text: which = 0 its loads (the image
+ * order), 1 its saves (the root order).  *count (may be NULL) receives how
+ * many; with buf non-NULL, name `index` is copied there (NUL-terminated,
+ * cut to len - 1 bytes).  A formula compiled from nodes has none.  Errors:
+ * VL_ERR_ARG (bad handle, which or index). */
+VL_API vl_status vl_formula_spec_names(const vl_formula* f, int32_t which, int32_t* count,
+                                       int32_t index, char* buf, int32_t len);
+
 /* Introspection of a compiled plan (debugging and host-side tests).  Call
  * with NULL arrays to get the sizes, then again with arrays of at least
  * those lengths.  Steps run in order; a step of kind 1 (fused group) runs

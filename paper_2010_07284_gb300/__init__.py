@@ -18,8 +18,9 @@ ctypes front-end.
   ctx.ccl_pointer_jumping(mask, labels)   # the paper's Alg. 1, for comparison
 """
 from ._native import (VlError, OPCODES, EXEC_FUSED, EXEC_PLAIN, load, lib_path)
-from .api import Context, Image, Formula, Result, Batch, Server, compile_formula
+from .api import Context, Image, Formula, Result, Batch, Server, compile_formula, compile_text
 from .buildlib import build, source_hash
 
 __all__ = ["VlError", "OPCODES", "EXEC_FUSED", "EXEC_PLAIN", "load", "lib_path", "Context",
-           "Image", "Formula", "Result", "Batch", "Server", "build", "source_hash", "compile_formula"]
+           "Image", "Formula", "Result", "Batch", "Server", "build", "source_hash", "compile_formula",
+           "compile_text"]

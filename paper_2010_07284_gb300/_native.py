@@ -133,6 +133,8 @@ SIGNATURES = [
     ("vl_mask_create_packed", C.c_int, [_P, _I32, _I32, _P, _I32, _P, _PP]),
     ("vl_image_info", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_compile", C.c_int, [_P, C.POINTER(VlNode), _I32, C.POINTER(_I32), _I32, _I32, _PP]),
+    ("vl_formula_compile_text", C.c_int, [_P, C.c_char_p, _I32, _PP, C.c_char_p, _I32]),
+    ("vl_formula_spec_names", C.c_int, [_P, _I32, C.POINTER(_I32), _I32, C.c_char_p, _I32]),
     ("vl_formula_step_deps", C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32)]),
     ("vl_formula_rank_tables", C.c_int, [_P, C.POINTER(VlPlanRank), C.POINTER(C.c_float)]),
     ("vl_formula_arith", C.c_int, [_P, C.POINTER(VlPlanArith), C.POINTER(_I32), C.POINTER(_I32),

@@ -176,6 +176,11 @@ class Context(_Handle):
         self._check(rc)
         return Formula(self, out.value)
 
+    def compile_text(self, src: str, conn: int = 8) -> "Formula":
+        """A specification text (vl_formula_compile_text) planned for this
+        context; images go in the order of its loads."""
+        return Formula(self, _compile_text(self._ptr, src, conn))
+
     # -------------------------------------------------------- evaluation
     def eval(self, formula: "Formula", images: Sequence["Image"], stream=None,
              mode: Optional[str] = None) -> "Result":
@@ -315,9 +320,47 @@ def compile_formula(nodes: Sequence, roots: Sequence[int], conn: int = 8) -> "Fo
     return Formula(None, out.value)
 
 
+def _compile_text(ctx_ptr, src: str, conn: int) -> int:
+    lib = N.load()
+    out = C.c_void_p()
+    err = C.create_string_buffer(512)
+    rc = lib.vl_formula_compile_text(ctx_ptr, src.encode(), conn, C.byref(out), err, len(err))
+    if rc != N.OK:
+        raise N.VlError(rc, err.value.decode() or "specification rejected")
+    return out.value
+
+
+def compile_text(src: str, conn: int = 8) -> "Formula":
+    """Compile a specification text (vl_formula_compile_text) without a
+    context (host only); images go in the order of its loads, roots are its
+    saves (Formula.loads, Formula.saves)."""
+    return Formula(None, _compile_text(None, src, conn))
+
+
 class Formula(_Handle):
     def __init__(self, ctx: Optional[Context], ptr: int):
         self.ctx, self._ptr = ctx, ptr
+
+    def _names(self, which: int) -> list:
+        lib = N.load()
+        n = C.c_int32()
+        self._check(lib.vl_formula_spec_names(self._ptr, which, C.byref(n), 0, None, 0))
+        buf = C.create_string_buffer(256)
+        out = []
+        for k in range(n.value):
+            self._check(lib.vl_formula_spec_names(self._ptr, which, None, k, buf, len(buf)))
+            out.append(buf.value.decode())
+        return out
+
+    @property
+    def loads(self) -> list:
+        """Image names of a formula compiled from text, in image order."""
+        return self._names(0)
+
+    @property
+    def saves(self) -> list:
+        """Output names of a formula compiled from text, in root order."""
+        return self._names(1)
 
     def plan(self) -> dict:
         """The compiled execution plan (steps, instructions, selects, slots)."""

@@ -20,7 +20,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels.cu", "executor.cu", "noalloc.cu", "pointer_jump.cu", "volume.cu"]
-CPP_SOURCES = ["api.cpp", "autotune.cpp", "compiler.cpp", "schedule.cpp", "server.cpp"]
+CPP_SOURCES = ["api.cpp", "autotune.cpp", "compiler.cpp", "schedule.cpp", "server.cpp", "spec.cpp"]
 
 
 def lib_path() -> str:

@@ -2,11 +2,13 @@
 // connected components.  See include/vl.h for the contract of each call.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 
 #include "runtime.h"
 #include "schedule.h"
+#include "spec.h"
 
 using namespace vl;
 
@@ -1276,6 +1278,41 @@ VL_API vl_status vl_formula_compile(vl_context* ctx, const vl_node* nodes, int32
   if (rc != VL_OK) return set_err(ctx, (vl_status)rc, err);
   f->plan_hash = plan_hash(f->plan);
   *out = f.release();
+  return VL_OK;
+}
+
+VL_API vl_status vl_formula_compile_text(vl_context* ctx, const char* src, int32_t connectivity,
+                                         vl_formula** out, char* err_buf, int32_t err_len) {
+  if (ctx && !valid(ctx, TAG_CTX)) return VL_ERR_ARG;
+  auto report = [&](vl_status s, const std::string& m) {
+    if (err_buf && err_len > 0) std::snprintf(err_buf, (size_t)err_len, "%s", m.c_str());
+    return s == VL_OK ? VL_OK : set_err(ctx, s, m);
+  };
+  if (!out || !src) return report(VL_ERR_ARG, "null argument");
+  TextSpec spec;
+  std::string err;
+  if (!parse_spec(src, &spec, &err)) return report(VL_ERR_FORMULA, err);
+  auto f = std::make_unique<vl_formula>();
+  f->ctx = ctx;
+  f->pp = ctx ? ctx->pp : default_plan_params();
+  const int rc = compile_formula(spec.nodes.data(), (int32_t)spec.nodes.size(), spec.roots.data(),
+                                 (int32_t)spec.roots.size(), connectivity, f->pp, &f->plan, &err);
+  if (rc != VL_OK) return report((vl_status)rc, err);
+  f->plan_hash = plan_hash(f->plan);
+  f->loads = spec.loads;
+  f->saves = spec.saves;
+  *out = f.release();
+  return report(VL_OK, "");
+}
+
+VL_API vl_status vl_formula_spec_names(const vl_formula* f, int32_t which, int32_t* count,
+                                       int32_t index, char* buf, int32_t len) {
+  if (!valid(f, TAG_FML) || (which != 0 && which != 1)) return VL_ERR_ARG;
+  const std::vector<std::string>& v = which == 0 ? f->loads : f->saves;
+  if (count) *count = (int32_t)v.size();
+  if (!buf) return VL_OK;
+  if (index < 0 || index >= (int32_t)v.size() || len < 1) return VL_ERR_ARG;
+  std::snprintf(buf, (size_t)len, "%s", v[index].c_str());
   return VL_OK;
 }
 

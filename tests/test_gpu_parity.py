@@ -255,3 +255,33 @@ def test_longest_sides(shape):
     ctx.ccl(ctx.mask(m), lab, 4)
     assert ctx.ccl_status() == 0
     np.testing.assert_array_equal(lab.cpu().numpy().reshape(shape), oracle.ccl(m, 4)[0])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+def test_specification_text_on_the_gpu(mode):
+    """A specification text (vl_formula_compile_text) evaluated through the
+    CUDA path equals the oracle on the node formula it spells out."""
+    torch_cuda()
+    ctx = context(mode)
+    src = """
+    load a = "a"
+    load b = "b"
+    let band(x, lo, hi) = intensity(x) >. lo & intensity(x) <. hi
+    let core = band(a, 0.6, 0.95)
+    save "grown" grow(core, band(b, 0.2, 0.9))
+    save "edge" N(core) & !core | touch(core, intensity(b) >. percentile(intensity(b), 0.8))
+    """
+    F = ctx.compile_text(src, 8)
+    assert F.loads == ["a", "b"] and F.saves == ["grown", "edge"]
+    ims = [wl.gaussian_field_image(200, 300, seed=11), wl.gaussian_field_image(200, 300, seed=12)]
+    res = ctx.eval(F, [ctx.image(im) for im in ims])
+    assert res.sync() == 0, ctx.last_error()
+    got = [res.mask(r) for r in range(2)]
+    N = lambda op, a=-1, b=-1, image=0, t=0.0, q=0.0: (op, a, b, image, 0, float(np.float32(t)), q)
+    nodes = [N("THR_GT", image=0, t=0.6), N("THR_LT", image=0, t=0.95), N("AND", 0, 1),
+             N("THR_GT", image=1, t=0.2), N("THR_LT", image=1, t=0.9), N("AND", 3, 4),
+             N("GROW", 2, 5), N("NEAR", 2), N("NOT", 2), N("AND", 7, 8),
+             N("PCT_GT", image=1, q=0.8), N("TOUCH", 2, 10), N("OR", 9, 11)]
+    exp = oracle.evaluate(nodes, [6, 12], ims, conn=8).masks
+    assert_same(got, exp, mode)
