@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <tuple>
 
@@ -122,6 +123,7 @@ struct Parser {
   std::vector<Token> t;
   size_t i = 0;
   std::vector<Ast> ast;
+  int depth = 0;  // nesting of the expression being parsed (bounded: no stack overflow)
 
   const Token& cur() const { return t[i]; }
   bool sym(const char* s) const { return cur().k == T_SYM && cur().s == s; }
@@ -149,7 +151,12 @@ struct Parser {
     ast[n].kids = {l, r};
     return n;
   }
-  int expr() { return or_(); }
+  int expr() {
+    if (++depth > 1000) fail(cur().line, cur().col, "expression nested deeper than 1000");
+    const int e = or_();
+    --depth;
+    return e;
+  }
   int or_() {
     int l = and_();
     while (sym("|")) { const Token at = t[i++]; l = binary(l, at, "|", and_()); }
@@ -182,10 +189,12 @@ struct Parser {
   int unary() {
     if (sym("!") || sym("-")) {
       const Token at = t[i++];
+      if (++depth > 1000) fail(at.line, at.col, "expression nested deeper than 1000");
       const int n = node(A_UN, at);
       ast[n].s = at.s;
       const int k = unary();
       ast[n].kids = {k};
+      --depth;
       return n;
     }
     return primary();
@@ -403,7 +412,14 @@ struct Eval {
     err(a, "unknown name " + s);
   }
 
+  int edepth = 0;  // expansion depth (macros included): bounded, no stack overflow
   Val eval(int a) {
+    struct Depth {
+      int& d;
+      explicit Depth(int& x) : d(x) { ++d; }
+      ~Depth() { --d; }
+    } guard(edepth);
+    if (edepth > 4000) err(a, "expression expands deeper than 4000");
     const Ast& n = ast[a];
     switch (n.k) {
       case A_NUM: return lit(n.v);
@@ -496,6 +512,9 @@ bool parse_spec(const char* src, TextSpec* out, std::string* err) {
     if (spec.roots.empty()) fail(p.cur().line, p.cur().col, "nothing saved: a specification needs a save");
   } catch (const SpecError& e) {
     if (err) *err = "line " + std::to_string(e.line) + ", column " + std::to_string(e.col) + ": " + e.what;
+    return false;
+  } catch (const std::exception& e) {  // (memory): nothing may cross the C boundary
+    if (err) *err = std::string("specification not read: ") + e.what();
     return false;
   }
   *out = std::move(spec);

@@ -170,3 +170,16 @@ def test_comments_imports_and_names_of_node_formulas():
     assert F.loads == ["z"] and F.saves == ["all", "none"]
     G = vg.compile_formula([N("TRUE")], [0])
     assert G.loads == [] and G.saves == []
+
+
+def test_deep_nesting_is_refused_not_a_crash():
+    for src in ['load a = "a"\nsave "o" ' + "(" * 5000 + "mask(a)" + ")" * 5000,
+                'load a = "a"\nsave "o" ' + "!" * 3000 + "mask(a)"]:
+        with pytest.raises(vg.VlError) as e:
+            vg.compile_text(src)
+        assert "nested deeper than 1000" in str(e.value)
+    # 60 macros each applying the previous one: expanded, and shared
+    chain = "".join(f"let f{i}(m) = N(m) & f{i - 1}(m)\n" if i else "let f0(m) = N(m)\n"
+                    for i in range(60))
+    F = vg.compile_text('load a = "a"\n' + chain + 'save "o" f59(mask(a))')
+    assert F.saves == ["o"]
