@@ -183,3 +183,60 @@ def test_deep_nesting_is_refused_not_a_crash():
                     for i in range(60))
     F = vg.compile_text('load a = "a"\n' + chain + 'save "o" f59(mask(a))')
     assert F.saves == ["o"]
+
+
+def formula_text(recs, roots, with_mask):
+    """A node formula spelled as a specification: one `let` per node."""
+    lines = ['load img0 = "numbers"'] + (['load img1 = "mask"'] if with_mask else [])
+    infix = {"ADD": "+", "SUB": "-", "MUL": "*", "DIV": "/", "AND": "&", "OR": "|"}
+    calls = {"NEAR": "N", "INTERIOR": "interior", "REACH": "rho", "SURROUNDED": "surrounded",
+             "GROW": "grow", "TOUCH": "touch"}
+    for i, (op, a, b, im, ch, t, q) in enumerate(recs):
+        chan = f"channel(img{im}, {ch})"
+        if op == "VALUE":
+            e = chan
+        elif op in ("ADD", "SUB", "MUL", "DIV"):
+            e = f"n{a} {infix[op]} " + (f"n{b}" if b >= 0 else repr(t))
+        elif op in ("THR_GT", "THR_LT"):
+            e = f"{f'n{a}' if a >= 0 else chan} {'>.' if op == 'THR_GT' else '<.'} {t!r}"
+        elif op in ("PCT_GT", "PCT_LT"):
+            term = f"n{a}" if a >= 0 else chan
+            e = f"{term} {'>.' if op == 'PCT_GT' else '<.'} percentile({term}, {q!r})"
+        elif op in ("TRUE", "FALSE"):
+            e = "tt" if op == "TRUE" else "ff"
+        elif op == "MASK":
+            e = f"mask(img{im})"
+        elif op == "NOT":
+            e = f"!n{a}"
+        elif op in ("AND", "OR"):
+            e = f"n{a} {infix[op]} n{b}"
+        elif op in ("NEAR", "INTERIOR"):
+            e = f"{calls[op]}(n{a})"
+        else:
+            e = f"{calls[op]}(n{a}, n{b})"
+        lines.append(f"let n{i} = {e}")
+    lines += [f'save "r{k}" n{r}' for k, r in enumerate(roots)]
+    return "\n".join(lines)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_formulas_spelled_as_text(seed):
+    """The compiler's fuzz formulas (every operator, number terms, masks),
+    written out as specification text: the text's plan, run by the host
+    simulation, equals the oracle on the node formula."""
+    from test_compiler_fuzz import random_formula
+    rng = np.random.default_rng(5000 + seed)
+    n_channels = int(rng.integers(1, 3))
+    with_mask = seed % 3 == 0
+    recs, roots = random_formula(rng, int(rng.integers(5, 70)), n_channels, with_mask)
+    H, W = int(rng.integers(1, 40)), int(rng.integers(1, 260))
+    conn = 8 if seed % 2 == 0 else 4
+    img = rng.random((n_channels, H, W)).astype(np.float32)
+    masks = {1: rng.random((H, W)) < 0.4} if with_mask else {}
+    recs_o = [(op, a, b, (0 if op == "MASK" else im), ch, t, q)
+              for (op, a, b, im, ch, t, q) in recs]
+    exp = oracle.evaluate(recs_o, roots, [img], [masks[1]] if with_mask else [], conn=conn).masks
+    F = vg.compile_text(formula_text(recs, roots, with_mask), conn)
+    assert len(F.saves) == len(roots)
+    got = plan_sim.simulate(F.plan(), [img, None] if with_mask else [img], masks, conn)
+    same(got, exp)
