@@ -300,7 +300,8 @@ VL_API vl_status vl_formula_compile_text(vl_context* ctx, const char* src,
                                          char* err_buf, int32_t err_len);
 
 /* Names of a formula compiled from a text: which = 0 its loads (the image
- * order), 1 its saves (the root order).  *count (may be NULL) receives how
+ * order), 1 its saves (the root order), 2 the strings of its loads (what
+ * each load names, in image order).  *count (may be NULL) receives how
  * many; with buf non-NULL, name `index` is copied there (NUL-terminated,
  * cut to len - 1 bytes).  A formula compiled from nodes has none.  Errors:
  * VL_ERR_ARG (bad handle, which or index). */

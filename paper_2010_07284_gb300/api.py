@@ -362,6 +362,11 @@ class Formula(_Handle):
         """Output names of a formula compiled from text, in root order."""
         return self._names(1)
 
+    @property
+    def sources(self) -> list:
+        """What each load of a formula compiled from text names, in image order."""
+        return self._names(2)
+
     def plan(self) -> dict:
         """The compiled execution plan (steps, instructions, selects, slots)."""
         lib = N.load()

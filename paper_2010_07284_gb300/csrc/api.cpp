@@ -1301,14 +1301,15 @@ VL_API vl_status vl_formula_compile_text(vl_context* ctx, const char* src, int32
   f->plan_hash = plan_hash(f->plan);
   f->loads = spec.loads;
   f->saves = spec.saves;
+  f->sources = spec.sources;
   *out = f.release();
   return report(VL_OK, "");
 }
 
 VL_API vl_status vl_formula_spec_names(const vl_formula* f, int32_t which, int32_t* count,
                                        int32_t index, char* buf, int32_t len) {
-  if (!valid(f, TAG_FML) || (which != 0 && which != 1)) return VL_ERR_ARG;
-  const std::vector<std::string>& v = which == 0 ? f->loads : f->saves;
+  if (!valid(f, TAG_FML) || which < 0 || which > 2) return VL_ERR_ARG;
+  const std::vector<std::string>& v = which == 0 ? f->loads : which == 1 ? f->saves : f->sources;
   if (count) *count = (int32_t)v.size();
   if (!buf) return VL_OK;
   if (index < 0 || index >= (int32_t)v.size() || len < 1) return VL_ERR_ARG;

@@ -93,7 +93,7 @@ struct vl_formula {
   vl::PlanParams pp{};
   vl::Plan plan;
   uint64_t plan_hash = 0;  // of the compiled plan: keys the tuning table
-  std::vector<std::string> loads, saves;  // names, when compiled from a specification text
+  std::vector<std::string> loads, saves, sources;  // when compiled from a specification text
 };
 
 struct vl_result {

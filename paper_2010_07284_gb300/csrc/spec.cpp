@@ -467,13 +467,14 @@ bool parse_spec(const char* src, TextSpec* out, std::string* err) {
         const std::string nm = p.ident("an image name");
         p.expect("=");
         if (p.cur().k != T_STR) fail(p.cur().line, p.cur().col, "expected a string");
-        ++p.i;
+        const std::string source = p.t[p.i++].s;
         if (ev.globals.count(nm) || ev.macros.count(nm)) fail(nt.line, nt.col, nm + " is already defined");
         Val v;
         v.k = V_IMG;
         v.img = (int)spec.loads.size();
         ev.globals[nm] = v;
         spec.loads.push_back(nm);
+        spec.sources.push_back(source);
       } else if (at.s == "let") {
         const Token nt = p.cur();
         const std::string nm = p.ident("a name");

@@ -12,6 +12,7 @@ struct TextSpec {
   std::vector<vl_node> nodes;       // topological order, shared sub-expressions
   std::vector<int32_t> roots;       // one per `save`, in order
   std::vector<std::string> loads;   // image names, in `load` order (image index)
+  std::vector<std::string> sources; // the strings of those loads (what they name)
   std::vector<std::string> saves;   // output names, in `save` order (root index)
 };
 

@@ -285,3 +285,24 @@ def test_specification_text_on_the_gpu(mode):
              N("PCT_GT", image=1, q=0.8), N("TOUCH", 2, 10), N("OR", 9, 11)]
     exp = oracle.evaluate(nodes, [6, 12], ims, conn=8).masks
     assert_same(got, exp, mode)
+
+
+@pytest.mark.gpu
+def test_command_line_runs_a_specification_file(tmp_path):
+    """`python -m paper_2010_07284_gb300 SPEC`: loads read NumPy files, saves
+    write the masks; the result equals the oracle."""
+    torch_cuda()
+    from paper_2010_07284_gb300.__main__ import run
+    img = wl.gaussian_field_image(64, 96, seed=3)
+    roi = np.random.default_rng(0).random((64, 96)) < 0.3
+    np.save(tmp_path / "scan.npy", img)
+    np.save(tmp_path / "roi.npy", roi)
+    (tmp_path / "spec.imgql").write_text(
+        'load scan = "scan.npy"\nload roi = "roi.npy"\n'
+        'let hot = intensity(scan) >. 0.6\nsave "out.npy" grow(hot, mask(roi) | hot)\n')
+    written = run(str(tmp_path / "spec.imgql"))
+    got = np.load(written[0])
+    nodes = [("THR_GT", -1, -1, 0, 0, float(np.float32(0.6)), 0.0), ("MASK", -1, -1, 0, 0, 0.0, 0.0),
+             ("OR", 1, 0, 0, 0, 0.0, 0.0), ("GROW", 0, 2, 0, 0, 0.0, 0.0)]
+    exp = oracle.evaluate(nodes, [3], [img], [roi], conn=8).masks[0]
+    assert got.dtype == np.bool_ and np.array_equal(got.astype(np.uint8), exp)
